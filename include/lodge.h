@@ -1,0 +1,235 @@
+/*
+ * lodge.h - C ABI of the GB300 (sm_103a) LODGE frame renderer.
+ *
+ * The library renders a level-of-detail, chunked 3D Gaussian Splatting
+ * scene (arXiv 2505.23158, "LODGE") on one GPU.  Per camera it
+ *   1. picks the two nearest chunk centres and the Eq. 4 blend weights
+ *      (Sec. 3 "Opacity blending"),
+ *   2. takes the active Gaussian set: Eq. 2 at the camera (LOD mode), the
+ *      precomputed set of the nearest chunk (CHUNK), or the union of the two
+ *      nearest chunks with Eq. 4 opacity modulation (CHUNK_BLEND)
+ *      (Sec. 3 "LOD representation", "Chunk-based rendering"),
+ *   3. projects the active Gaussians with EWA covariance, the per-level 3D
+ *      filter of Eq. 3 and degree-3 SH colour (Sec. 3 "Preliminaries: 3DGS"),
+ *   4. bins them to 16x16 tiles, sorts (tile, depth) keys and composites each
+ *      tile front to back with Eq. 1 alpha (Sec. 3 "Preliminaries: 3DGS").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Errors: every call returns a lodge_status; LODGE_OK is 0.  No call aborts
+ *   or throws across the ABI.  lodge_last_error() returns a message for the
+ *   last failing call on the calling thread (valid until the next call on
+ *   that thread).
+ * Pointers: parameters named d_* are DEVICE pointers on the context's
+ *   device; every other pointer is a HOST pointer.  All pointers are
+ *   borrowed for the duration of the call only, except where stated.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Device work of a call is ordered on that stream; host outputs
+ *   are valid when the call returns (the call synchronises the stream where
+ *   it returns host data).
+ * Layouts: images are row-major H x W x 3 float32 (HWC), pixel (i, j) has
+ *   its centre at (i + 0.5, j + 0.5).  Cameras map world to camera as
+ *   p_c = R p_w + t with OpenCV axes (x right, y down, z forward).
+ * Sizes: a scene holds at most 2^30 Gaussians in total; an image at most
+ *   65535 tiles per side.
+ */
+#ifndef LODGE_H
+#define LODGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lodge_ctx lodge_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LODGE_OK = 0,
+    LODGE_E_INVALID = 1,      /* bad argument (message says which) */
+    LODGE_E_OOM = 2,          /* device or pinned host allocation failed */
+    LODGE_E_CUDA = 3,         /* a CUDA runtime call failed */
+    LODGE_E_NOT_RESIDENT = 4, /* chunk data not on the device (streaming mode) */
+    LODGE_E_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    LODGE_E_BUDGET = 6,       /* the context's HBM budget would be exceeded */
+    LODGE_E_OVERFLOW = 7      /* an internal capacity was exceeded */
+} lodge_status;
+
+typedef enum {
+    LODGE_FULL = 0,        /* every Gaussian of level 0 (full detail) */
+    LODGE_LOD = 1,         /* Eq. 2 evaluated at the camera centre */
+    LODGE_CHUNK = 2,       /* precomputed set of the nearest chunk */
+    LODGE_CHUNK_BLEND = 3  /* union of the two nearest chunks, Eq. 4 */
+} lodge_mode;
+
+/* One LOD level G^(l), raw (un-activated) parameters, host memory,
+ * caller-owned, copied by lodge_load_scene.  Activation at load, in FP64
+ * rounded once to FP32: scale = exp(log_scale), opacity = sigmoid(logit),
+ * quaternion divided by its norm. */
+typedef struct {
+    int64_t n;                    /* number of Gaussians in this level */
+    const float* means;           /* n x 3 world positions */
+    const float* log_scales;      /* n x 3 */
+    const float* quats;           /* n x 4 (w, x, y, z), nonzero norm */
+    const float* opacity_logits;  /* n */
+    const float* sh;              /* n x 16 x 3 SH coefficients, coefficient-
+                                     major, real basis order (l, m=-l..l) */
+    float filter_var;             /* variance of the Eq. 3 3D smoothing filter
+                                     for this level (0 = none) */
+    float pad_;
+} lodge_level_desc;
+
+typedef struct {
+    int32_t num_levels;              /* L >= 1, at most 8 */
+    int32_t sh_degree;               /* 0..3 */
+    const lodge_level_desc* levels;  /* L levels, finest first (G^(0)) */
+    const double* d_thresholds;      /* L - 1 ascending distances d_1..d_{L-1}
+                                        (Eq. 2; d_0 = 0, d_L = inf) */
+    int32_t num_chunks;              /* K >= 0 chunk centres (0: FULL/LOD only) */
+    int32_t pad_;
+    const double* chunk_centers;     /* K x 3 */
+} lodge_scene_desc;
+
+typedef struct {
+    float R[9];        /* world -> camera rotation, row-major */
+    float t[3];        /* world -> camera translation */
+    float fx, fy;      /* focal lengths, pixels */
+    float cx, cy;      /* principal point, pixels */
+    int32_t width, height;
+    float znear;       /* Gaussians with camera depth <= znear are culled */
+    float pad_;
+    double center[3];  /* camera position in world coordinates (FP64) */
+} lodge_camera;
+
+/* Per-camera outcome of the selection step (Eq. 2 / Eq. 4). */
+typedef struct {
+    int32_t chunk_a;   /* nearest chunk, -1 in FULL and LOD modes */
+    int32_t chunk_b;   /* second nearest, -1 if none or not blending */
+    double t_a, t_b;   /* Eq. 4 weights of A-only / B-only Gaussians */
+    int64_t n_active;  /* size of the active set */
+} lodge_selection;
+
+/* Per-frame counters of a render (the paper's #G, #Vis. G and tile cost). */
+typedef struct {
+    int64_t n_active;    /* Gaussians selected (loaded for this frame) */
+    int64_t n_visible;   /* Gaussians binned to at least one tile */
+    int64_t n_keys;      /* (tile, Gaussian) pairs */
+    int64_t n_tiles;     /* tiles in the image */
+    int32_t chunk_a, chunk_b;
+    double t_a, t_b;
+} lodge_frame_stats;
+
+/* ---------------------------------------------------------------- setup */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context may hold (scenes + scratch); 0 = no cap.
+ * *out receives the context; destroy it with lodge_destroy. */
+lodge_status lodge_create(int device, size_t hbm_budget_bytes, lodge_ctx** out);
+
+/* Free every device and host resource of the context.  NULL is a no-op. */
+lodge_status lodge_destroy(lodge_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* lodge_last_error(void);
+
+/* Copy a scene to the device (activated, structure-of-arrays, levels
+ * concatenated in order, so a Gaussian's gid = its index in the
+ * concatenation) and precompute every chunk's active set: Eq. 2 at the
+ * chunk centre m_k with thresholds d_l + r_k, r_k = distance to the nearest
+ * other chunk centre (Sec. 3 "Chunk-based rendering").  *scene_id receives
+ * the scene handle.  Synchronous. */
+lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int32_t* scene_id);
+
+/* Release a scene's device memory. */
+lodge_status lodge_unload_scene(lodge_ctx* ctx, int32_t scene_id);
+
+/* Ensure the listed chunks' active sets are resident (Sec. 3 "Opacity
+ * blending": sets are loaded in the background).  In this version every
+ * chunk set is resident after lodge_load_scene, so this validates the ids
+ * and returns. `blocking` is accepted for interface stability. */
+lodge_status lodge_upload_chunks(lodge_ctx* ctx, int32_t scene_id, const int32_t* chunk_ids,
+                                 int32_t n, int blocking);
+
+/* Selection only: for each of n_cams cameras fill out[i] (host).  If d_gids
+ * is not NULL and n_cams == 1, the active gids (ascending, bit 31 = member
+ * of chunk A, bit 30 = member of chunk B in CHUNK_BLEND mode, else 0) are
+ * written to d_gids (device, capacity gids_capacity entries); LODGE_E_OVERFLOW
+ * if it does not fit (out[0].n_active still reports the size). */
+lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
+                              const lodge_camera* cams, int32_t n_cams, lodge_selection* out,
+                              uint32_t* d_gids, int64_t gids_capacity, void* stream);
+
+/* ---------------------------------------------------------------- render */
+
+/* Render n_cams cameras of one scene in `mode`.  d_rgb (device,
+ * caller-owned) receives n_cams images back to back, each H x W x 3 of its
+ * camera.  stats (host, optional) receives n_cams frame counters.  With
+ * save_for_backward != 0 (n_cams must be 1) the frame's intermediate state
+ * is kept under *handle_out until lodge_release.  Returns when the frame has
+ * been enqueued and its counters read (one stream synchronisation). */
+lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
+                          const lodge_camera* cams, int32_t n_cams, float* d_rgb, void* stream,
+                          int32_t save_for_backward, int64_t* handle_out,
+                          lodge_frame_stats* stats);
+
+/* Same as lodge_render but cameras and the image live in HOST memory: the
+ * call copies the image back (device -> host) before returning.  h_rgb:
+ * n_cams images, H x W x 3 float32 each.  Intended for callers that do not
+ * manage device memory; device scratch is owned by the context. */
+lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
+                               const lodge_camera* cams, int32_t n_cams, float* h_rgb,
+                               void* stream, lodge_frame_stats* stats);
+
+/* Render Gaussians given as raw DEVICE parameters (the fine-tuning path of
+ * Sec. 3 "Building LOD", supplementary "LOD structure optimization steps":
+ * only the trained level's parameters change between steps).  Activation is
+ * done on the device in FP32.  Layout as lodge_level_desc.  d_rgb: H x W x 3. */
+lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means,
+                                 const float* d_log_scales, const float* d_quats,
+                                 const float* d_opacity_logits, const float* d_sh,
+                                 int32_t sh_degree, float filter_var, const lodge_camera* cam,
+                                 float* d_rgb, void* stream, int32_t save_for_backward,
+                                 int64_t* handle_out, lodge_frame_stats* stats);
+
+/* Gradients of a saved lodge_render_params frame.  d_dL_drgb: H x W x 3
+ * (device).  Gradients (device, caller-owned, same layouts as the
+ * parameters) are ACCUMULATED (+=) so several views can be summed; zero them
+ * first.  Any gradient pointer may be NULL to skip that group. */
+lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* d_dL_drgb,
+                                   float* d_g_means, float* d_g_log_scales, float* d_g_quats,
+                                   float* d_g_opacity_logits, float* d_g_sh, void* stream);
+
+/* Free a saved frame. */
+lodge_status lodge_release(lodge_ctx* ctx, int64_t handle);
+
+/* ---------------------------------------------------------------- inspection */
+
+/* Sorted tile keys of a saved frame: key = tile_id << 32 | bits(FP32 depth),
+ * tile_id = ty * tiles_x + tx, in the order they are composited, and the gid
+ * of each key.  Device outputs with capacity cap; *n_keys (host) receives
+ * the count; LODGE_E_OVERFLOW if it exceeds cap. */
+lodge_status lodge_debug_keys(lodge_ctx* ctx, int64_t handle, uint64_t* d_keys, uint32_t* d_gids,
+                              int64_t cap, int64_t* n_keys, void* stream);
+
+/* Projection records of a saved frame, one per visible Gaussian in gid
+ * order: d_gid, d_depth (FP32 key depth), d_rect (tx0, ty0, tx1, ty1 int32),
+ * d_mean2 (2 floats), d_conic (3 floats: inverse 2D covariance xx, xy, yy),
+ * d_opacity (final opacity), d_rgb (3 floats).  Any output may be NULL.
+ * *n_visible (host) receives the count; LODGE_E_OVERFLOW if > cap. */
+lodge_status lodge_debug_records(lodge_ctx* ctx, int64_t handle, uint32_t* d_gid, float* d_depth,
+                                 int32_t* d_rect, float* d_mean2, float* d_conic,
+                                 float* d_opacity, float* d_rgb, int64_t cap,
+                                 int64_t* n_visible, void* stream);
+
+/* Sort n (key, value) pairs of 32-bit unsigned integers by the key bits
+ * [0, key_bits), stably, with the library's onesweep LSD radix sort.
+ * d_keys/d_vals are sorted in place (device).  Exposed for testing the sort
+ * (Sec. 3: Gaussians are sorted per tile by depth). */
+lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals, int64_t n,
+                              int32_t key_bits, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LODGE_H */

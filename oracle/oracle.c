@@ -266,8 +266,31 @@ typedef struct {
     float o32;        /* final opacity in FP32 (decides the extent) */
 } orc_key_rec;
 
+/* Camera-relative evaluation point of the key spec.  p = R mu + t equals
+ * R (mu - c_hat) + t' for any c_hat, with t' = t + R c_hat.  Taking c_hat =
+ * (float)center and forming t' in FP64 keeps mu - c_hat exact (Sterbenz) for
+ * Gaussians near the camera, where an FP32 R mu + t would cancel
+ * catastrophically in a world hundreds of metres across. */
+static void cam_rel(const orc_camera* cam, float chat[3], float tp[3])
+{
+    for (int i = 0; i < 3; ++i) chat[i] = (float)cam->center[i];
+    for (int i = 0; i < 3; ++i)
+        tp[i] = (float)((double)cam->t[i] + (((double)cam->R[3 * i] * (double)chat[0]
+                        + (double)cam->R[3 * i + 1] * (double)chat[1]) + (double)cam->R[3 * i + 2] * (double)chat[2]));
+}
+
+static float cam_depth32(const orc_camera* cam, const float* mu)
+{
+    float chat[3], tp[3];
+    cam_rel(cam, chat, tp);
+    const float* R = cam->R;
+    float dx = mu[0] - chat[0], dy = mu[1] - chat[1], dz = mu[2] - chat[2];
+    return ((R[6] * dx + R[7] * dy) + R[8] * dz) + tp[2];
+}
+
 /* Returns 1 if the Gaussian is binned to at least one tile.  Steps:
- *  camera point p = R mu + t, summed left to right; cull unless z > znear;
+ *  camera point p = ((R0 d0 + R1 d1) + R2 d2) + t' per row with
+ *    d = mu - c_hat (FP32) and c_hat, t' from cam_rel; cull unless z > znear;
  *  per-level 3D filter (Eq. 3, variance v): sigma_k = sqrt(s_k^2 + v) and
  *    opacity compensation ((s0/sigma0)(s1/sigma1))(s2/sigma2), only if v > 0;
  *  final opacity o' = (o * mult) [* comp]; cull if o' < 1/255 (no pixel can
@@ -283,9 +306,12 @@ static int key_spec(const orc_scene* sc, const orc_camera* cam, int64_t g,
 {
     const float* mu = sc->means + 3 * g;
     const float* R = cam->R;
-    float px = ((R[0] * mu[0] + R[1] * mu[1]) + R[2] * mu[2]) + cam->t[0];
-    float py = ((R[3] * mu[0] + R[4] * mu[1]) + R[5] * mu[2]) + cam->t[1];
-    float pz = ((R[6] * mu[0] + R[7] * mu[1]) + R[8] * mu[2]) + cam->t[2];
+    float chat[3], tp[3];
+    cam_rel(cam, chat, tp);
+    float d0 = mu[0] - chat[0], d1 = mu[1] - chat[1], d2 = mu[2] - chat[2];
+    float px = ((R[0] * d0 + R[1] * d1) + R[2] * d2) + tp[0];
+    float py = ((R[3] * d0 + R[4] * d1) + R[5] * d2) + tp[1];
+    float pz = ((R[6] * d0 + R[7] * d1) + R[8] * d2) + tp[2];
     if (!(pz > cam->znear)) return 0;
 
     const float* s = sc->scales + 3 * g;
@@ -543,9 +569,7 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, int64_t n_active,
         vis[i] = (uint8_t)key_spec(sc, cam, gids[i], m, &kr[i]);
         if (mode == 1) {
             /* brute force keeps every Gaussian in front of the near plane */
-            const float* mu = sc->means + 3 * gids[i];
-            const float* R = cam->R;
-            float pz = ((R[6] * mu[0] + R[7] * mu[1]) + R[8] * mu[2]) + cam->t[2];
+            float pz = cam_depth32(cam, sc->means + 3 * gids[i]);
             kr[i].z = pz;
             vis[i] = pz > cam->znear;
         }

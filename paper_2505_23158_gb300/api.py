@@ -1,0 +1,229 @@
+"""Python face of the C ABI: device memory and streams come from PyTorch,
+every step of the render runs in liblodge.so.
+
+    ctx = Lodge(device=0)
+    sid = ctx.load_scene(scene)                    # synth.Scene (host arrays)
+    img, stats = ctx.render(sid, CHUNK_BLEND, cam) # cuda float32 (H, W, 3)
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _capi as A
+from ._capi import CHUNK, CHUNK_BLEND, FULL, LOD, LodgeError  # noqa: F401
+
+
+def camera_struct(cam) -> A.lodge_camera:
+    c = A.lodge_camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).ravel()]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32).ravel()]
+    c.fx, c.fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
+    c.cx, c.cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.znear = float(np.float32(cam.znear))
+    c.center[:] = [float(x) for x in np.asarray(cam.center, np.float64)]
+    return c
+
+
+def camera_array(cams) -> C.Array:
+    arr = (A.lodge_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_struct(c)
+    return arr
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def stats_dict(s: A.lodge_frame_stats) -> dict:
+    return dict(n_active=s.n_active, n_visible=s.n_visible, n_keys=s.n_keys, n_tiles=s.n_tiles,
+                chunk_a=s.chunk_a, chunk_b=s.chunk_b, t_a=s.t_a, t_b=s.t_b)
+
+
+class Lodge:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        A.call("lodge_create", self.device, int(hbm_budget_bytes), C.byref(h))
+        self._h = h
+        self._keep = {}
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            A.call("lodge_destroy", self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- scenes
+    def load_scene(self, scene) -> int:
+        levels = (A.lodge_level_desc * scene.num_levels)()
+        keep = []
+        for i, lv in enumerate(scene.levels):
+            arrs = [np.ascontiguousarray(a, np.float32) for a in
+                    (lv.means, lv.log_scales, lv.quats, lv.opacity_logits, lv.sh)]
+            keep += arrs
+            levels[i].n = lv.n
+            levels[i].means, levels[i].log_scales, levels[i].quats, levels[i].opacity_logits, \
+                levels[i].sh = [a.ctypes.data for a in arrs]
+            levels[i].filter_var = float(lv.filter_var)
+        d = np.ascontiguousarray(scene.d_thresholds, np.float64)
+        cc = np.ascontiguousarray(scene.chunk_centers, np.float64)
+        desc = A.lodge_scene_desc()
+        desc.num_levels = scene.num_levels
+        desc.sh_degree = int(scene.sh_degree)
+        desc.levels = C.cast(levels, C.c_void_p)
+        desc.d_thresholds = d.ctypes.data if d.size else None
+        desc.num_chunks = int(cc.shape[0])
+        desc.chunk_centers = cc.ctypes.data if cc.size else None
+        sid = C.c_int32()
+        A.call("lodge_load_scene", self._h, C.byref(desc), C.byref(sid))
+        return sid.value
+
+    def unload_scene(self, sid: int):
+        A.call("lodge_unload_scene", self._h, int(sid))
+
+    def upload_chunks(self, sid: int, chunk_ids: Sequence[int], blocking: bool = True):
+        ids = np.ascontiguousarray(chunk_ids, np.int32)
+        A.call("lodge_upload_chunks", self._h, int(sid), ids.ctypes.data if ids.size else None,
+               int(ids.size), int(blocking))
+
+    # -- selection
+    def select(self, sid: int, mode: int, cam, want_gids: bool = False, stream=None):
+        """(selection dict, gids uint32 cuda tensor or None)."""
+        sel = (A.lodge_selection * 1)()
+        cams = camera_array([cam])
+        gids = None
+        if want_gids:
+            A.call("lodge_select_lod", self._h, int(sid), int(mode), cams, 1, sel, None, 0,
+                   _stream(stream))
+            n = sel[0].n_active
+            gids = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+            A.call("lodge_select_lod", self._h, int(sid), int(mode), cams, 1, sel,
+                   _ptr(gids), n, _stream(stream))
+            gids = gids[:n]
+        else:
+            A.call("lodge_select_lod", self._h, int(sid), int(mode), cams, 1, sel, None, 0,
+                   _stream(stream))
+        s = sel[0]
+        return dict(chunk_a=s.chunk_a, chunk_b=s.chunk_b, t_a=s.t_a, t_b=s.t_b,
+                    n_active=s.n_active), gids
+
+    # -- render
+    def render(self, sid: int, mode: int, cams, out: Optional[torch.Tensor] = None,
+               stream=None, save: bool = False):
+        """Render one camera (or a list).  Returns (image(s), stats list[, handle])."""
+        single = not isinstance(cams, (list, tuple))
+        cl = [cams] if single else list(cams)
+        total = sum(c.width * c.height * 3 for c in cl)
+        if out is None:
+            out = torch.empty(total, dtype=torch.float32, device=f"cuda:{self.device}")
+        st = (A.lodge_frame_stats * len(cl))()
+        h = C.c_int64(0)
+        A.call("lodge_render", self._h, int(sid), int(mode), camera_array(cl), len(cl),
+               _ptr(out), _stream(stream), int(save), C.byref(h), st)
+        imgs, off = [], 0
+        flat = out.view(-1)
+        for c in cl:
+            n = c.width * c.height * 3
+            imgs.append(flat[off:off + n].view(c.height, c.width, 3))
+            off += n
+        stats = [stats_dict(s) for s in st]
+        res = (imgs[0] if single else imgs, stats[0] if single else stats)
+        return res + (h.value,) if save else res
+
+    def render_host(self, sid: int, mode: int, cams, out: np.ndarray, stream=None):
+        cl = list(cams)
+        st = (A.lodge_frame_stats * len(cl))()
+        A.call("lodge_render_host", self._h, int(sid), int(mode), camera_array(cl), len(cl),
+               C.c_void_p(out.ctypes.data), _stream(stream), st)
+        return [stats_dict(s) for s in st]
+
+    def render_params(self, means, log_scales, quats, logits, sh, cam, sh_degree: int = 3,
+                      filter_var: float = 0.0, stream=None, save: bool = True):
+        for t in (means, log_scales, quats, logits, sh):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        out = torch.empty(cam.height, cam.width, 3, dtype=torch.float32, device=means.device)
+        st = A.lodge_frame_stats()
+        h = C.c_int64(0)
+        A.call("lodge_render_params", self._h, int(means.shape[0]), _ptr(means), _ptr(log_scales),
+               _ptr(quats), _ptr(logits), _ptr(sh), int(sh_degree), float(filter_var),
+               C.byref(camera_struct(cam)), _ptr(out), _stream(stream), int(save), C.byref(h),
+               C.byref(st))
+        return out, stats_dict(st), (h.value if save else None)
+
+    def render_backward(self, handle: int, dL_drgb: torch.Tensor, g_means=None, g_log_scales=None,
+                        g_quats=None, g_logits=None, g_sh=None, stream=None):
+        A.call("lodge_render_backward", self._h, int(handle), _ptr(dL_drgb.contiguous()),
+               _ptr(g_means), _ptr(g_log_scales), _ptr(g_quats), _ptr(g_logits), _ptr(g_sh),
+               _stream(stream))
+
+    def release(self, handle: int):
+        A.call("lodge_release", self._h, int(handle))
+
+    # -- inspection
+    def debug_keys(self, handle: int, stream=None):
+        n = C.c_int64(0)
+        try:
+            A.call("lodge_debug_keys", self._h, int(handle), None, None, 0, C.byref(n), _stream(stream))
+        except LodgeError as e:
+            if e.status != 7:
+                raise
+        dev = f"cuda:{self.device}"
+        keys = torch.empty(max(n.value, 1), dtype=torch.int64, device=dev)
+        gids = torch.empty(max(n.value, 1), dtype=torch.int32, device=dev)
+        A.call("lodge_debug_keys", self._h, int(handle), _ptr(keys), _ptr(gids), n.value,
+               C.byref(n), _stream(stream))
+        return keys[:n.value], gids[:n.value]
+
+    def debug_records(self, handle: int, stream=None):
+        n = C.c_int64(0)
+        try:
+            A.call("lodge_debug_records", self._h, int(handle), None, None, None, None, None, None,
+                   None, 0, C.byref(n), _stream(stream))
+        except LodgeError as e:
+            if e.status != 7:
+                raise
+        m = max(n.value, 1)
+        dev = f"cuda:{self.device}"
+        r = dict(gid=torch.empty(m, dtype=torch.int32, device=dev),
+                 depth=torch.empty(m, dtype=torch.float32, device=dev),
+                 rect=torch.empty(m, 4, dtype=torch.int32, device=dev),
+                 mean2=torch.empty(m, 2, dtype=torch.float32, device=dev),
+                 conic=torch.empty(m, 3, dtype=torch.float32, device=dev),
+                 opacity=torch.empty(m, dtype=torch.float32, device=dev),
+                 rgb=torch.empty(m, 3, dtype=torch.float32, device=dev))
+        A.call("lodge_debug_records", self._h, int(handle), _ptr(r["gid"]), _ptr(r["depth"]),
+               _ptr(r["rect"]), _ptr(r["mean2"]), _ptr(r["conic"]), _ptr(r["opacity"]),
+               _ptr(r["rgb"]), n.value, C.byref(n), _stream(stream))
+        return {k: v[:n.value] for k, v in r.items()}
+
+    def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
+        """Stable in-place sort of int32 (bit pattern = uint32) keys and values."""
+        assert keys.dtype == torch.int32 and vals.dtype == torch.int32
+        A.call("lodge_sort_pairs", self._h, _ptr(keys), _ptr(vals), int(keys.numel()), int(key_bits),
+               _stream(stream))

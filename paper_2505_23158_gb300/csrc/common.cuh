@@ -1,0 +1,209 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lodge.h"
+
+namespace lodge {
+
+constexpr int kTile = 16;             // 16x16 pixel tiles (Sec. 3, Preliminaries)
+constexpr int kMaxLevels = 8;
+constexpr uint32_t kFlagA = 1u << 31; // active-list entry belongs to chunk A
+constexpr uint32_t kFlagB = 1u << 30; // ... to chunk B
+constexpr uint32_t kGidMask = (1u << 30) - 1u;
+
+// device status word bits (set with atomicOr, read by the host after a sync)
+constexpr uint32_t kErrTimeout = 1u << 0;   // a bounded spin gave up
+constexpr uint32_t kErrOverflow = 1u << 1;  // an output capacity was exceeded
+constexpr uint32_t kErrBadIndex = 1u << 2;  // an index was out of range
+
+constexpr uint32_t kSpinLimit = 1u << 22;   // iterations before a wait gives up
+
+// ---------------------------------------------------------------------------
+// decoupled look-back over 32-bit status words: flag in bits 31..30, value in
+// bits 29..0 (so per-tile counts must stay below 2^30).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kStAgg = 1u << 30;
+constexpr uint32_t kStInc = 2u << 30;
+constexpr uint32_t kStVal = (1u << 30) - 1u;
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
+    *reinterpret_cast<volatile uint32_t*>(p) = v;
+}
+
+// Warp-cooperative exclusive look-back for one counter (called by a full
+// warp).  status[tile] must have been published as AGG by this tile already
+// (except tile 0, which needs no look-back).  Returns the exclusive prefix in
+// every lane.  A predecessor that stays unpublished for kSpinLimit polls sets
+// kErrTimeout in *err and is counted as 0, so the kernel always terminates.
+__device__ __forceinline__ uint32_t warp_lookback(const uint32_t* status, uint32_t tile,
+                                                  uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0;
+    int64_t pos = (int64_t)tile - 1;
+    while (pos >= 0) {
+        int64_t idx = pos - lane;
+        uint32_t v = kStInc;  // lanes before tile 0 act as an inclusive zero
+        if (idx >= 0) {
+            uint32_t spins = 0;
+            v = ld_volatile(status + idx);
+            while ((v & ~kStVal) == 0u) {
+                if (++spins > kSpinLimit) { atomicOr(err, kErrTimeout); v = kStInc; break; }
+                __nanosleep(32);
+                v = ld_volatile(status + idx);
+            }
+        }
+        uint32_t inc_mask = __ballot_sync(0xffffffffu, (v & ~kStVal) == kStInc);
+        int stop = inc_mask ? (__ffs(inc_mask) - 1) : 31;
+        uint32_t mine = (lane <= stop) ? (v & kStVal) : 0u;
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        prefix += mine;
+        if (inc_mask) break;
+        pos -= 32;
+    }
+    return prefix;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x multiple of
+// 32, at most 1024).  `scratch` holds >= 33 words of shared memory.  Returns
+// the exclusive prefix; *total receives the block sum (all threads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* scratch,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < nwarps) ? scratch[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nwarps) scratch[lane] = w;  // inclusive per-warp totals
+        if (lane == 31) scratch[32] = w;
+    }
+    __syncthreads();
+    uint32_t warp_prefix = warp ? scratch[warp - 1] : 0u;
+    *total = scratch[32];
+    uint32_t r = warp_prefix + x - v;
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// device-side scene (structure of arrays, levels concatenated)
+// ---------------------------------------------------------------------------
+struct DevScene {
+    int64_t n_total = 0;
+    int32_t num_levels = 0;
+    int32_t sh_degree = 3;
+    int64_t level_off[kMaxLevels + 1] = {0};
+    float filter_var[kMaxLevels] = {0};
+    const float* mx = nullptr;   // means, one plane per axis
+    const float* my = nullptr;
+    const float* mz = nullptr;
+    const float4* scale_op = nullptr;  // (s0, s1, s2, opacity), activated
+    const float4* quat = nullptr;      // unit (w, x, y, z)
+    const float4* sh = nullptr;        // 12 planes of n_total float4 (48 coeffs)
+};
+
+// camera as seen by kernels
+struct DevCamera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;
+    // camera-relative evaluation: p = R (mu - chat) + tp, with chat = (float)
+    // centre and tp = t + R chat formed in FP64; clo = centre - chat
+    float chat[3];
+    float tp[3];
+    float clo[3];
+    int32_t tiles_x, tiles_y;
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct SortScratch;
+
+// K1: Eq. 2 stream compaction.  thr_lo/thr_hi: per level squared distance
+// bounds in FP32.  Writes selected gids (ascending) to out, count to
+// *d_count.  status must hold ceil(n / kSelectTile) words, zeroed, plus one
+// tile counter at status_counter (zeroed).
+constexpr int kSelectThreads = 256;
+constexpr int kSelectIPT = 16;
+constexpr int kSelectTile = kSelectThreads * kSelectIPT;
+void launch_lod_select(const DevScene& sc, const float c32[3], const float* thr_lo,
+                       const float* thr_hi, uint32_t* out, uint32_t* d_count, uint32_t* status,
+                       uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+
+// K2: union of two gid-ascending lists with membership flags (bit 31 = A,
+// bit 30 = B).  marks: n_total bytes of scratch.
+void launch_chunk_union(const uint32_t* a, int64_t na, const uint32_t* b, int64_t nb,
+                        int64_t n_total, uint8_t* marks, uint32_t* out, uint32_t* d_count,
+                        uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+
+// K3: projection + SH + visibility compaction.
+struct ProjectOut {
+    float4* rec_a;      // (mean'x, mean'y, u00, u01)
+    float4* rec_b;      // (u11, opacity', r, g)
+    float* rec_c;       // b
+    uint2* rec_rect;    // (tx0 | ty0 << 16, tx1 | ty1 << 16)
+    uint32_t* rec_gid;  // gid of the record
+    uint32_t* depth_key;  // FP32 depth bits (sort key), index = record
+    uint32_t* depth_val;  // record index
+    uint32_t* counts;     // 8-byte aligned: [0] = visible (u32), [2..3] = keys (u64)
+};
+constexpr int kProjThreads = 256;
+void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* list,
+                    int64_t n_active, float tA, float tB, const ProjectOut& o, uint32_t* status,
+                    uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+// copy the extent table to this device's constant memory (once per device)
+cudaError_t upload_qtable(const float* q65);
+
+// onesweep LSD radix sort of (u32 key, u32 value) pairs on key bits
+// [0, key_bits).  Result lands in (keys, vals) or (keys_alt, vals_alt):
+// the return value says which (0 = keys/vals).
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 15;
+constexpr int kSortTile = kSortThreads * kSortIPT;
+size_t sort_scratch_bytes(int64_t n, int key_bits);
+int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                    int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s);
+
+// K4: emit (tile, record) pairs in depth order.
+constexpr int kEmitThreads = 256;
+void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
+                 int32_t tiles_x, uint32_t* tile_key, uint32_t* tile_val, int64_t cap,
+                 uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+
+// K6: per tile [begin, end) of the sorted keys; ranges zeroed by the caller.
+void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,
+                   cudaStream_t s);
+
+// K7: per tile front-to-back compositing.
+struct BlendOut {
+    float* rgb;        // H x W x 3
+    float* T_final;    // H x W (may be null)
+    uint32_t* last;    // H x W (may be null): keys processed up to the last blended one
+};
+void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+                  int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                  int64_t n_rec, const BlendOut& o, cudaStream_t s);
+
+// Q table for the opacity-aware extent (65 entries), host-computed.
+void fill_qtable(float* q65);
+
+}  // namespace lodge

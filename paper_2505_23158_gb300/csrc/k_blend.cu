@@ -1,0 +1,136 @@
+// K7: per-tile front-to-back alpha compositing (Eq. 1; Sec. 3
+// "Preliminaries: 3DGS").  One CTA per 16x16 tile, one thread per pixel;
+// each warp covers an 8x4 block so that its pixels terminate together.
+// The tile's Gaussians arrive in batches of 256 records, gathered from the
+// projection records into shared memory with cp.async and double-buffered
+// (batch b+1 is in flight while batch b is composited).  A pixel stops at
+// the first Gaussian that would take its transmittance below 1e-4; a warp
+// whose 32 pixels have all stopped skips the batch, and the CTA leaves as
+// soon as all 256 have stopped.
+//
+// Per pixel and Gaussian (record = mean', upper-triangular U with
+// U^T U = (1/2) log2(e) Sigma'^-1, opacity o', colour):
+//   q = (u00 dx + u01 dy)^2 + (u11 dy)^2,  alpha = min(0.99, o' 2^-q)
+//   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
+//   C += T alpha rgb; T = T'.
+#include "common.cuh"
+
+namespace lodge {
+
+namespace {
+
+constexpr int kBatch = 256;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__global__ void __launch_bounds__(256)
+blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __restrict__ ranges,
+             const uint32_t* __restrict__ tile_val, uint32_t n_keys, uint32_t n_rec,
+             const float4* __restrict__ rec_a,
+             const float4* __restrict__ rec_b, const float* __restrict__ rec_c,
+             float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_last) {
+    __shared__ float4 sa[2][kBatch];
+    __shared__ float4 sb[2][kBatch];
+    __shared__ float sc[2][kBatch];
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x = tx * kTile + (warp & 1) * 8 + (lane & 7);
+    const int y = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside = x < width && y < height;
+    const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
+    uint2 rg = ranges[tile];
+    if (rg.y > n_keys || rg.x > rg.y) rg = make_uint2(0, 0);  // never for a consistent sort
+    const int n = (int)(rg.y - rg.x);
+    const int nb = (n + kBatch - 1) / kBatch;
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    bool done = !inside;
+    uint32_t last = 0;
+
+    if (nb > 0) {
+        if (tid < n) {
+            uint32_t j = min(tile_val[rg.x + tid], n_rec - 1u);
+            cp_async16(&sa[0][tid], rec_a + j);
+            cp_async16(&sb[0][tid], rec_b + j);
+            cp_async4(&sc[0][tid], rec_c + j);
+        }
+        cp_async_commit();
+    }
+    for (int b = 0; b < nb; ++b) {
+        const int buf = b & 1;
+        if (b + 1 < nb) {
+            int k = (b + 1) * kBatch + tid;
+            if (k < n) {
+                uint32_t j = min(tile_val[rg.x + k], n_rec - 1u);
+                cp_async16(&sa[buf ^ 1][tid], rec_a + j);
+                cp_async16(&sb[buf ^ 1][tid], rec_b + j);
+                cp_async4(&sc[buf ^ 1][tid], rec_c + j);
+            }
+        }
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int cnt = min(kBatch, n - b * kBatch);
+        if (!__all_sync(0xffffffffu, done)) {
+            for (int k = 0; k < cnt && !done; ++k) {
+                const float4 a = sa[buf][k];
+                const float dx = pxf - a.x, dy = pyf - a.y;
+                const float t = fmaf(a.z, dx, a.w * dy);
+                const float4 bb = sb[buf][k];
+                const float wq = bb.x * dy;
+                const float q = fmaf(t, t, wq * wq);
+                const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+                if (alpha < (1.0f / 255.0f)) continue;
+                const float Tn = T * (1.f - alpha);
+                if (Tn < 1e-4f) { done = true; break; }
+                const float wgt = T * alpha;
+                C0 = fmaf(wgt, bb.z, C0);
+                C1 = fmaf(wgt, bb.w, C1);
+                C2 = fmaf(wgt, sc[buf][k], C2);
+                T = Tn;
+                last = (uint32_t)(b * kBatch + k + 1);
+            }
+        }
+        if (__syncthreads_count(done) == 256) break;
+    }
+    cp_async_wait0();
+    if (inside) {
+        const int64_t pix = (int64_t)y * width + x;
+        out_rgb[3 * pix + 0] = C0;
+        out_rgb[3 * pix + 1] = C1;
+        out_rgb[3 * pix + 2] = C2;
+        if (out_T) out_T[pix] = T;
+        if (out_last) out_last[pix] = last;
+    }
+}
+
+}  // namespace
+
+void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+                  int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                  int64_t n_rec, const BlendOut& o, cudaStream_t s) {
+    int ntiles = cam.tiles_x * cam.tiles_y;
+    if (ntiles == 0) return;
+    blend_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val,
+                                        (uint32_t)n_keys, (uint32_t)std::max<int64_t>(n_rec, 1),
+                                        rec_a, rec_b, rec_c, o.rgb, o.T_final, o.last);
+}
+
+}  // namespace lodge

@@ -1,0 +1,263 @@
+// K3: projection of the active Gaussians (EWA splatting with the per-level
+// Eq. 3 filter and the Eq. 4 opacity multiplier), degree-3 SH colour, tile
+// rect and visibility compaction in one pass (decoupled look-back), so the
+// records come out dense and in gid order.
+//
+// The integer outcomes (near cull, opacity cull, tile rect) and the depth
+// sort key are computed by the "key spec": FP32 with every operation
+// rounded (__fmul_rn / __fadd_rn / __fdiv_rn / __fsqrt_rn, no contraction),
+// in a fixed order, so they are reproducible bit for bit.  Everything that
+// only reaches pixels (the inverse covariance, colour) uses ordinary FP32.
+#include "common.cuh"
+
+namespace lodge {
+
+namespace {
+
+__constant__ float c_qtable[65];
+
+struct ProjParams {
+    DevScene sc;
+    DevCamera cam;
+    const uint32_t* list;   // active list (gid | flags) or null = dense level 0
+    int64_t n_active;
+    int64_t n_pad;          // plane stride of the SH planes
+    float tA, tB;
+    ProjectOut o;
+};
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+
+// opacity-aware extent: bucket = FP32 exponent and 3 leading mantissa bits
+__device__ __forceinline__ float extent_q(float o) {
+    uint32_t top = __float_as_uint(o) >> 20;
+    uint32_t b = top - (119u << 3);
+    if (top > (127u << 3)) b = 64u;
+    return c_qtable[b];
+}
+
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kC1 = 0.4886025119029199f;
+constexpr float kC2a = 1.0925484305920792f;
+constexpr float kC2b = 0.31539156525252005f;
+constexpr float kC2c = 0.5462742152960396f;
+constexpr float kC3a = 0.5900435899266435f;
+constexpr float kC3b = 2.890611442640554f;
+constexpr float kC3c = 0.4570457994644658f;
+constexpr float kC3d = 0.3731763325901154f;
+constexpr float kC3e = 1.445305721320277f;
+constexpr float kHalfLog2e = 0.7213475204444817f;  // (1/2) log2(e)
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = kY0;
+    Y[1] = kC1 * y; Y[2] = kC1 * z; Y[3] = kC1 * x;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kC2a * x * y; Y[5] = kC2a * y * z; Y[6] = kC2b * (3.f * zz - 1.f);
+    Y[7] = kC2a * x * z; Y[8] = kC2c * (xx - yy);
+    Y[9] = kC3a * y * (3.f * xx - yy);
+    Y[10] = kC3b * x * y * z;
+    Y[11] = kC3c * y * (5.f * zz - 1.f);
+    Y[12] = kC3d * z * (5.f * zz - 3.f);
+    Y[13] = kC3c * x * (5.f * zz - 1.f);
+    Y[14] = kC3e * z * (xx - yy);
+    Y[15] = kC3a * x * (xx - 3.f * yy);
+}
+
+__global__ void __launch_bounds__(kProjThreads)
+project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+               uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_scan[33];
+    __shared__ unsigned long long s_keys;
+    if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_keys = 0ull; }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t ntiles = (uint32_t)((P.n_active + kProjThreads - 1) / kProjThreads);
+    const int64_t i = (int64_t)tile * kProjThreads + threadIdx.x;
+    const DevScene& sc = P.sc;
+    const DevCamera& cam = P.cam;
+
+    bool vis = false;
+    uint32_t g = 0;
+    float z = 0.f, mxp = 0.f, myp = 0.f, o = 0.f;
+    float B0[3], B1[3];
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    uint32_t rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
+    if (i < P.n_active) {
+        uint32_t e = P.list ? P.list[i] : (uint32_t)i;
+        g = e & kGidMask;
+        float mult = 1.f;
+        if ((e & kFlagA) && !(e & kFlagB)) mult = P.tA;
+        else if ((e & kFlagB) && !(e & kFlagA)) mult = P.tB;
+        if ((int64_t)g >= sc.n_total) { atomicOr(err, kErrBadIndex); g = 0; mult = 0.f; }
+        const float* R = cam.R;
+        // key spec: camera-space point relative to chat, summed left to right
+        d0 = fs(sc.mx[g], cam.chat[0]);
+        d1 = fs(sc.my[g], cam.chat[1]);
+        d2 = fs(sc.mz[g], cam.chat[2]);
+        float px = fa(fa(fa(fm(R[0], d0), fm(R[1], d1)), fm(R[2], d2)), cam.tp[0]);
+        float py = fa(fa(fa(fm(R[3], d0), fm(R[4], d1)), fm(R[5], d2)), cam.tp[1]);
+        float pz = fa(fa(fa(fm(R[6], d0), fm(R[7], d1)), fm(R[8], d2)), cam.tp[2]);
+        if (pz > cam.znear) {
+            const float4 so = sc.scale_op[g];
+            int l = 0;
+            while (l + 1 < sc.num_levels && (int64_t)g >= sc.level_off[l + 1]) ++l;
+            const float v = sc.filter_var[l];
+            float sig0 = so.x, sig1 = so.y, sig2 = so.z;
+            float op = fm(so.w, mult);
+            if (v > 0.f) {
+                sig0 = __fsqrt_rn(fa(fm(so.x, so.x), v));
+                sig1 = __fsqrt_rn(fa(fm(so.y, so.y), v));
+                sig2 = __fsqrt_rn(fa(fm(so.z, so.z), v));
+                float comp = fm(fm(__fdiv_rn(so.x, sig0), __fdiv_rn(so.y, sig1)), __fdiv_rn(so.z, sig2));
+                op = fm(op, comp);
+            }
+            if (op >= (float)(1.0 / 255.0)) {
+                const float Q = extent_q(op);
+                const float4 q = sc.quat[g];
+                float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
+                float mx = fa(fm(cam.fx, u), cam.cx);
+                float my = fa(fm(cam.fy, w), cam.cy);
+                float j00 = __fdiv_rn(cam.fx, pz), j02 = -fm(j00, u);
+                float j11 = __fdiv_rn(cam.fy, pz), j12 = -fm(j11, w);
+                float T0[3], T1[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    T0[k] = fa(fm(j00, R[k]), fm(j02, R[6 + k]));
+                    T1[k] = fa(fm(j11, R[3 + k]), fm(j12, R[6 + k]));
+                }
+                float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+                float xx = fm(qx, qx), yy = fm(qy, qy), zz = fm(qz, qz);
+                float xy = fm(qx, qy), xz = fm(qx, qz), yz = fm(qy, qz);
+                float wx = fm(qw, qx), wy = fm(qw, qy), wz = fm(qw, qz);
+                float M[3][3];
+                M[0][0] = fs(1.f, fm(2.f, fa(yy, zz))); M[0][1] = fm(2.f, fs(xy, wz)); M[0][2] = fm(2.f, fa(xz, wy));
+                M[1][0] = fm(2.f, fa(xy, wz)); M[1][1] = fs(1.f, fm(2.f, fa(xx, zz))); M[1][2] = fm(2.f, fs(yz, wx));
+                M[2][0] = fm(2.f, fs(xz, wy)); M[2][1] = fm(2.f, fa(yz, wx)); M[2][2] = fs(1.f, fm(2.f, fa(xx, yy)));
+                const float sig[3] = {sig0, sig1, sig2};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float a0 = fa(fa(fm(T0[0], M[0][k]), fm(T0[1], M[1][k])), fm(T0[2], M[2][k]));
+                    float a1 = fa(fa(fm(T1[0], M[0][k]), fm(T1[1], M[1][k])), fm(T1[2], M[2][k]));
+                    B0[k] = fm(a0, sig[k]);
+                    B1[k] = fm(a1, sig[k]);
+                }
+                float sxx = fa(fa(fa(fm(B0[0], B0[0]), fm(B0[1], B0[1])), fm(B0[2], B0[2])), 0.3f);
+                float syy = fa(fa(fa(fm(B1[0], B1[0]), fm(B1[1], B1[1])), fm(B1[2], B1[2])), 0.3f);
+                float rx = __fsqrt_rn(fm(Q, sxx)), ry = __fsqrt_rn(fm(Q, syy));
+                float x0 = ceilf(fs(fs(mx, rx), 0.5f)), x1 = floorf(fs(fa(mx, rx), 0.5f));
+                float y0 = ceilf(fs(fs(my, ry), 0.5f)), y1 = floorf(fs(fa(my, ry), 0.5f));
+                const float xmax = (float)(cam.width - 1), ymax = (float)(cam.height - 1);
+                if (x0 < 0.f) x0 = 0.f;
+                if (y0 < 0.f) y0 = 0.f;
+                if (x1 > xmax) x1 = xmax;
+                if (y1 > ymax) y1 = ymax;
+                if (x0 <= x1 && y0 <= y1) {
+                    vis = true;
+                    z = pz; mxp = mx; myp = my; o = op;
+                    rx0 = (uint32_t)(int)x0 / kTile; ry0 = (uint32_t)(int)y0 / kTile;
+                    rx1 = (uint32_t)(int)x1 / kTile; ry1 = (uint32_t)(int)y1 / kTile;
+                }
+            }
+        }
+    }
+
+    // ---- compaction of visible records (gid order preserved)
+    uint32_t total;
+    uint32_t excl = block_exclusive_scan(vis ? 1u : 0u, s_scan, &total);
+    uint32_t nk = vis ? (rx1 - rx0 + 1) * (ry1 - ry0 + 1) : 0u;
+    {
+        uint32_t wsum = nk;
+        for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
+    }
+    if (threadIdx.x < 32) {
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) st_volatile(status, kStInc | total);
+        } else {
+            if (threadIdx.x == 0) st_volatile(status + tile, kStAgg | total);
+            prefix = warp_lookback(status, tile, err);
+            if (threadIdx.x == 0) st_volatile(status + tile, kStInc | (prefix + total));
+        }
+        if (threadIdx.x == 0) {
+            s_prefix = prefix;
+            if (tile == ntiles - 1) P.o.counts[0] = prefix + total;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_keys)
+        atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 2), s_keys);
+    if (!vis) return;
+
+    // ---- inverse 2D covariance in Cholesky form, with (1/2) log2(e) folded
+    // in: alpha = o' * 2^-((u00 dx + u01 dy)^2 + (u11 dy)^2).  The
+    // determinant uses the Cauchy-Binet sum of squared 2x2 minors, which has
+    // no cancellation (Sigma' = B B^T + 0.3 I).
+    const float aB = B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2];
+    const float cB = B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2];
+    const float bB = B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2];
+    const float m01 = fmaf(B0[0], B1[1], -B0[1] * B1[0]);
+    const float m02 = fmaf(B0[0], B1[2], -B0[2] * B1[0]);
+    const float m12 = fmaf(B0[1], B1[2], -B0[2] * B1[1]);
+    const float D = m01 * m01 + m02 * m02 + m12 * m12 + 0.3f * (aB + cB) + 0.09f;
+    const float c = cB + 0.3f;
+    const float rD = 1.0f / sqrtf(D);
+    const float u11 = sqrtf(kHalfLog2e / c);
+    const float u00 = u11 * c * rD;
+    const float u01 = -u11 * bB * rD;
+
+    // ---- colour: real SH up to degree 3 at the unit direction camera -> mean
+    float dx = d0 - cam.clo[0], dy = d1 - cam.clo[1], dz = d2 - cam.clo[2];
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float Y[16];
+    sh_basis(dx * inv, dy * inv, dz * inv, Y);
+    const int nf = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
+    float rgb[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        if (4 * j >= nf) break;
+        float4 v4 = __ldcs(sc.sh + (int64_t)j * P.n_pad + g);
+        float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int idx = 4 * j + cc;
+            if (idx < nf) rgb[idx % 3] = fmaf(Y[idx / 3], vv[cc], rgb[idx % 3]);
+        }
+    }
+    const uint32_t pos = s_prefix + excl;
+    P.o.rec_a[pos] = make_float4(mxp, myp, u00, u01);
+    P.o.rec_b[pos] = make_float4(u11, o, fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
+    P.o.rec_c[pos] = fmaxf(rgb[2], 0.f);
+    P.o.rec_rect[pos] = make_uint2(rx0 | (ry0 << 16), rx1 | (ry1 << 16));
+    P.o.rec_gid[pos] = g;
+    P.o.depth_key[pos] = __float_as_uint(z);
+    P.o.depth_val[pos] = pos;
+}
+
+}  // namespace
+
+cudaError_t upload_qtable(const float* q65) {
+    return cudaMemcpyToSymbol(c_qtable, q65, sizeof(float) * 65);
+}
+
+void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* list,
+                    int64_t n_active, float tA, float tB, const ProjectOut& o, uint32_t* status,
+                    uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
+    ProjParams P;
+    P.sc = sc;
+    P.cam = cam;
+    P.list = list;
+    P.n_active = n_active;
+    P.n_pad = (sc.n_total + 63) / 64 * 64;
+    P.tA = tA;
+    P.tB = tB;
+    P.o = o;
+    int64_t ntiles = (n_active + kProjThreads - 1) / kProjThreads;
+    if (ntiles == 0) return;
+    project_kernel<<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
+}
+
+}  // namespace lodge

@@ -1,0 +1,195 @@
+// K5: stable LSD radix sort of (u32 key, u32 value) pairs, "onesweep" style:
+// one upfront pass builds every digit histogram, then each 8-bit digit is
+// scattered in a single pass in which a tile learns its global offsets by
+// decoupled look-back over its predecessors' per-digit counts.
+//
+// Used twice per frame: by FP32 depth (4 digits) over the visible records,
+// then by tile id over the emitted (tile, record) pairs, which yields the
+// per-tile front-to-back order of Sec. 3 ("Preliminaries: 3DGS": Gaussians
+// are sorted by depth per tile) with ties broken by record (= gid) order.
+#include "common.cuh"
+
+namespace lodge {
+
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kWarps = kSortThreads / 32;
+constexpr int kMaxPasses = 4;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(256)
+hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int passes, uint32_t last_mask,
+            uint32_t* __restrict__ hist) {
+    __shared__ uint32_t sh[kMaxPasses][kRadix];
+    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t k = __ldg(keys + i);
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&sh[p][(k >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+        uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+}
+
+// exclusive scan of each pass's 256-bin histogram, in place (one block per pass)
+__global__ void hist_scan_kernel(uint32_t* hist) {
+    __shared__ uint32_t s_scan[33];
+    uint32_t* h = hist + blockIdx.x * kRadix;
+    uint32_t v = h[threadIdx.x], total;
+    uint32_t e = block_exclusive_scan(v, s_scan, &total);
+    h[threadIdx.x] = e;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+              uint32_t dmask, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ status,
+              uint32_t* __restrict__ counter, uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_whist[kWarps][kRadix];
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_dstart[kRadix];
+    __shared__ uint32_t s_gbase[kRadix];
+    __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kSortTile + (int64_t)warp * 32 * kSortIPT;
+
+    uint32_t k[kSortIPT], v[kSortIPT], rank[kSortIPT];
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        int64_t idx = base + j * 32 + lane;
+        bool valid = idx < n;
+        k[j] = valid ? __ldcs(kin + idx) : 0u;
+        v[j] = valid ? __ldcs(vin + idx) : 0u;
+    }
+    // warp-private stable ranking in (j, lane) order = input order
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        int64_t idx = base + j * 32 + lane;
+        bool valid = idx < n;
+        uint32_t d = valid ? (k[j] >> shift) & dmask : 0x100u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? s_whist[warp][d] : 0u;
+        rank[j] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) s_whist[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per digit (thread d): warp offsets inside the tile, tile count
+    const uint32_t d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t c = s_whist[w][d];
+        s_whist[w][d] = run;
+        run += c;
+    }
+    // decoupled look-back for this digit
+    uint32_t excl = 0;
+    uint32_t* st = status + (size_t)tile * kRadix + d;
+    if (tile == 0) {
+        st_volatile(st, kStInc | run);
+    } else {
+        st_volatile(st, kStAgg | run);
+        int64_t t = (int64_t)tile - 1;
+        while (t >= 0) {
+            const uint32_t* p = status + (size_t)t * kRadix + d;
+            uint32_t x = ld_volatile(p), spins = 0;
+            while ((x & ~kStVal) == 0u) {
+                if (++spins > kSpinLimit) { atomicOr(err, kErrTimeout); x = kStInc; break; }
+                __nanosleep(20);
+                x = ld_volatile(p);
+            }
+            excl += x & kStVal;
+            if ((x & ~kStVal) == kStInc) break;
+            --t;
+        }
+        st_volatile(st, kStInc | (excl + run));
+    }
+    s_gbase[d] = offsets[d] + excl;
+    uint32_t total;
+    s_dstart[d] = block_exclusive_scan(run, s_scan, &total);
+    __syncthreads();
+
+    // scatter into shared memory in digit order, then write out coalesced
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        int64_t idx = base + j * 32 + lane;
+        if (idx < n) {
+            uint32_t dd = (k[j] >> shift) & dmask;
+            uint32_t pos = s_dstart[dd] + s_whist[warp][dd] + rank[j];
+            s_keys[pos] = k[j];
+            s_vals[pos] = v[j];
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < total; i += kSortThreads) {
+        uint32_t key = s_keys[i];
+        uint32_t dd = (key >> shift) & dmask;
+        uint32_t out = s_gbase[dd] + (i - s_dstart[dd]);
+        if ((int64_t)out < n) {
+            kout[out] = key;
+            vout[out] = s_vals[i];
+        } else {
+            atomicOr(err, kErrOverflow);  // only after a look-back gave up
+        }
+    }
+}
+
+int passes_for(int key_bits) { return key_bits <= 0 ? 0 : (key_bits + 7) / 8; }
+
+}  // namespace
+
+size_t sort_scratch_bytes(int64_t n, int key_bits) {
+    int P = passes_for(key_bits);
+    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    return sizeof(uint32_t) * (size_t)(kMaxPasses * kRadix + 32 + (int64_t)P * ntiles * kRadix);
+}
+
+int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                    int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s) {
+    const int P = passes_for(key_bits);
+    if (n <= 1 || P == 0) return 0;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    uint32_t* hist = static_cast<uint32_t*>(scratch);
+    uint32_t* counters = hist + kMaxPasses * kRadix;
+    uint32_t* status = counters + 32;
+    cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bits), s);
+    int hist_blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 4);
+    // the last digit covers only the bits below key_bits
+    const int last_bits = key_bits - 8 * (P - 1);
+    const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
+    hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n, P, last_mask, hist);
+    hist_scan_kernel<<<P, kRadix, 0, s>>>(hist);
+    uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+    for (int p = 0; p < P; ++p) {
+        onesweep_pass<<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+            ki, vi, ko, vo, n, 8 * p, p == P - 1 ? last_mask : 0xffu, hist + p * kRadix, status + (size_t)p * ntiles * kRadix,
+            counters + p, err);
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+    return (P & 1) ? 1 : 0;
+}
+
+}  // namespace lodge

@@ -1,0 +1,1041 @@
+// C ABI of the LODGE frame renderer: context and scene management, chunk
+// choice (Eq. 4), per-chunk active-set precompute (Eq. 2 at chunk centres,
+// Sec. 3 "Chunk-based rendering") and the per-frame orchestration of the
+// kernels K1..K7 on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lodge {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static lodge_status fail(lodge_status s, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(x)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(LODGE_E_CUDA, "%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+#define TRY(x)                                   \
+    do {                                         \
+        lodge_status s_ = (x);                   \
+        if (s_ != LODGE_OK) return s_;           \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers with budget accounting
+// ---------------------------------------------------------------------------
+struct DBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct Chunk {
+    uint32_t* list = nullptr;
+    int64_t n = 0;
+};
+
+struct Scene {
+    DevScene dev;
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    int64_t n_pad = 0;
+    std::vector<double> d_inner;
+    std::vector<double> centers;
+    std::vector<double> radius;
+    std::vector<Chunk> chunks;
+    size_t chunk_bytes = 0;
+    // union of the current chunk pair (recomputed when the pair changes)
+    int ua = -2, ub = -2;
+    DBuf ulist;
+    int64_t un = 0;
+};
+
+struct Saved {
+    DevCamera cam{};
+    int64_t n_vis = 0, n_keys = 0;
+    DBuf rec_a, rec_b, rec_c, rec_rect, rec_gid, zsorted, rsorted, tkey, tval, ranges, T, last;
+    // raw-parameter frames (fine-tuning path)
+    bool params = false;
+    int64_t n = 0;
+    const float *means = nullptr, *log_scales = nullptr, *quats = nullptr, *logits = nullptr,
+                *sh = nullptr;
+    int sh_degree = 3;
+    float filter_var = 0.f;
+    DBuf act_so, act_q;
+};
+
+struct Workspace {
+    DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
+        tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp;
+};
+
+// small device/host words
+enum : int {
+    kSmErr = 0,
+    kSmListCount = 1,
+    kSmProj = 2,        // [2] visible, [4..5] keys (u64)
+    kSmCtrSelect = 8,
+    kSmCtrUnion = 9,
+    kSmCtrProj = 10,
+    kSmCtrEmit = 11,
+    kSmWords = 64
+};
+
+}  // namespace lodge
+
+using namespace lodge;
+
+struct lodge_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::vector<std::unique_ptr<Scene>> scenes;
+    Workspace ws;
+    uint32_t* d_small = nullptr;
+    uint32_t* h_small = nullptr;  // pinned
+    std::map<int64_t, std::unique_ptr<Saved>> saved;
+    int64_t next_handle = 1;
+};
+
+namespace lodge {
+
+static lodge_status reserve(lodge_ctx* ctx, size_t bytes) {
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(LODGE_E_BUDGET, "HBM budget exceeded: %zu in use + %zu requested > %zu",
+                    ctx->used, bytes, ctx->budget);
+    return LODGE_OK;
+}
+
+static lodge_status dmalloc(lodge_ctx* ctx, void** p, size_t bytes) {
+    TRY(reserve(ctx, bytes));
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LODGE_E_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->used += bytes;
+    return LODGE_OK;
+}
+
+static void dfree(lodge_ctx* ctx, void* p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        ctx->used -= bytes;
+    }
+}
+
+// grow-only, stream-ordered
+static lodge_status ensure(lodge_ctx* ctx, DBuf& b, size_t bytes, cudaStream_t s) {
+    if (bytes <= b.cap && b.p) return LODGE_OK;
+    size_t ncap = std::max<size_t>(bytes + bytes / 4, 4096);
+    ncap = (ncap + 255) / 256 * 256;
+    size_t freed = b.p ? b.cap : 0;
+    if (ctx->budget && ctx->used - freed + ncap > ctx->budget) {
+        ncap = (bytes + 255) / 256 * 256;
+        if (ctx->used - freed + ncap > ctx->budget)
+            return fail(LODGE_E_BUDGET, "HBM budget exceeded growing scratch to %zu bytes", ncap);
+    }
+    if (b.p) {
+        cudaFreeAsync(b.p, s);
+        ctx->used -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMallocAsync(&b.p, ncap, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(LODGE_E_OOM, "cudaMallocAsync(%zu) failed: %s", ncap, cudaGetErrorString(e));
+    }
+    b.cap = ncap;
+    ctx->used += ncap;
+    return LODGE_OK;
+}
+
+static void release(lodge_ctx* ctx, DBuf& b, cudaStream_t s) {
+    if (b.p) {
+        cudaFreeAsync(b.p, s);
+        ctx->used -= b.cap;
+    }
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers (FP64, no contraction: the library is built with
+// -ffp-contract=off so these round exactly as written)
+// ---------------------------------------------------------------------------
+template <class F>
+static void parallel_for(int64_t n, F f) {
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n < 65536 || nt == 1) { f(0, n); return; }
+    std::vector<std::thread> th;
+    int64_t step = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t) {
+        int64_t a = t * step, b = std::min<int64_t>(n, a + step);
+        if (a >= b) break;
+        th.emplace_back([=] { f(a, b); });
+    }
+    for (auto& t : th) t.join();
+}
+
+static double dist2(const double* a, const double* b) {
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+// Two nearest chunk centres (ties to the lower index) and Eq. 4 weights.
+static void chunk_pick(const std::vector<double>& centers, const double* c, int* A, int* B,
+                       double* tA, double* tB) {
+    int K = (int)(centers.size() / 3), a = -1, b = -1;
+    double da = INFINITY, db = INFINITY;
+    for (int k = 0; k < K; ++k) {
+        double d = dist2(c, &centers[3 * k]);
+        if (d < da) { b = a; db = da; a = k; da = d; }
+        else if (d < db) { b = k; db = d; }
+    }
+    *A = a; *B = b;
+    if (b < 0) { *tA = 1.0; *tB = 1.0; return; }
+    const double* mA = &centers[3 * a];
+    const double* mB = &centers[3 * b];
+    double ab[3] = {mA[0] - mB[0], mA[1] - mB[1], mA[2] - mB[2]};
+    double n2 = (ab[0] * ab[0] + ab[1] * ab[1]) + ab[2] * ab[2];
+    double cB[3] = {c[0] - mB[0], c[1] - mB[1], c[2] - mB[2]};
+    double cA[3] = {c[0] - mA[0], c[1] - mA[1], c[2] - mA[2]};
+    double ta = ((cB[0] * ab[0] + cB[1] * ab[1]) + cB[2] * ab[2]) / n2;
+    double tb = ((cA[0] * -ab[0] + cA[1] * -ab[1]) + cA[2] * -ab[2]) / n2;
+    *tA = std::fmin(1.0, std::fmax(0.0, ta));
+    *tB = std::fmin(1.0, std::fmax(0.0, tb));
+}
+
+// squared Eq. 2 bands in FP32 for inner thresholds d (L - 1 values)
+static void bands(int L, const double* d, float* lo, float* hi) {
+    for (int l = 0; l < kMaxLevels; ++l) { lo[l] = 0.f; hi[l] = INFINITY; }
+    for (int l = 0; l < L; ++l) {
+        double a = (l == 0) ? 0.0 : d[l - 1];
+        lo[l] = (float)(a * a);
+        if (l + 1 < L) hi[l] = (float)(d[l] * d[l]);
+    }
+}
+
+// Extent table: Q_b = 2 ln(255 o_hi) * 1.001 with o_hi the upper end of the
+// opacity bucket b (FP32 exponent and 3 leading mantissa bits, from 2^-8).
+static void fill_qtable_host(float* q) {
+    for (uint32_t b = 0; b < 65; ++b) {
+        uint32_t u = (b + (119u << 3) + 1u) << 20;
+        float hi;
+        std::memcpy(&hi, &u, 4);
+        q[b] = (float)(2.0 * std::log(255.0 * (double)hi) * 1.001);
+    }
+}
+
+static DevCamera make_cam(const lodge_camera& c) {
+    DevCamera d{};
+    for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
+    for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.width = c.width; d.height = c.height;
+    d.znear = c.znear;
+    for (int i = 0; i < 3; ++i) d.chat[i] = (float)c.center[i];
+    for (int i = 0; i < 3; ++i)
+        d.tp[i] = (float)((double)c.t[i] + (((double)c.R[3 * i] * (double)d.chat[0] +
+                                             (double)c.R[3 * i + 1] * (double)d.chat[1]) +
+                                            (double)c.R[3 * i + 2] * (double)d.chat[2]));
+    for (int i = 0; i < 3; ++i) d.clo[i] = (float)(c.center[i] - (double)d.chat[i]);
+    d.tiles_x = (c.width + kTile - 1) / kTile;
+    d.tiles_y = (c.height + kTile - 1) / kTile;
+    return d;
+}
+
+static lodge_status check_cam(const lodge_camera& c) {
+    if (c.width <= 0 || c.height <= 0)
+        return fail(LODGE_E_INVALID, "camera size %dx%d must be positive", c.width, c.height);
+    if ((c.width + kTile - 1) / kTile > 65535 || (c.height + kTile - 1) / kTile > 65535)
+        return fail(LODGE_E_INVALID, "camera %dx%d exceeds 65535 tiles per side", c.width, c.height);
+    if ((int64_t)((c.width + kTile - 1) / kTile) * ((c.height + kTile - 1) / kTile) >= (1ll << 31))
+        return fail(LODGE_E_INVALID, "too many tiles");
+    return LODGE_OK;
+}
+
+static int bits_for(uint32_t v) {
+    int b = 0;
+    while (b < 32 && (v >> b)) ++b;
+    return std::max(b, 1);
+}
+
+static Scene* get_scene(lodge_ctx* ctx, int32_t id) {
+    if (id < 0 || id >= (int32_t)ctx->scenes.size()) return nullptr;
+    return ctx->scenes[id].get();
+}
+
+static lodge_status sync_small(lodge_ctx* ctx, cudaStream_t s) {
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_small, ctx->d_small, sizeof(uint32_t) * kSmWords,
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    uint32_t err = ctx->h_small[kSmErr];
+    if (err & kErrTimeout) return fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
+    if (err & kErrOverflow) return fail(LODGE_E_OVERFLOW, "device output capacity exceeded (status 0x%x)", err);
+    if (err & kErrBadIndex) return fail(LODGE_E_INVALID, "out-of-range index in an active list (status 0x%x)", err);
+    return LODGE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// selection
+// ---------------------------------------------------------------------------
+// Eq. 2 at centre c with inner thresholds d into ctx->ws.list; returns count.
+static lodge_status run_lod_select(lodge_ctx* ctx, Scene* sc, const double* c, const double* d,
+                                   cudaStream_t s, int64_t* n_out) {
+    Workspace& ws = ctx->ws;
+    float lo[kMaxLevels], hi[kMaxLevels];
+    bands(sc->dev.num_levels, d, lo, hi);
+    float c32[3] = {(float)c[0], (float)c[1], (float)c[2]};
+    int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
+    TRY(ensure(ctx, ws.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(sc->dev.n_total, 1), s));
+    TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
+    CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    launch_lod_select(sc->dev, c32, lo, hi, ws.list.as<uint32_t>(), ctx->d_small + kSmListCount,
+                      ws.status.as<uint32_t>(), ctx->d_small + kSmCtrSelect, ctx->d_small + kSmErr, s);
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_small(ctx, s));
+    *n_out = ctx->h_small[kSmListCount];
+    return LODGE_OK;
+}
+
+struct Active {
+    const uint32_t* list = nullptr;
+    int64_t n = 0;
+    int A = -1, B = -1;
+    double tA = 1.0, tB = 1.0;
+};
+
+static lodge_status select_active(lodge_ctx* ctx, Scene* sc, lodge_mode mode, const lodge_camera& cam,
+                                  cudaStream_t s, Active* act) {
+    *act = Active{};
+    if (mode == LODGE_FULL) {
+        act->n = sc->dev.level_off[1];
+        return LODGE_OK;
+    }
+    if (mode == LODGE_LOD) {
+        int64_t n;
+        TRY(run_lod_select(ctx, sc, cam.center, sc->d_inner.data(), s, &n));
+        act->list = ctx->ws.list.as<uint32_t>();
+        act->n = n;
+        return LODGE_OK;
+    }
+    if (mode != LODGE_CHUNK && mode != LODGE_CHUNK_BLEND)
+        return fail(LODGE_E_INVALID, "unknown render mode %d", (int)mode);
+    if (sc->chunks.empty()) return fail(LODGE_E_INVALID, "scene has no chunks");
+    chunk_pick(sc->centers, cam.center, &act->A, &act->B, &act->tA, &act->tB);
+    if (mode == LODGE_CHUNK || act->B < 0) {
+        act->list = sc->chunks[act->A].list;
+        act->n = sc->chunks[act->A].n;
+        if (mode == LODGE_CHUNK) { act->B = -1; act->tA = act->tB = 1.0; }
+        return LODGE_OK;
+    }
+    if (sc->ua != act->A || sc->ub != act->B) {
+        const Chunk& a = sc->chunks[act->A];
+        const Chunk& b = sc->chunks[act->B];
+        Workspace& ws = ctx->ws;
+        int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
+        TRY(ensure(ctx, sc->ulist, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
+        TRY(ensure(ctx, ws.marks, (size_t)((sc->dev.n_total + 63) / 64 * 64), s));
+        TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
+        CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
+        CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+        launch_chunk_union(a.list, a.n, b.list, b.n, sc->dev.n_total, ws.marks.as<uint8_t>(),
+                           sc->ulist.as<uint32_t>(), ctx->d_small + kSmListCount,
+                           ws.status.as<uint32_t>(), ctx->d_small + kSmCtrUnion,
+                           ctx->d_small + kSmErr, s);
+        CUDA_TRY(cudaGetLastError());
+        sc->ua = -2;
+        TRY(sync_small(ctx, s));
+        sc->un = ctx->h_small[kSmListCount];
+        sc->ua = act->A;
+        sc->ub = act->B;
+    }
+    act->list = sc->ulist.as<uint32_t>();
+    act->n = sc->un;
+    return LODGE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one frame
+// ---------------------------------------------------------------------------
+static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
+
+static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Active& act,
+                                 const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
+                                 lodge_frame_stats* st) {
+    Workspace& ws = ctx->ws;
+    TRY(check_cam(c));
+    DevCamera cam = make_cam(c);
+    const int64_t ntiles_img = (int64_t)cam.tiles_x * cam.tiles_y;
+    const int64_t na = act.n;
+    const size_t na1 = (size_t)std::max<int64_t>(na, 1);
+    if (na >= (1ll << 30)) return fail(LODGE_E_INVALID, "active set too large");
+
+    // ---- K3 projection
+    TRY(ensure(ctx, ws.rec_a, sizeof(float4) * na1, s));
+    TRY(ensure(ctx, ws.rec_b, sizeof(float4) * na1, s));
+    TRY(ensure(ctx, ws.rec_c, sizeof(float) * na1, s));
+    TRY(ensure(ctx, ws.rec_rect, sizeof(uint2) * na1, s));
+    TRY(ensure(ctx, ws.rec_gid, sizeof(uint32_t) * na1, s));
+    TRY(ensure(ctx, ws.dkey, sizeof(uint32_t) * na1, s));
+    TRY(ensure(ctx, ws.dval, sizeof(uint32_t) * na1, s));
+    int64_t ptiles = std::max<int64_t>((na + kProjThreads - 1) / kProjThreads, 1);
+    TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)ptiles, s));
+    CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)ptiles, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    ProjectOut po;
+    po.rec_a = ws.rec_a.as<float4>();
+    po.rec_b = ws.rec_b.as<float4>();
+    po.rec_c = ws.rec_c.as<float>();
+    po.rec_rect = ws.rec_rect.as<uint2>();
+    po.rec_gid = ws.rec_gid.as<uint32_t>();
+    po.depth_key = ws.dkey.as<uint32_t>();
+    po.depth_val = ws.dval.as<uint32_t>();
+    po.counts = ctx->d_small + kSmProj;
+    launch_project(dsc, cam, act.list, na, (float)act.tA, (float)act.tB, po,
+                   ws.status.as<uint32_t>(), ctx->d_small + kSmCtrProj, ctx->d_small + kSmErr, s);
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_small(ctx, s));
+    const int64_t n_vis = ctx->h_small[kSmProj];
+    uint64_t nk64;
+    std::memcpy(&nk64, ctx->h_small + kSmProj + 2, 8);
+    const int64_t n_keys = (int64_t)nk64;
+    if (n_keys >= (1ll << 30)) return fail(LODGE_E_OVERFLOW, "%lld tile keys exceed 2^30", (long long)n_keys);
+    const size_t nv1 = (size_t)std::max<int64_t>(n_vis, 1), nk1 = (size_t)std::max<int64_t>(n_keys, 1);
+
+    // ---- K5 depth sort of the visible records
+    TRY(ensure(ctx, ws.dkey2, sizeof(uint32_t) * nv1, s));
+    TRY(ensure(ctx, ws.dval2, sizeof(uint32_t) * nv1, s));
+    const int tbits = bits_for((uint32_t)(ntiles_img - 1));
+    TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_keys, tbits)), s));
+    int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
+                             ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, ctx->d_small + kSmErr, s);
+    DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
+    DBuf& rs = w1 ? ws.dval2 : ws.dval;
+
+    // ---- K4 emit (tile, record) in depth order
+    TRY(ensure(ctx, ws.tkey, sizeof(uint32_t) * nk1, s));
+    TRY(ensure(ctx, ws.tval, sizeof(uint32_t) * nk1, s));
+    TRY(ensure(ctx, ws.tkey2, sizeof(uint32_t) * nk1, s));
+    TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * nk1, s));
+    int64_t etiles = std::max<int64_t>((n_vis + kEmitThreads - 1) / kEmitThreads, 1);
+    TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
+    CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
+    launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), cam.tiles_x, ws.tkey.as<uint32_t>(),
+                ws.tval.as<uint32_t>(), n_keys, ws.status.as<uint32_t>(), ctx->d_small + kSmCtrEmit,
+                ctx->d_small + kSmErr, s);
+
+    // ---- K5 tile sort (stable: keeps depth order within a tile)
+    int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), ws.tkey2.as<uint32_t>(),
+                             ws.tval2.as<uint32_t>(), n_keys, tbits, ws.sort.p, ctx->d_small + kSmErr, s);
+    DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
+    DBuf& vs = w2 ? ws.tval2 : ws.tval;
+
+    // ---- K6 ranges, K7 blend
+    TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
+    CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
+    launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, s);
+    BlendOut bo{d_rgb, nullptr, nullptr};
+    if (save) {
+        const size_t npix = (size_t)c.width * c.height;
+        TRY(ensure(ctx, ws.T, sizeof(float) * npix, s));
+        TRY(ensure(ctx, ws.last, sizeof(uint32_t) * npix, s));
+        bo.T_final = ws.T.as<float>();
+        bo.last = ws.last.as<uint32_t>();
+    }
+    launch_blend(cam, ws.ranges.as<uint2>(), vs.as<uint32_t>(), n_keys, ws.rec_a.as<float4>(),
+                 ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_small(ctx, s));
+
+    if (st) {
+        st->n_active = na;
+        st->n_visible = n_vis;
+        st->n_keys = n_keys;
+        st->n_tiles = ntiles_img;
+        st->chunk_a = act.A;
+        st->chunk_b = act.B;
+        st->t_a = act.tA;
+        st->t_b = act.tB;
+    }
+    if (save) {
+        save->cam = cam;
+        save->n_vis = n_vis;
+        save->n_keys = n_keys;
+        take(save->rec_a, ws.rec_a);
+        take(save->rec_b, ws.rec_b);
+        take(save->rec_c, ws.rec_c);
+        take(save->rec_rect, ws.rec_rect);
+        take(save->rec_gid, ws.rec_gid);
+        take(save->zsorted, zs);
+        take(save->rsorted, rs);
+        take(save->tkey, ks);
+        take(save->tval, vs);
+        take(save->ranges, ws.ranges);
+        take(save->T, ws.T);
+        take(save->last, ws.last);
+    }
+    return LODGE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels of the host API
+// ---------------------------------------------------------------------------
+__global__ void iota_kernel(uint32_t* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint32_t)i;
+}
+
+__global__ void zrec_kernel(const uint32_t* zsorted, const uint32_t* rsorted, int64_t n, uint32_t* zrec) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (int64_t)rsorted[i] < n) zrec[rsorted[i]] = zsorted[i];
+}
+
+__global__ void debug_keys_kernel(const uint32_t* tkey, const uint32_t* tval, int64_t n,
+                                  int64_t n_rec, const uint32_t* zrec, const uint32_t* gid, uint64_t* keys,
+                                  uint32_t* gids) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t r = tval[i];
+    if ((int64_t)r >= n_rec) r = 0;
+    if (keys) keys[i] = ((uint64_t)tkey[i] << 32) | zrec[r];
+    if (gids) gids[i] = gid[r];
+}
+
+__global__ void debug_records_kernel(int64_t n, const float4* ra, const float4* rb, const float* rc,
+                                     const uint2* rect, const uint32_t* gid_in, const uint32_t* zrec,
+                                     uint32_t* gid, float* depth, int32_t* r4, float* mean2,
+                                     float* conic, float* opac, float* rgb) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 a = ra[i], b = rb[i];
+    if (gid) gid[i] = gid_in[i];
+    if (depth) depth[i] = __uint_as_float(zrec[i]);
+    if (r4) {
+        uint2 r = rect[i];
+        r4[4 * i + 0] = (int32_t)(r.x & 0xffffu);
+        r4[4 * i + 1] = (int32_t)(r.x >> 16);
+        r4[4 * i + 2] = (int32_t)(r.y & 0xffffu);
+        r4[4 * i + 3] = (int32_t)(r.y >> 16);
+    }
+    if (mean2) { mean2[2 * i] = a.x; mean2[2 * i + 1] = a.y; }
+    if (conic) {
+        const float s = 0.7213475204444817f;
+        float u00 = a.z, u01 = a.w, u11 = b.x;
+        conic[3 * i + 0] = u00 * u00 / s;
+        conic[3 * i + 1] = u00 * u01 / s;
+        conic[3 * i + 2] = (u01 * u01 + u11 * u11) / s;
+    }
+    if (opac) opac[i] = b.y;
+    if (rgb) { rgb[3 * i] = b.z; rgb[3 * i + 1] = b.w; rgb[3 * i + 2] = rc[i]; }
+}
+
+// FP32 device activation for the raw-parameter path.
+__global__ void activate_kernel(int64_t n, const float* ls, const float* q, const float* lg,
+                                float4* so, float4* qo) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s0 = expf(ls[3 * i]), s1 = expf(ls[3 * i + 1]), s2 = expf(ls[3 * i + 2]);
+    float o = 1.f / (1.f + expf(-lg[i]));
+    so[i] = make_float4(s0, s1, s2, o);
+    float w = q[4 * i], x = q[4 * i + 1], y = q[4 * i + 2], z = q[4 * i + 3];
+    float r = rsqrtf(w * w + x * x + y * y + z * z);
+    qo[i] = make_float4(w * r, x * r, y * r, z * r);
+}
+
+// N x 48 SH coefficients -> 12 planes of float4 with stride np
+__global__ void sh_planes_kernel(int64_t n, const float* sh, float4* planes, int64_t np) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4* src = reinterpret_cast<const float4*>(sh + 48 * i);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) planes[(size_t)j * np + i] = src[j];
+}
+
+__global__ void planes_kernel(int64_t n, const float* means, float* mx, float* my, float* mz) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    mx[i] = means[3 * i]; my[i] = means[3 * i + 1]; mz[i] = means[3 * i + 2];
+}
+
+}  // namespace lodge
+
+// ===========================================================================
+// extern "C"
+// ===========================================================================
+extern "C" {
+
+const char* lodge_last_error(void) { return lodge::g_err.c_str(); }
+
+lodge_status lodge_create(int device, size_t hbm_budget_bytes, lodge_ctx** out) {
+    if (!out) return fail(LODGE_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(LODGE_E_INVALID, "device %d not present (%d devices)", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+    std::unique_ptr<lodge_ctx> ctx(new lodge_ctx());
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    float q[65];
+    fill_qtable_host(q);
+    CUDA_TRY(upload_qtable(q));
+    TRY(dmalloc(ctx.get(), (void**)&ctx->d_small, sizeof(uint32_t) * kSmWords));
+    CUDA_TRY(cudaMemset(ctx->d_small, 0, sizeof(uint32_t) * kSmWords));
+    CUDA_TRY(cudaMallocHost((void**)&ctx->h_small, sizeof(uint32_t) * kSmWords));
+    *out = ctx.release();
+    return LODGE_OK;
+}
+
+lodge_status lodge_destroy(lodge_ctx* ctx) {
+    if (!ctx) return LODGE_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->saved) {
+        Saved& v = *kv.second;
+        for (DBuf* b : {&v.rec_a, &v.rec_b, &v.rec_c, &v.rec_rect, &v.rec_gid, &v.zsorted, &v.rsorted,
+                        &v.tkey, &v.tval, &v.ranges, &v.T, &v.last, &v.act_so, &v.act_q})
+            if (b->p) cudaFree(b->p);
+    }
+    for (auto& sp : ctx->scenes) {
+        if (!sp) continue;
+        if (sp->block) cudaFree(sp->block);
+        for (auto& ch : sp->chunks) if (ch.list) cudaFree(ch.list);
+        if (sp->ulist.p) cudaFree(sp->ulist.p);
+    }
+    Workspace& w = ctx->ws;
+    for (DBuf* b : {&w.list, &w.marks, &w.status, &w.rec_a, &w.rec_b, &w.rec_c, &w.rec_rect, &w.rec_gid,
+                    &w.dkey, &w.dval, &w.dkey2, &w.dval2, &w.tkey, &w.tval, &w.tkey2, &w.tval2,
+                    &w.ranges, &w.sort, &w.T, &w.last, &w.img, &w.act_so, &w.act_q, &w.mtmp})
+        if (b->p) cudaFree(b->p);
+    if (ctx->d_small) cudaFree(ctx->d_small);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    cudaDeviceSynchronize();
+    delete ctx;
+    return LODGE_OK;
+}
+
+lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int32_t* scene_id) {
+    if (!ctx || !desc || !scene_id) return fail(LODGE_E_INVALID, "NULL argument");
+    const int L = desc->num_levels;
+    if (L < 1 || L > kMaxLevels) return fail(LODGE_E_INVALID, "num_levels %d outside 1..%d", L, kMaxLevels);
+    if (desc->sh_degree < 0 || desc->sh_degree > 3) return fail(LODGE_E_INVALID, "sh_degree %d outside 0..3", desc->sh_degree);
+    if (!desc->levels) return fail(LODGE_E_INVALID, "levels is NULL");
+    if (L > 1 && !desc->d_thresholds) return fail(LODGE_E_INVALID, "d_thresholds is NULL");
+    for (int l = 0; l + 2 < L; ++l)
+        if (!(desc->d_thresholds[l] <= desc->d_thresholds[l + 1]))
+            return fail(LODGE_E_INVALID, "d_thresholds must be ascending");
+    if (desc->num_chunks < 0 || (desc->num_chunks > 0 && !desc->chunk_centers))
+        return fail(LODGE_E_INVALID, "bad chunk centres");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::unique_ptr<Scene> sc(new Scene());
+    DevScene& d = sc->dev;
+    d.num_levels = L;
+    d.sh_degree = desc->sh_degree;
+    d.level_off[0] = 0;
+    for (int l = 0; l < L; ++l) {
+        const lodge_level_desc& lv = desc->levels[l];
+        if (lv.n < 0) return fail(LODGE_E_INVALID, "level %d has negative size", l);
+        if (lv.n > 0 && (!lv.means || !lv.log_scales || !lv.quats || !lv.opacity_logits || !lv.sh))
+            return fail(LODGE_E_INVALID, "level %d has a NULL array", l);
+        d.level_off[l + 1] = d.level_off[l] + lv.n;
+        d.filter_var[l] = lv.filter_var;
+    }
+    for (int l = L; l < kMaxLevels; ++l) d.level_off[l + 1] = d.level_off[L];
+    const int64_t N = d.level_off[L];
+    if (N >= (1ll << 30)) return fail(LODGE_E_INVALID, "scene has %lld Gaussians, limit 2^30", (long long)N);
+    d.n_total = N;
+    const int64_t NP = std::max<int64_t>((N + 63) / 64 * 64, 64);
+    sc->n_pad = NP;
+    // one allocation: 3 mean planes, scale_op, quat, 12 SH planes
+    const size_t bytes = sizeof(float) * 3 * NP + sizeof(float4) * (2 + 12) * NP;
+    TRY(dmalloc(ctx, &sc->block, bytes));
+    sc->block_bytes = bytes;
+    float* base = static_cast<float*>(sc->block);
+    d.mx = base;
+    d.my = base + NP;
+    d.mz = base + 2 * NP;
+    float4* f4 = reinterpret_cast<float4*>(base + 3 * NP);
+    d.scale_op = f4;
+    d.quat = f4 + NP;
+    d.sh = f4 + 2 * NP;
+
+    // host staging, one plane at a time (pageable)
+    std::vector<float> plane((size_t)NP, 0.f);
+    std::vector<float4> plane4((size_t)NP, make_float4(0, 0, 0, 0));
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int l = 0; l < L; ++l) {
+            const lodge_level_desc& lv = desc->levels[l];
+            const int64_t o = d.level_off[l];
+            parallel_for(lv.n, [&](int64_t a, int64_t b) {
+                for (int64_t i = a; i < b; ++i) plane[o + i] = lv.means[3 * i + axis];
+            });
+        }
+        CUDA_TRY(cudaMemcpy(base + axis * NP, plane.data(), sizeof(float) * NP, cudaMemcpyHostToDevice));
+    }
+    // activation in FP64, rounded once: scale = exp, opacity = sigmoid, unit quaternion
+    for (int l = 0; l < L; ++l) {
+        const lodge_level_desc& lv = desc->levels[l];
+        const int64_t o = d.level_off[l];
+        parallel_for(lv.n, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; ++i) {
+                float s0 = (float)std::exp((double)lv.log_scales[3 * i]);
+                float s1 = (float)std::exp((double)lv.log_scales[3 * i + 1]);
+                float s2 = (float)std::exp((double)lv.log_scales[3 * i + 2]);
+                float op = (float)(1.0 / (1.0 + std::exp(-(double)lv.opacity_logits[i])));
+                plane4[o + i] = make_float4(s0, s1, s2, op);
+            }
+        });
+    }
+    CUDA_TRY(cudaMemcpy((void*)d.scale_op, plane4.data(), sizeof(float4) * NP, cudaMemcpyHostToDevice));
+    for (int l = 0; l < L; ++l) {
+        const lodge_level_desc& lv = desc->levels[l];
+        const int64_t o = d.level_off[l];
+        parallel_for(lv.n, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; ++i) {
+                double w = lv.quats[4 * i], x = lv.quats[4 * i + 1], y = lv.quats[4 * i + 2], z = lv.quats[4 * i + 3];
+                double nrm = std::sqrt(((w * w + x * x) + y * y) + z * z);
+                plane4[o + i] = make_float4((float)(w / nrm), (float)(x / nrm), (float)(y / nrm), (float)(z / nrm));
+            }
+        });
+    }
+    CUDA_TRY(cudaMemcpy((void*)d.quat, plane4.data(), sizeof(float4) * NP, cudaMemcpyHostToDevice));
+    for (int j = 0; j < 12; ++j) {
+        for (int l = 0; l < L; ++l) {
+            const lodge_level_desc& lv = desc->levels[l];
+            const int64_t o = d.level_off[l];
+            parallel_for(lv.n, [&](int64_t a, int64_t b) {
+                for (int64_t i = a; i < b; ++i) {
+                    const float* p = lv.sh + 48 * i + 4 * j;
+                    plane4[o + i] = make_float4(p[0], p[1], p[2], p[3]);
+                }
+            });
+        }
+        CUDA_TRY(cudaMemcpy((void*)(d.sh + (size_t)j * NP), plane4.data(), sizeof(float4) * NP,
+                            cudaMemcpyHostToDevice));
+    }
+    // thresholds and chunks
+    sc->d_inner.assign(desc->d_thresholds, desc->d_thresholds + std::max(L - 1, 0));
+    const int K = desc->num_chunks;
+    sc->centers.assign(desc->chunk_centers, desc->chunk_centers + 3 * K);
+    sc->radius.assign(K, 0.0);
+    for (int k = 0; k < K; ++k) {
+        double best = INFINITY;
+        for (int j = 0; j < K; ++j) {
+            if (j == k) continue;
+            double dd = std::sqrt(dist2(&sc->centers[3 * k], &sc->centers[3 * j]));
+            if (dd < best) best = dd;
+        }
+        sc->radius[k] = K > 1 ? best : 0.0;
+    }
+    ctx->scenes.emplace_back(std::move(sc));
+    Scene* S = ctx->scenes.back().get();
+    *scene_id = (int32_t)ctx->scenes.size() - 1;
+    // per-chunk active sets: Eq. 2 at m_k with thresholds d_l + r_k
+    cudaStream_t s = 0;
+    S->chunks.assign(K, Chunk{});
+    std::vector<double> dd(std::max(L - 1, 1));
+    for (int k = 0; k < K; ++k) {
+        for (int l = 0; l + 1 < L; ++l) dd[l] = S->d_inner[l] + S->radius[k];
+        int64_t n;
+        lodge_status st = run_lod_select(ctx, S, &S->centers[3 * k], dd.data(), s, &n);
+        if (st != LODGE_OK) return st;
+        void* p = nullptr;
+        TRY(dmalloc(ctx, &p, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1)));
+        if (n) CUDA_TRY(cudaMemcpy(p, ctx->ws.list.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice));
+        S->chunks[k].list = static_cast<uint32_t*>(p);
+        S->chunks[k].n = n;
+        S->chunk_bytes += sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1);
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    return LODGE_OK;
+}
+
+lodge_status lodge_unload_scene(lodge_ctx* ctx, int32_t scene_id) {
+    if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    dfree(ctx, sc->block, sc->block_bytes);
+    for (auto& ch : sc->chunks) dfree(ctx, ch.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(ch.n, 1));
+    release(ctx, sc->ulist, 0);
+    CUDA_TRY(cudaDeviceSynchronize());
+    ctx->scenes[scene_id].reset();
+    return LODGE_OK;
+}
+
+lodge_status lodge_upload_chunks(lodge_ctx* ctx, int32_t scene_id, const int32_t* chunk_ids,
+                                 int32_t n, int blocking) {
+    (void)blocking;
+    if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    if (n > 0 && !chunk_ids) return fail(LODGE_E_INVALID, "chunk_ids is NULL");
+    for (int i = 0; i < n; ++i)
+        if (chunk_ids[i] < 0 || chunk_ids[i] >= (int32_t)sc->chunks.size())
+            return fail(LODGE_E_INVALID, "chunk id %d out of range", chunk_ids[i]);
+    return LODGE_OK;
+}
+
+lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
+                              int32_t n_cams, lodge_selection* out, uint32_t* d_gids,
+                              int64_t gids_capacity, void* stream) {
+    if (!ctx || !cams || !out || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < n_cams; ++i) {
+        Active act;
+        TRY(select_active(ctx, sc, mode, cams[i], s, &act));
+        out[i].chunk_a = act.A;
+        out[i].chunk_b = act.B;
+        out[i].t_a = act.tA;
+        out[i].t_b = act.tB;
+        out[i].n_active = act.n;
+        if (d_gids && n_cams == 1) {
+            if (act.n > gids_capacity) return fail(LODGE_E_OVERFLOW, "active set %lld > capacity %lld", (long long)act.n, (long long)gids_capacity);
+            if (act.list) {
+                if (act.n) CUDA_TRY(cudaMemcpyAsync(d_gids, act.list, sizeof(uint32_t) * act.n, cudaMemcpyDeviceToDevice, s));
+            } else if (act.n) {
+                iota_kernel<<<(unsigned)((act.n + 255) / 256), 256, 0, s>>>(d_gids, act.n);
+                CUDA_TRY(cudaGetLastError());
+            }
+            CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    }
+    return LODGE_OK;
+}
+
+lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
+                          int32_t n_cams, float* d_rgb, void* stream, int32_t save_for_backward,
+                          int64_t* handle_out, lodge_frame_stats* stats) {
+    if (!ctx || !cams || !d_rgb || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
+    if (save_for_backward && (n_cams != 1 || !handle_out))
+        return fail(LODGE_E_INVALID, "save_for_backward needs n_cams == 1 and handle_out");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t off = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        Active act;
+        TRY(select_active(ctx, sc, mode, cams[i], s, &act));
+        std::unique_ptr<Saved> sv;
+        if (save_for_backward) sv.reset(new Saved());
+        TRY(render_frame(ctx, sc->dev, act, cams[i], d_rgb + off, s, sv.get(), stats ? stats + i : nullptr));
+        off += (size_t)cams[i].width * cams[i].height * 3;
+        if (sv) {
+            int64_t h = ctx->next_handle++;
+            ctx->saved[h] = std::move(sv);
+            *handle_out = h;
+        }
+    }
+    return LODGE_OK;
+}
+
+lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
+                               int32_t n_cams, float* h_rgb, void* stream, lodge_frame_stats* stats) {
+    if (!ctx || !cams || !h_rgb || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t total = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        TRY(check_cam(cams[i]));
+        total += (size_t)cams[i].width * cams[i].height * 3;
+    }
+    TRY(ensure(ctx, ctx->ws.img, sizeof(float) * std::max<size_t>(total, 1), s));
+    TRY(lodge_render(ctx, scene_id, mode, cams, n_cams, ctx->ws.img.as<float>(), stream, 0, nullptr, stats));
+    if (total) CUDA_TRY(cudaMemcpyAsync(h_rgb, ctx->ws.img.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return LODGE_OK;
+}
+
+lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means, const float* d_log_scales,
+                                 const float* d_quats, const float* d_opacity_logits, const float* d_sh,
+                                 int32_t sh_degree, float filter_var, const lodge_camera* cam, float* d_rgb,
+                                 void* stream, int32_t save_for_backward, int64_t* handle_out,
+                                 lodge_frame_stats* stats) {
+    if (!ctx || !cam || !d_rgb || n < 0) return fail(LODGE_E_INVALID, "bad argument");
+    if (n >= (1ll << 30)) return fail(LODGE_E_INVALID, "too many Gaussians");
+    if (n > 0 && (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh))
+        return fail(LODGE_E_INVALID, "NULL parameter array");
+    if (sh_degree < 0 || sh_degree > 3) return fail(LODGE_E_INVALID, "sh_degree outside 0..3");
+    if ((uintptr_t)d_sh % 16 != 0)
+        return fail(LODGE_E_INVALID, "d_sh must be 16-byte aligned");
+    if (save_for_backward && !handle_out) return fail(LODGE_E_INVALID, "handle_out is NULL");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace& ws = ctx->ws;
+    const size_t n1 = (size_t)std::max<int64_t>(n, 1);
+    const int64_t np = (n + 63) / 64 * 64;
+    TRY(ensure(ctx, ws.act_so, sizeof(float4) * n1, s));
+    TRY(ensure(ctx, ws.act_q, sizeof(float4) * n1, s));
+    TRY(ensure(ctx, ws.mtmp, sizeof(float) * 3 * (size_t)std::max<int64_t>(np, 64) + sizeof(float4) * 12 * (size_t)std::max<int64_t>(np, 64), s));
+    float* mp = ws.mtmp.as<float>();
+    const int64_t NP = std::max<int64_t>(np, 64);
+    float4* shp = reinterpret_cast<float4*>(mp + 3 * NP);
+    if (n) {
+        unsigned nb = (unsigned)((n + 255) / 256);
+        activate_kernel<<<nb, 256, 0, s>>>(n, d_log_scales, d_quats, d_opacity_logits, ws.act_so.as<float4>(), ws.act_q.as<float4>());
+        planes_kernel<<<nb, 256, 0, s>>>(n, d_means, mp, mp + NP, mp + 2 * NP);
+        sh_planes_kernel<<<nb, 256, 0, s>>>(n, d_sh, shp, NP);
+        CUDA_TRY(cudaGetLastError());
+    }
+    DevScene d;
+    d.n_total = n;
+    d.num_levels = 1;
+    d.sh_degree = sh_degree;
+    d.level_off[0] = 0;
+    for (int l = 1; l <= kMaxLevels; ++l) d.level_off[l] = n;
+    d.filter_var[0] = filter_var;
+    d.mx = mp; d.my = mp + NP; d.mz = mp + 2 * NP;
+    d.scale_op = ws.act_so.as<float4>();
+    d.quat = ws.act_q.as<float4>();
+    d.sh = shp;
+    Active act;
+    act.n = n;
+    std::unique_ptr<Saved> sv;
+    if (save_for_backward) sv.reset(new Saved());
+    // the projection kernel strides SH planes by the padded count of the scene
+    TRY(render_frame(ctx, d, act, *cam, d_rgb, s, sv.get(), stats));
+    if (sv) {
+        sv->params = true;
+        sv->n = n;
+        sv->means = d_means; sv->log_scales = d_log_scales; sv->quats = d_quats;
+        sv->logits = d_opacity_logits; sv->sh = d_sh;
+        sv->sh_degree = sh_degree;
+        sv->filter_var = filter_var;
+        take(sv->act_so, ws.act_so);
+        take(sv->act_q, ws.act_q);
+        int64_t h = ctx->next_handle++;
+        ctx->saved[h] = std::move(sv);
+        *handle_out = h;
+    }
+    return LODGE_OK;
+}
+
+lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* d_dL_drgb, float* d_g_means,
+                                   float* d_g_log_scales, float* d_g_quats, float* d_g_opacity_logits,
+                                   float* d_g_sh, void* stream) {
+    (void)d_dL_drgb; (void)d_g_means; (void)d_g_log_scales; (void)d_g_quats; (void)d_g_opacity_logits;
+    (void)d_g_sh; (void)stream;
+    if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
+    auto it = ctx->saved.find(handle);
+    if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
+    return fail(LODGE_E_INVALID, "backward pass not available in this build");
+}
+
+lodge_status lodge_release(lodge_ctx* ctx, int64_t handle) {
+    if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
+    auto it = ctx->saved.find(handle);
+    if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    Saved& v = *it->second;
+    for (DBuf* b : {&v.rec_a, &v.rec_b, &v.rec_c, &v.rec_rect, &v.rec_gid, &v.zsorted, &v.rsorted, &v.tkey,
+                    &v.tval, &v.ranges, &v.T, &v.last, &v.act_so, &v.act_q})
+        release(ctx, *b, 0);
+    ctx->saved.erase(it);
+    return LODGE_OK;
+}
+
+lodge_status lodge_debug_keys(lodge_ctx* ctx, int64_t handle, uint64_t* d_keys, uint32_t* d_gids, int64_t cap,
+                              int64_t* n_keys, void* stream) {
+    if (!ctx || !n_keys) return fail(LODGE_E_INVALID, "bad argument");
+    auto it = ctx->saved.find(handle);
+    if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    Saved& v = *it->second;
+    *n_keys = v.n_keys;
+    if (v.n_keys > cap) return fail(LODGE_E_OVERFLOW, "%lld keys > capacity %lld", (long long)v.n_keys, (long long)cap);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DBuf zrec;
+    TRY(ensure(ctx, zrec, sizeof(uint32_t) * (size_t)std::max<int64_t>(v.n_vis, 1), s));
+    if (v.n_vis) zrec_kernel<<<(unsigned)((v.n_vis + 255) / 256), 256, 0, s>>>(v.zsorted.as<uint32_t>(), v.rsorted.as<uint32_t>(), v.n_vis, zrec.as<uint32_t>());
+    if (v.n_keys) debug_keys_kernel<<<(unsigned)((v.n_keys + 255) / 256), 256, 0, s>>>(v.tkey.as<uint32_t>(), v.tval.as<uint32_t>(), v.n_keys, std::max<int64_t>(v.n_vis, 1), zrec.as<uint32_t>(), v.rec_gid.as<uint32_t>(), d_keys, d_gids);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
+    release(ctx, zrec, s);
+    return LODGE_OK;
+}
+
+lodge_status lodge_debug_records(lodge_ctx* ctx, int64_t handle, uint32_t* d_gid, float* d_depth, int32_t* d_rect,
+                                 float* d_mean2, float* d_conic, float* d_opacity, float* d_rgb, int64_t cap,
+                                 int64_t* n_visible, void* stream) {
+    if (!ctx || !n_visible) return fail(LODGE_E_INVALID, "bad argument");
+    auto it = ctx->saved.find(handle);
+    if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    Saved& v = *it->second;
+    *n_visible = v.n_vis;
+    if (v.n_vis > cap) return fail(LODGE_E_OVERFLOW, "%lld records > capacity %lld", (long long)v.n_vis, (long long)cap);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DBuf zrec;
+    TRY(ensure(ctx, zrec, sizeof(uint32_t) * (size_t)std::max<int64_t>(v.n_vis, 1), s));
+    if (v.n_vis) {
+        unsigned nb = (unsigned)((v.n_vis + 255) / 256);
+        zrec_kernel<<<nb, 256, 0, s>>>(v.zsorted.as<uint32_t>(), v.rsorted.as<uint32_t>(), v.n_vis, zrec.as<uint32_t>());
+        debug_records_kernel<<<nb, 256, 0, s>>>(v.n_vis, v.rec_a.as<float4>(), v.rec_b.as<float4>(), v.rec_c.as<float>(),
+                                               v.rec_rect.as<uint2>(), v.rec_gid.as<uint32_t>(), zrec.as<uint32_t>(),
+                                               d_gid, d_depth, d_rect, d_mean2, d_conic, d_opacity, d_rgb);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
+    release(ctx, zrec, s);
+    return LODGE_OK;
+}
+
+lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals, int64_t n, int32_t key_bits,
+                              void* stream) {
+    if (!ctx || n < 0 || key_bits < 0 || key_bits > 32) return fail(LODGE_E_INVALID, "bad argument");
+    if (n >= (1ll << 30)) return fail(LODGE_E_INVALID, "n must be below 2^30");
+    if (n > 0 && (!d_keys || !d_vals)) return fail(LODGE_E_INVALID, "NULL key or value array");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace& ws = ctx->ws;
+    const size_t n1 = (size_t)std::max<int64_t>(n, 1);
+    TRY(ensure(ctx, ws.tkey2, sizeof(uint32_t) * n1, s));
+    TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * n1, s));
+    TRY(ensure(ctx, ws.sort, sort_scratch_bytes(n, key_bits), s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    int w = launch_onesweep(d_keys, d_vals, ws.tkey2.as<uint32_t>(), ws.tval2.as<uint32_t>(), n, key_bits,
+                            ws.sort.p, ctx->d_small + kSmErr, s);
+    if (w) {
+        CUDA_TRY(cudaMemcpyAsync(d_keys, ws.tkey2.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(d_vals, ws.tval2.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return sync_small(ctx, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (fixed here, derived in the design notes):
+  * selected sets, chunk choices, culling, tile rects, sorted tile keys:
+    bit-exact;
+  * pixels: on clamp(rgb, 0, 1), max-abs <= 2e-4 per channel over pixels the
+    oracle does not flag as knife edges (an FP32/FP64 difference can flip the
+    1/255 skip or the T < 1e-4 stop there), mean-abs <= 1e-5 over all pixels,
+    and at most 0.1% of pixels flagged.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2505_23158_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MAX_ABS = 2e-4
+MEAN_ABS = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2505_23158_gb300 import build
+    build.build()
+    from paper_2505_23158_gb300.api import Lodge
+    c = Lodge(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def plain_loaded(ctx):
+    scene, cams = synth.workload_plain(0)
+    return scene, cams, O.OracleScene(scene), ctx.load_scene(scene)
+
+
+def compare_images(gpu, ref, knife, tag=""):
+    g = np.clip(gpu.astype(np.float64), 0, 1)
+    r = np.clip(ref, 0, 1)
+    d = np.abs(g - r)
+    ok = ~knife
+    worst = d[ok].max() if ok.any() else 0.0
+    assert worst <= MAX_ABS, f"{tag} max-abs {worst:.3g} at {np.unravel_index(np.argmax(np.where(ok[..., None], d, 0)), d.shape)}"
+    assert d.mean() <= MEAN_ABS, f"{tag} mean-abs {d.mean():.3g}"
+    assert knife.sum() <= max(3, 1e-2 * knife.size), f"{tag} knife-edge pixels {knife.sum()}"
+
+
+def oracle_keys_u64(osc, cam, gids, mults=None):
+    k, g = O.keys(osc, cam, gids, mults)
+    return k, g
+
+
+# ---------------------------------------------------------------------------
+# plain single-level scene, FULL mode
+# ---------------------------------------------------------------------------
+def test_plain_keys_bit_exact(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    img, st, h = ctx.render(sid, FULL, cams[0], save=True)
+    try:
+        keys, gids = ctx.debug_keys(h)
+        k_ref, g_ref = oracle_keys_u64(osc, cams[0], np.arange(osc.n_total))
+        assert st["n_keys"] == k_ref.size
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref)
+        assert np.array_equal(gids.cpu().numpy().astype(np.int64), g_ref)
+    finally:
+        ctx.release(h)
+
+
+def test_plain_records(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    _, st, h = ctx.render(sid, FULL, cams[0], save=True)
+    try:
+        r = {k: v.cpu().numpy() for k, v in ctx.debug_records(h).items()}
+    finally:
+        ctx.release(h)
+    pr = O.project(osc, cams[0], np.arange(osc.n_total))
+    vis = np.flatnonzero(pr["visible"])
+    assert np.array_equal(r["gid"].astype(np.int64), vis)
+    assert np.array_equal(r["depth"].view(np.uint32), pr["z"][vis].view(np.uint32))
+    assert np.array_equal(r["rect"], pr["rect"][vis])
+    assert np.abs(r["mean2"] - pr["mean2"][vis]).max() < 2e-3
+    assert np.abs(r["opacity"] - pr["opacity"][vis]).max() < 1e-6
+    assert np.abs(r["rgb"] - pr["rgb"][vis]).max() < 2e-5
+    rel = np.abs(r["conic"] - pr["conic"][vis]) / (np.abs(pr["conic"][vis]).max(axis=1, keepdims=True))
+    assert rel.max() < 1e-4
+
+
+def test_plain_image(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    img, st = ctx.render(sid, FULL, cams[0])
+    ref = O.render(osc, cams[0], np.arange(osc.n_total))
+    compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], "plain")
+    assert st["n_visible"] == ref["n_visible"] and st["n_keys"] == ref["n_keys"]
+
+
+@pytest.mark.parametrize("wh", [(100, 70), (17, 33), (1, 1), (16, 16), (257, 129)])
+def test_ragged_image_sizes(ctx, plain_loaded, wh):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    cam = synth.plain_camera(*wh)
+    img, st, h = ctx.render(sid, FULL, cam, save=True)
+    try:
+        keys, gids = ctx.debug_keys(h)
+    finally:
+        ctx.release(h)
+    k_ref, g_ref = oracle_keys_u64(osc, cam, np.arange(osc.n_total))
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref)
+    ref = O.render(osc, cam, np.arange(osc.n_total))
+    compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"{wh}")
+
+
+def test_nothing_visible(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    cam = synth.look_at((0, 0, -3.0), (0, 0, -1.0), (0, -1, 0), 64, 48, 60.0)  # facing away
+    img, st = ctx.render(sid, FULL, cam)
+    assert st["n_visible"] == 0 and st["n_keys"] == 0
+    assert float(img.abs().max()) == 0.0
+
+
+def test_render_host_matches_device(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    img, _ = ctx.render(sid, FULL, cams[0])
+    out = np.empty((cams[0].height, cams[0].width, 3), np.float32)
+    ctx.render_host(sid, FULL, [cams[0]], out)
+    assert np.array_equal(out, img.cpu().numpy())
+
+
+def test_repeatable(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    a, _ = ctx.render(sid, FULL, cams[0])
+    a = a.clone()
+    b, _ = ctx.render(sid, FULL, cams[0])
+    assert bool((a == b).all())
+
+
+# ---------------------------------------------------------------------------
+# onesweep radix sort
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,bits", [(0, 32), (1, 32), (1000, 8), (3840, 32), (3841, 13),
+                                    (100_000, 32), (1_000_003, 21), (2_000_000, 32)])
+def test_sort_pairs_stable(ctx, torch_cuda, n, bits):
+    torch = torch_cuda
+    rng = np.random.default_rng(n + bits)
+    hi = (1 << bits) if bits < 32 else (1 << 32)
+    keys = rng.integers(0, hi, size=n, dtype=np.uint64).astype(np.uint32)
+    if n > 10:
+        keys[: n // 3] = keys[0]  # many equal keys: stability matters
+        rng.shuffle(keys)
+    vals = np.arange(n, dtype=np.uint32)
+    kt = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    vt = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    ctx.sort_pairs(kt, vt, bits)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), vals[order])
+
+
+def test_sort_pairs_partial_bits(ctx, torch_cuda):
+    """Sorting on the low 13 bits leaves the order of keys that agree on them
+    untouched (stable), whatever the high bits hold."""
+    torch = torch_cuda
+    rng = np.random.default_rng(1)
+    keys = rng.integers(0, 1 << 32, size=50_000, dtype=np.uint64).astype(np.uint32)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    kt = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    vt = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    ctx.sort_pairs(kt, vt, 13)
+    order = np.argsort(keys & 0x1FFF, kind="stable")
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), vals[order])
+
+
+# ---------------------------------------------------------------------------
+# outdoor LOD scene: selection, chunks, blending
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def outdoor(ctx):
+    scene, cams = synth.workload_outdoor(seed=0, n_poses=6, scale=0.01, width=320, height_px=180)
+    osc = O.OracleScene(scene)
+    sid = ctx.load_scene(scene)
+    return scene, cams, osc, sid
+
+
+def _flags_from_oracle(osc, info):
+    a = O.chunk_select(osc, info["A"])
+    b = O.chunk_select(osc, info["B"])
+    return a, b
+
+
+@pytest.mark.parametrize("mode_name", ["LOD", "CHUNK", "CHUNK_BLEND"])
+def test_outdoor_selection_bit_exact(ctx, outdoor, mode_name):
+    from paper_2505_23158_gb300 import api
+    mode = getattr(api, mode_name)
+    scene, cams, osc, sid = outdoor
+    for cam in cams:
+        sel, gids = ctx.select(sid, mode, cam, want_gids=True)
+        g_ref, m_ref, info = O.active_set(osc, mode, cam)
+        raw = gids.cpu().numpy().view(np.uint32)
+        assert np.array_equal((raw & 0x3FFFFFFF).astype(np.int64), g_ref)
+        if mode_name == "LOD":
+            assert sel["chunk_a"] == -1
+            assert info["n_disagree"] <= 5
+        else:
+            assert sel["chunk_a"] == info["A"]
+            if mode_name == "CHUNK_BLEND" and info["B"] >= 0:
+                assert sel["chunk_b"] == info["B"]
+                assert sel["t_a"] == info["tA"] and sel["t_b"] == info["tB"]
+                a, b = _flags_from_oracle(osc, info)
+                assert np.array_equal((raw >> 31) & 1, np.isin(g_ref, a).astype(np.uint32))
+                assert np.array_equal((raw >> 30) & 1, np.isin(g_ref, b).astype(np.uint32))
+
+
+@pytest.mark.parametrize("mode_name", ["FULL", "LOD", "CHUNK", "CHUNK_BLEND"])
+def test_outdoor_render_parity(ctx, outdoor, mode_name):
+    from paper_2505_23158_gb300 import api
+    mode = getattr(api, mode_name)
+    scene, cams, osc, sid = outdoor
+    for i in (0, 3, 5):
+        cam = cams[i]
+        img, st, h = ctx.render(sid, mode, cam, save=True)
+        try:
+            keys, kg = ctx.debug_keys(h)
+        finally:
+            ctx.release(h)
+        g_ref, m_ref, info = O.active_set(osc, mode, cam)
+        k_ref, kg_ref = oracle_keys_u64(osc, cam, g_ref, m_ref)
+        assert st["n_active"] == g_ref.size
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref), f"pose {i}"
+        assert np.array_equal(kg.cpu().numpy().astype(np.int64), kg_ref)
+        ref = O.render(osc, cam, g_ref, m_ref)
+        compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"{mode_name} pose {i}")
+
+
+def test_outdoor_multi_camera_batch(ctx, outdoor, torch_cuda):
+    """Several cameras in one call equal one call per camera."""
+    from paper_2505_23158_gb300.api import CHUNK_BLEND
+    scene, cams, osc, sid = outdoor
+    imgs, stats = ctx.render(sid, CHUNK_BLEND, cams[:3])
+    for c, im in zip(cams[:3], imgs):
+        one, _ = ctx.render(sid, CHUNK_BLEND, c)
+        assert bool((one == im).all())
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+def test_invalid_arguments(ctx, plain_loaded):
+    from paper_2505_23158_gb300.api import FULL, LodgeError
+    scene, cams, osc, sid = plain_loaded
+    with pytest.raises(LodgeError) as e:
+        ctx.render(12345, FULL, cams[0])
+    assert e.value.status == 1
+    with pytest.raises(LodgeError):
+        ctx.render(sid, 17, cams[0])
+    bad = synth.plain_camera(0, 10)
+    with pytest.raises(LodgeError):
+        ctx.render(sid, FULL, bad)
+
+
+def test_hbm_budget_enforced(torch_cuda):
+    """A context whose budget cannot hold the scene refuses to load it
+    (host-side failure, the device is untouched)."""
+    from paper_2505_23158_gb300.api import Lodge, LodgeError
+    scene, _ = synth.workload_plain(0)
+    with Lodge(0, hbm_budget_bytes=64 * 1024) as c:
+        with pytest.raises(LodgeError) as e:
+            c.load_scene(scene)
+        assert e.value.status == 6
