@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Frame-rate benchmark of the LODGE render path on one node.
+
+Workload: the outdoor LOD scene (16M / 4M / 1M / 250k Gaussians over a 1 km x
+1 km heightfield, 16 x 16 chunk grid, SH degree 3, fp32 attributes) and a
+300-pose street-level trajectory at 1920 x 1080.  A step renders
+--poses-per-step consecutive poses of the trajectory in LOD+chunk mode with
+opacity blending (the paper's method); value = frames/s over all ranks.  The
+same poses are also rendered at full detail (every level-0 Gaussian) on the
+same GPU for the speedup.  Inputs are resident in HBM before timing (5.0 GB
+scene, larger than L2, no flush between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lodge|reference]
+
+Under torchrun (N > 1) every rank renders its own trajectory (weak scaling,
+no data-path collective); the barrier and a max over ranks bracket the timed
+region.  --impl reference times the CPU oracle on the same workload (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s, LOD+chunk vs full-detail 3DGS (same GPU); p50/p99 serve latency"
+UNIT = "frames/s"
+
+# stages of lodge_profile, in order
+STAGES = ["select", "union", "project", "depth_sort", "emit", "tile_sort", "ranges", "blend"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lodge", "reference"], default="lodge")
+    ap.add_argument("--scale", type=float, default=1.0, help="scene size factor (1.0 = full)")
+    ap.add_argument("--n-poses", type=int, default=300)
+    ap.add_argument("--poses-per-step", type=int, default=30)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--full-steps", type=int, default=None)
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def stage_bytes(stage: str, prof: dict) -> float:
+    """Algorithmic bytes of one stage summed over the profiled frames."""
+    a, v, k = prof["active"], prof["visible"], prof["keys"]
+    if stage == "project":
+        # list entry + means per active Gaussian; scale/opacity, quaternion and
+        # 48 SH coefficients per visible Gaussian; 56 B of records written
+        return a * (4 + 12) + v * (16 + 16 + 192 + 56)
+    if stage == "depth_sort":
+        return v * (4 + 4 * 16)          # histogram read + 4 passes of read/write key+value
+    if stage == "emit":
+        return v * (4 + 8) + k * 8
+    if stage == "tile_sort":
+        return k * (4 + 2 * 16)          # 13-bit tile ids: histogram + 2 passes
+    if stage == "ranges":
+        return k * 4
+    return 0.0
+
+
+def run_lodge(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_23158_gb300 import build, synth
+    from paper_2505_23158_gb300.api import CHUNK_BLEND, FULL, Lodge
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.time()
+    scene, cams = synth.workload_outdoor(seed=args.seed, n_poses=args.n_poses, scale=args.scale,
+                                         width=args.width, height_px=args.height)
+    if world > 1:
+        # weak scaling: every rank walks its own seeded trajectory of the same scene
+        cams = synth.outdoor_trajectory(scene, seed=args.seed + 1000 * rank, n_poses=args.n_poses,
+                                        width=args.width, height_px=args.height)
+    t_gen = time.time() - t0
+    ctx = Lodge(local_rank)
+    t0 = time.time()
+    sid = ctx.load_scene(scene)
+    t_load = time.time() - t0
+    n_total = scene.n_total
+    P = args.poses_per_step
+    npix = args.width * args.height
+    out = torch.empty(npix * 3, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def frames(step):
+        return [cams[(step * P + j) % len(cams)] for j in range(P)]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(mode, steps, per_frame_events=True):
+        evs = []
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = e0
+        for s in range(steps):
+            for cam in frames(s):
+                ctx.render(sid, mode, cam, out=out)
+                if per_frame_events:
+                    e = torch.cuda.Event(enable_timing=True)
+                    e.record(stream)
+                    evs.append((last, e))
+                    last = e
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t = e0.elapsed_time(e1) / 1e3
+        lat = [a.elapsed_time(b) for a, b in evs]
+        return t, lat
+
+    # warm-up (also grows every scratch buffer to its steady size)
+    for s in range(args.warmup):
+        for cam in frames(s):
+            ctx.render(sid, CHUNK_BLEND, cam, out=out)
+    for cam in frames(0)[:2]:
+        ctx.render(sid, FULL, cam, out=out)
+    torch.cuda.synchronize()
+
+    # ---- timed: LOD + chunk + opacity blending
+    clk = ClockSampler(local_rank)
+    ctx.profile_enable(True)
+    clk.start()
+    t_blend, lat = timed(CHUNK_BLEND, args.steps)
+    clocks = clk.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    t_blend = max_over_ranks(t_blend)
+    n_frames = args.steps * P
+    value = n_frames * world / t_blend
+
+    # ---- full detail on the same poses
+    fsteps = args.full_steps if args.full_steps is not None else max(1, args.steps // 2)
+    ctx.profile_enable(True)
+    t_full, lat_full = timed(FULL, fsteps)
+    prof_full = ctx.profile_read()
+    ctx.profile_enable(False)
+    t_full = max_over_ranks(t_full)
+    full_fps = fsteps * P * world / t_full
+
+    # ---- end to end through the host-buffer entry point (camera H2D, image D2H)
+    host = torch.empty(npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        for cam in frames(s):
+            ctx.render_host(sid, CHUNK_BLEND, [cam], host)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    e2e_fps = e2e_steps * P * world / t_e2e
+
+    # ---- roofline of the dominant kernel stage
+    pk, pk_kind = peaks()
+    ms = prof["ms"]
+    dom = max(ms, key=lambda k: ms[k])
+    launches = sum(prof["launches"].values())
+    roof = None
+    if dom == "blend":
+        # ALU-bound: bound by the FP32 pipes; report against the SM count x
+        # 128 lanes x 2 flops x max clock.  Evaluated pairs are not counted in
+        # this build, so report the pipe-peak and leave achieved to the
+        # counters (see profiles/).
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": None, "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": "blend",
+                "peak_source": f"{pk_kind}: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
+    else:
+        by = stage_bytes(dom, prof)
+        ach = by / (ms[dom] / 1e3) / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "kernel": dom,
+                "peak_source": f"{pk_kind} hbm_gbs"}
+    stages = {k: round(v / max(prof["frames"], 1), 4) for k, v in ms.items()}
+    stages_full = {k: round(v / max(prof_full["frames"], 1), 4) for k, v in prof_full["ms"].items()}
+    stage_gbs = {}
+    for k in ("project", "depth_sort", "emit", "tile_sort", "ranges"):
+        if ms[k] > 0:
+            stage_gbs[k] = round(stage_bytes(k, prof) / (ms[k] / 1e3) / 1e9, 1)
+
+    res = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_blend / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"outdoor LOD scene {n_total} Gaussians "
+                               f"({', '.join(str(l.n) for l in scene.levels)}), 16x16 chunks, "
+                               f"{len(cams)}-pose trajectory, {args.width}x{args.height}, "
+                               "CHUNK_BLEND (LOD + chunks + opacity blending)",
+                   "poses_per_step": P, "scale": args.scale,
+                   "l2": "inputs larger than L2 (resident scene), consecutive poses, no flush"},
+        "full_detail_fps": round(full_fps, 2),
+        "speedup_vs_full": round(value / full_fps, 3),
+        "mpix_per_s": round(value * npix / 1e6, 1),
+        "frame_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
+                             "p99": round(float(np.percentile(lat, 99)), 4),
+                             "full_p50": round(float(np.percentile(lat_full, 50)), 4)},
+        "serve_latency": None,
+        "per_frame": {"active": prof["active"] // max(prof["frames"], 1),
+                      "visible": prof["visible"] // max(prof["frames"], 1),
+                      "keys": prof["keys"] // max(prof["frames"], 1),
+                      "full_active": prof_full["active"] // max(prof_full["frames"], 1),
+                      "full_visible": prof_full["visible"] // max(prof_full["frames"], 1),
+                      "full_keys": prof_full["keys"] // max(prof_full["frames"], 1)},
+        "stage_ms_per_frame": stages, "stage_ms_per_frame_full": stages_full,
+        "stage_gbs": stage_gbs,
+        "e2e": {"value": round(e2e_fps, 2), "unit": UNIT, "h2d_bytes_per_step": 104 * P,
+                "d2h_bytes_per_step": 4 * 3 * npix * P},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "setup_s": {"generate": round(t_gen, 1), "load_scene": round(t_load, 1)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args, scene, cams)
+    ctx.close()
+    return res
+
+
+def cpu_baseline(args, scene, cams, budget_s=None, max_frames=None):
+    """The oracle timed on this host's cores on a bounded sample: whole
+    CHUNK_BLEND frames of the same trajectory until the time budget is
+    spent (at least one)."""
+    import oracle as O
+    budget_s = args.cpu_budget_s if budget_s is None else budget_s
+    osc = O.OracleScene(scene)
+    ncores = os.cpu_count()
+    done, spent, idx = 0, 0.0, 0
+    while (done == 0 or spent < budget_s) and (max_frames is None or done < max_frames):
+        cam = cams[(idx * 37) % len(cams)]
+        # per-chunk sets are a load-time precompute on both sides; warm them
+        A, B, _, _ = O.chunk_pick(osc.centers, cam.center)
+        O.chunk_select(osc, A)
+        if B >= 0:
+            O.chunk_select(osc, B)
+        t0 = time.perf_counter()
+        g, m, _ = O.active_set(osc, O.MODE_CHUNK_BLEND, cam)
+        O.render(osc, cam, g, m)
+        spent += time.perf_counter() - t0
+        done += 1
+        idx += 1
+    return {"value": round(done / spent, 4), "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{done} whole CHUNK_BLEND {args.width}x{args.height} frames of the trajectory "
+                      f"(FP64 binned oracle, OpenMP over tiles), chunk sets precomputed"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2505_23158_gb300 import synth
+    import oracle as O
+    scene, cams = synth.workload_outdoor(seed=args.seed, n_poses=args.n_poses, scale=args.scale,
+                                         width=args.width, height_px=args.height)
+    osc = O.OracleScene(scene)
+
+    def step(s):
+        cam = cams[(s * 37) % len(cams)]
+        A, B, _, _ = O.chunk_pick(osc.centers, cam.center)
+        O.chunk_select(osc, A)
+        if B >= 0:
+            O.chunk_select(osc, B)
+        t0 = time.perf_counter()
+        g, m, _ = O.active_set(osc, O.MODE_CHUNK_BLEND, cam)
+        O.render(osc, cam, g, m)
+        return time.perf_counter() - t0
+
+    for s in range(args.warmup):
+        step(s)
+    ts = [step(args.warmup + s) for s in range(args.steps)]
+    t = sum(ts)
+    value = args.steps / t
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"outdoor LOD scene {scene.n_total} Gaussians, 16x16 chunks, "
+                                   f"{args.width}x{args.height}, CHUNK_BLEND; one whole frame per step",
+                       "scale": args.scale},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": "one whole CHUNK_BLEND frame per step (FP64 binned oracle, "
+                                       "OpenMP over tiles), chunk sets precomputed"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_lodge(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

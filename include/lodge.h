@@ -229,6 +229,40 @@ lodge_status lodge_debug_records(lodge_ctx* ctx, int64_t handle, uint32_t* d_gid
 lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals, int64_t n,
                               int32_t key_bits, void* stream);
 
+/* ---------------------------------------------------------------- profiling */
+
+/* Stages of a frame, in launch order. */
+typedef enum {
+    LODGE_STAGE_SELECT = 0,     /* K1 Eq. 2 selection (LOD mode) */
+    LODGE_STAGE_UNION = 1,      /* K2 chunk-pair union (when the pair changes) */
+    LODGE_STAGE_PROJECT = 2,    /* K3 projection + SH + compaction */
+    LODGE_STAGE_DEPTH_SORT = 3, /* K5 onesweep sort by depth */
+    LODGE_STAGE_EMIT = 4,       /* K4 tile emission */
+    LODGE_STAGE_TILE_SORT = 5,  /* K5 onesweep sort by tile */
+    LODGE_STAGE_RANGES = 6,     /* K6 tile ranges */
+    LODGE_STAGE_BLEND = 7,      /* K7 compositing */
+    LODGE_NUM_STAGES = 8
+} lodge_stage;
+
+/* Accumulated device time per stage, measured with CUDA events recorded on
+ * the render stream around each stage (ms), the number of kernel launches per
+ * stage, and the number of frames. */
+typedef struct {
+    double ms[LODGE_NUM_STAGES];
+    int64_t launches[LODGE_NUM_STAGES];
+    int64_t frames;
+    int64_t keys;      /* sum of per-frame tile keys */
+    int64_t visible;   /* sum of per-frame visible Gaussians */
+    int64_t active;    /* sum of per-frame active Gaussians */
+} lodge_profile;
+
+/* Start (enable != 0, counters reset) or stop collecting the profile.
+ * Launch counts are always collected; event timing only while enabled. */
+lodge_status lodge_profile_enable(lodge_ctx* ctx, int enable);
+
+/* Copy the accumulated profile to *out (host). */
+lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,16 @@ class lodge_selection(C.Structure):
                 ("t_b", C.c_double), ("n_active", C.c_int64)]
 
 
+NUM_STAGES = 8
+STAGE_NAMES = ["select", "union", "project", "depth_sort", "emit", "tile_sort", "ranges", "blend"]
+
+
+class lodge_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * NUM_STAGES), ("launches", C.c_int64 * NUM_STAGES),
+                ("frames", C.c_int64), ("keys", C.c_int64), ("visible", C.c_int64),
+                ("active", C.c_int64)]
+
+
 class lodge_frame_stats(C.Structure):
     _fields_ = [("n_active", C.c_int64), ("n_visible", C.c_int64), ("n_keys", C.c_int64),
                 ("n_tiles", C.c_int64), ("chunk_a", C.c_int32), ("chunk_b", C.c_int32),
@@ -74,6 +84,8 @@ _SIGS = {
     "lodge_debug_records": [P, C.c_int64, P, P, P, P, P, P, P, C.c_int64,
                             C.POINTER(C.c_int64), P],
     "lodge_sort_pairs": [P, P, P, C.c_int64, C.c_int32, P],
+    "lodge_profile_enable": [P, C.c_int],
+    "lodge_profile_read": [P, C.POINTER(lodge_profile)],
 }
 
 _lib = None

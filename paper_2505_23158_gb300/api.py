@@ -222,6 +222,16 @@ class Lodge:
                _ptr(r["rgb"]), n.value, C.byref(n), _stream(stream))
         return {k: v[:n.value] for k, v in r.items()}
 
+    def profile_enable(self, enable: bool = True):
+        A.call("lodge_profile_enable", self._h, int(enable))
+
+    def profile_read(self) -> dict:
+        p = A.lodge_profile()
+        A.call("lodge_profile_read", self._h, C.byref(p))
+        return dict(ms={n: p.ms[i] for i, n in enumerate(A.STAGE_NAMES)},
+                    launches={n: p.launches[i] for i, n in enumerate(A.STAGE_NAMES)},
+                    frames=p.frames, keys=p.keys, visible=p.visible, active=p.active)
+
     def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
         """Stable in-place sort of int32 (bit pattern = uint32) keys and values."""
         assert keys.dtype == torch.int32 and vals.dtype == torch.int32

@@ -179,15 +179,26 @@ cudaError_t upload_qtable(const float* q65);
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 15;
 constexpr int kSortTile = kSortThreads * kSortIPT;
+// digit_offsets: optional exclusive per-pass digit offsets (passes x 256)
+// that replace the upfront histogram; final_keys = false skips writing the
+// keys in the last pass (only the values are wanted).
 size_t sort_scratch_bytes(int64_t n, int key_bits);
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                    int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s);
+                    int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
+                    const uint32_t* digit_offsets = nullptr, bool final_keys = true);
+int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
-// K4: emit (tile, record) pairs in depth order.
+// K4: emit (tile, record) pairs in depth order.  koff: n_vis + 1 words;
+// srec / srect: n_vis gathered record ids and rects; n_keys from the
+// projection's count.  digit_hist (zeroed, 4 x 256 words) receives the
+// exclusive digit offsets of the tile sort on key_bits tile bits.
 constexpr int kEmitThreads = 256;
+constexpr int kEmitKeysPerCta = 2048;
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
-                 int32_t tiles_x, uint32_t* tile_key, uint32_t* tile_val, int64_t cap,
-                 uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+                 int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
+                 int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int key_bits,
+                 uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
+                 cudaStream_t s);
 
 // K6: per tile [begin, end) of the sorted keys; ranges zeroed by the caller.
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,

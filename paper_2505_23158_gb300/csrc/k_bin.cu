@@ -1,41 +1,44 @@
 // K4: tile binning.  Walks the visible records in depth order and emits one
 // (tile id, record) pair per tile that the record's rect covers (Sec. 3
 // "Preliminaries: 3DGS": each 2D Gaussian is assigned to every 16x16 tile it
-// overlaps).  Offsets come from a block scan plus decoupled look-back; each
-// block then writes its pairs cooperatively (load-balanced: thread s finds
-// its record by binary search over the block's prefix sums), so the writes
-// are coalesced however unequal the rect sizes are.
+// overlaps).  Two passes: key offsets by block scan plus decoupled look-back,
+// then key-balanced emission (every CTA writes the same number of keys, so a
+// few huge near-camera rects cannot serialise the pass).
 //
-// K6: per-tile [begin, end) ranges of the tile-sorted pairs.
+// K6: per-tile [begin, end) ranges of the tile-sorted keys.
 #include "common.cuh"
 
 namespace lodge {
 
 namespace {
 
+// Pass 1: per depth-sorted visible record, its tile count; block scan plus
+// decoupled look-back give the exclusive key offset koff[i] (koff[n_vis] =
+// total).  The record id and rect are gathered into depth order (srec,
+// srect) so that pass 2 reads them contiguously.
 __global__ void __launch_bounds__(kEmitThreads)
-emit_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
-            const uint2* __restrict__ rec_rect, int32_t tiles_x, uint32_t* __restrict__ tile_key,
-            uint32_t* __restrict__ tile_val, int64_t cap, uint32_t* __restrict__ status,
-            uint32_t* __restrict__ counter, uint32_t* __restrict__ err) {
-    __shared__ uint32_t s_pref[kEmitThreads + 1];
-    __shared__ uint2 s_rect[kEmitThreads];
-    __shared__ uint32_t s_rec[kEmitThreads];
+emit_offsets_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
+                    const uint2* __restrict__ rec_rect, uint32_t* __restrict__ koff,
+                    uint32_t* __restrict__ srec, uint2* __restrict__ srect,
+                    uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
+                    uint32_t* __restrict__ err) {
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_tile, s_prefix;
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    const uint32_t ntiles = (uint32_t)((n_vis + kEmitThreads - 1) / kEmitThreads);
     const int64_t i = (int64_t)tile * kEmitThreads + threadIdx.x;
-    uint32_t cnt = 0, rec = 0;
-    uint2 r = make_uint2(0, 0);
+    uint32_t cnt = 0;
     if (i < n_vis) {
-        rec = sorted_rec[i];
+        uint32_t rec = sorted_rec[i];
         if ((int64_t)rec >= n_vis) { atomicOr(err, kErrBadIndex); rec = 0; }
-        r = rec_rect[rec];
+        uint2 r = rec_rect[rec];
         uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu) + 1u;
         uint32_t h = (r.y >> 16) - (r.x >> 16) + 1u;
         cnt = w * h;
+        srec[i] = rec;
+        srect[i] = r;
     }
     uint32_t total;
     uint32_t excl = block_exclusive_scan(cnt, s_scan, &total);
@@ -48,61 +51,161 @@ emit_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
             prefix = warp_lookback(status, tile, err);
             if (threadIdx.x == 0) st_volatile(status + tile, kStInc | (prefix + total));
         }
-        if (threadIdx.x == 0) s_prefix = prefix;
+        if (threadIdx.x == 0) {
+            s_prefix = prefix;
+            if (tile == ntiles - 1) koff[n_vis] = prefix + total;
+        }
     }
-    s_pref[threadIdx.x] = excl;
-    s_rect[threadIdx.x] = r;
-    s_rec[threadIdx.x] = rec;
-    if (threadIdx.x == 0) s_pref[kEmitThreads] = total;
     __syncthreads();
-    const int64_t base = s_prefix;
-    for (uint32_t s = threadIdx.x; s < total; s += kEmitThreads) {
-        int lo = 0, hi = kEmitThreads;
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (s_pref[mid] <= s) lo = mid; else hi = mid;
+    if (i < n_vis) koff[i] = s_prefix + excl;
+}
+
+// Pass 2: the key list is cut into slices of kEmitKeysPerCta keys; a CTA
+// writes whole slices (grid-stride).  The (at most kEmitKeysPerCta) records
+// that own a slice are located by one warp-parallel search in koff, staged in
+// shared memory, and each key finds its record by binary search there, so
+// every slice costs the same however large single rects are.  The CTA also
+// counts the tile sort's digits (shared-memory histograms flushed once).
+__device__ __forceinline__ int64_t warp_upper_bound(const uint32_t* __restrict__ a, int64_t n,
+                                                    uint32_t v) {
+    // last index g in [0, n) with a[g] <= v (a ascending, a[0] <= v)
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = lo + (int64_t)lane * step;
+        const bool ok = p < hi && a[p] <= v;
+        const uint32_t m = __ballot_sync(0xffffffffu, ok);
+        const int last = 31 - __clz(m);   // lane 0 always qualifies
+        const int64_t nlo = lo + (int64_t)last * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    const int64_t p = lo + lane;
+    const bool ok = p < hi && a[p] <= v;
+    const uint32_t m = __ballot_sync(0xffffffffu, ok);
+    return lo + (31 - __clz(m));
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+emit_keys_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__ srec,
+                 const uint2* __restrict__ srect, int64_t n_vis, int64_t n_keys, int32_t tiles_x,
+                 uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val,
+                 int passes, uint32_t last_mask, uint32_t* __restrict__ digit_hist,
+                 uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_off[kEmitKeysPerCta + 1];
+    __shared__ uint2 s_rect[kEmitKeysPerCta];
+    __shared__ uint32_t s_rec[kEmitKeysPerCta];
+    __shared__ uint32_t s_hist[3][256];
+    __shared__ int64_t s_g0;
+    __shared__ int s_m;
+    for (int i = threadIdx.x; i < 3 * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+    const int64_t nslices = (n_keys + kEmitKeysPerCta - 1) / kEmitKeysPerCta;
+    for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+        const int64_t k0 = sl * kEmitKeysPerCta;
+        const int64_t k1 = min(k0 + (int64_t)kEmitKeysPerCta, n_keys);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int64_t g0 = warp_upper_bound(koff, n_vis, (uint32_t)k0);
+            const int64_t g1 = warp_upper_bound(koff + g0, n_vis - g0, (uint32_t)(k1 - 1)) + g0;
+            if (threadIdx.x == 0) {
+                int64_t m = g1 - g0 + 1;
+                if (m > kEmitKeysPerCta) { atomicOr(err, kErrOverflow); m = kEmitKeysPerCta; }
+                s_g0 = g0;
+                s_m = (int)m;
+            }
         }
-        uint32_t k = s - s_pref[lo];
-        uint2 rr = s_rect[lo];
-        uint32_t tx0 = rr.x & 0xffffu, ty0 = rr.x >> 16, tx1 = rr.y & 0xffffu;
-        uint32_t w = tx1 - tx0 + 1u;
-        uint32_t ty = ty0 + k / w, tx = tx0 + k % w;
-        int64_t out = base + s;
-        if (out < cap) {
-            tile_key[out] = ty * (uint32_t)tiles_x + tx;
-            tile_val[out] = s_rec[lo];
-        } else {
-            atomicOr(err, kErrOverflow);
+        __syncthreads();
+        const int64_t g0 = s_g0;
+        const int m = s_m;
+        for (int j = threadIdx.x; j < m; j += kEmitThreads) {
+            s_off[j] = koff[g0 + j];
+            s_rect[j] = srect[g0 + j];
+            s_rec[j] = srec[g0 + j];
         }
+        __syncthreads();
+        for (int64_t key = k0 + threadIdx.x; key < k1; key += kEmitThreads) {
+            int lo = 0, hi = m;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= (uint32_t)key) lo = mid; else hi = mid;
+            }
+            const uint32_t k = (uint32_t)key - s_off[lo];
+            const uint2 rr = s_rect[lo];
+            const uint32_t tx0 = rr.x & 0xffffu, ty0 = rr.x >> 16, tx1 = rr.y & 0xffffu;
+            const uint32_t w = tx1 - tx0 + 1u;
+            const uint32_t q = k / w;
+            const uint32_t tile = (ty0 + q) * (uint32_t)tiles_x + tx0 + (k - q * w);
+            tile_key[key] = tile;
+            tile_val[key] = s_rec[lo];
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_hist[p][(tile >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += kEmitThreads) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(digit_hist + i, c);
     }
 }
 
+// exclusive scan of each pass's 256-bin digit histogram, in place
+__global__ void digit_scan_kernel(uint32_t* hist) {
+    __shared__ uint32_t s_scan[33];
+    uint32_t* h = hist + blockIdx.x * 256;
+    uint32_t v = h[threadIdx.x], total;
+    h[threadIdx.x] = block_exclusive_scan(v, s_scan, &total);
+}
+
+// K6: per tile [begin, end) of the tile-sorted keys; 4 keys per thread.
 __global__ void ranges_kernel(const uint32_t* __restrict__ key, int64_t n, uint2* __restrict__ ranges,
                               uint32_t ntiles) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t t = key[i];
-    if (t >= ntiles) return;
-    if (i == 0 || key[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i == n - 1 || key[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i0 >= n) return;
+    uint32_t prev = i0 > 0 ? key[i0 - 1] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= n) break;
+        const uint32_t t = key[i];
+        const uint32_t next = i + 1 < n ? key[i + 1] : 0xffffffffu;
+        if (t < ntiles) {
+            if (t != prev) ranges[t].x = (uint32_t)i;
+            if (t != next) ranges[t].y = (uint32_t)(i + 1);
+        }
+        prev = t;
+    }
 }
 
 }  // namespace
 
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
-                 int32_t tiles_x, uint32_t* tile_key, uint32_t* tile_val, int64_t cap,
-                 uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
+                 int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
+                 int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int key_bits,
+                 uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
+                 cudaStream_t s) {
+    (void)tiles_y;
     int64_t nb = (n_vis + kEmitThreads - 1) / kEmitThreads;
     if (nb == 0) return;
-    emit_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, tiles_x, tile_key,
-                                                      tile_val, cap, status, tile_counter, err);
+    emit_offsets_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, koff, srec,
+                                                              srect, status, tile_counter, err);
+    const int64_t nslices = (n_keys + kEmitKeysPerCta - 1) / kEmitKeysPerCta;
+    if (nslices == 0) return;
+    const int P = (key_bits + 7) / 8;
+    const int last_bits = key_bits - 8 * (P - 1);
+    const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
+    const unsigned grid = (unsigned)std::min<int64_t>(nslices, 152 * 4);
+    emit_keys_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, n_keys, tiles_x, tile_key,
+                                                   tile_val, P, last_mask, digit_hist, err);
+    digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
 }
 
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,
                    cudaStream_t s) {
     if (n_keys == 0) return;
-    ranges_kernel<<<(unsigned)((n_keys + 255) / 256), 256, 0, s>>>(tile_key, n_keys, ranges,
-                                                                 (uint32_t)ntiles);
+    const int64_t nt = (n_keys + 3) / 4;
+    ranges_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(tile_key, n_keys, ranges,
+                                                             (uint32_t)ntiles);
 }
 
 }  // namespace lodge

@@ -1,12 +1,19 @@
 // K5: stable LSD radix sort of (u32 key, u32 value) pairs, "onesweep" style:
-// one upfront pass builds every digit histogram, then each 8-bit digit is
-// scattered in a single pass in which a tile learns its global offsets by
-// decoupled look-back over its predecessors' per-digit counts.
+// the digit histograms are known before the first pass (one upfront
+// histogram pass, or supplied by the caller), then each 8-bit digit is
+// scattered in a single pass in which a tile of 3840 pairs learns its global
+// offsets by decoupled look-back over its predecessors' per-digit counts.
 //
 // Used twice per frame: by FP32 depth (4 digits) over the visible records,
 // then by tile id over the emitted (tile, record) pairs, which yields the
 // per-tile front-to-back order of Sec. 3 ("Preliminaries: 3DGS": Gaussians
 // are sorted by depth per tile) with ties broken by record (= gid) order.
+//
+// Ranking inside a tile is warp-private and stable: each warp ranks its 15 x
+// 32 keys in input order with __match_any_sync and a per-warp digit
+// histogram; warps are combined by a per-digit exclusive scan.  Keys are held
+// in registers, ranks packed two per register, values are read only when they
+// are scattered, which keeps the pass at four 256-thread CTAs per SM.
 #include "common.cuh"
 
 namespace lodge {
@@ -51,7 +58,8 @@ __global__ void hist_scan_kernel(uint32_t* hist) {
     h[threadIdx.x] = e;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+template <bool kWriteKeys>
+__global__ void __launch_bounds__(kSortThreads, 4)
 onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
               uint32_t dmask, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ status,
@@ -69,26 +77,26 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    const int64_t base = (int64_t)tile * kSortTile + (int64_t)warp * 32 * kSortIPT;
+    const int64_t seg = (int64_t)tile * kSortTile + (int64_t)warp * 32 * kSortIPT;
+    const int64_t base = seg + lane;
+    const int64_t nvalid = n - seg;   // items of this warp's segment that exist (may be <= 0)
 
-    uint32_t k[kSortIPT], v[kSortIPT], rank[kSortIPT];
+    uint32_t k[kSortIPT];
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
-        int64_t idx = base + j * 32 + lane;
-        bool valid = idx < n;
-        k[j] = valid ? __ldcs(kin + idx) : 0u;
-        v[j] = valid ? __ldcs(vin + idx) : 0u;
-    }
-    // warp-private stable ranking in (j, lane) order = input order
+    for (int j = 0; j < kSortIPT; ++j) k[j] = (j * 32 + lane < nvalid) ? __ldcs(kin + base + j * 32) : 0u;
+
+    // warp-private stable ranking in (j, lane) order = input order; ranks
+    // (< 2^16) packed two per register
     const uint32_t lt = lanemask_lt();
+    uint32_t rk[(kSortIPT + 1) / 2];
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
-        int64_t idx = base + j * 32 + lane;
-        bool valid = idx < n;
-        uint32_t d = valid ? (k[j] >> shift) & dmask : 0x100u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = valid ? s_whist[warp][d] : 0u;
-        rank[j] = before + __popc(peers & lt);
+        const bool valid = j * 32 + lane < nvalid;
+        const uint32_t d = valid ? (k[j] >> shift) & dmask : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? s_whist[warp][d] : 0u;
+        const uint32_t r = before + __popc(peers & lt);
+        if (j & 1) rk[j >> 1] |= r << 16; else rk[j >> 1] = r;
         __syncwarp();
         if (valid && (peers & lt) == 0u) s_whist[warp][d] = before + __popc(peers);
         __syncwarp();
@@ -104,7 +112,7 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
         s_whist[w][d] = run;
         run += c;
     }
-    // decoupled look-back for this digit
+    // decoupled look-back for this digit (bounded waits)
     uint32_t excl = 0;
     uint32_t* st = status + (size_t)tile * kRadix + d;
     if (tile == 0) {
@@ -131,24 +139,24 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     s_dstart[d] = block_exclusive_scan(run, s_scan, &total);
     __syncthreads();
 
-    // scatter into shared memory in digit order, then write out coalesced
+    // scatter keys and values into shared memory in digit order
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
-        int64_t idx = base + j * 32 + lane;
-        if (idx < n) {
-            uint32_t dd = (k[j] >> shift) & dmask;
-            uint32_t pos = s_dstart[dd] + s_whist[warp][dd] + rank[j];
+        if (j * 32 + lane < nvalid) {
+            const uint32_t dd = (k[j] >> shift) & dmask;
+            const uint32_t r = (j & 1) ? (rk[j >> 1] >> 16) : (rk[j >> 1] & 0xffffu);
+            const uint32_t pos = s_dstart[dd] + s_whist[warp][dd] + r;
             s_keys[pos] = k[j];
-            s_vals[pos] = v[j];
+            s_vals[pos] = __ldcs(vin + base + j * 32);
         }
     }
     __syncthreads();
     for (uint32_t i = tid; i < total; i += kSortThreads) {
-        uint32_t key = s_keys[i];
-        uint32_t dd = (key >> shift) & dmask;
-        uint32_t out = s_gbase[dd] + (i - s_dstart[dd]);
+        const uint32_t key = s_keys[i];
+        const uint32_t dd = (key >> shift) & dmask;
+        const uint32_t out = s_gbase[dd] + (i - s_dstart[dd]);
         if ((int64_t)out < n) {
-            kout[out] = key;
+            if (kWriteKeys) kout[out] = key;
             vout[out] = s_vals[i];
         } else {
             atomicOr(err, kErrOverflow);  // only after a look-back gave up
@@ -157,6 +165,12 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
 }
 
 int passes_for(int key_bits) { return key_bits <= 0 ? 0 : (key_bits + 7) / 8; }
+
+uint32_t last_mask_for(int key_bits) {
+    const int P = passes_for(key_bits);
+    const int last_bits = key_bits - 8 * (P - 1);
+    return last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
+}
 
 }  // namespace
 
@@ -167,29 +181,47 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 }
 
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                    int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s) {
+                    int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
+                    const uint32_t* digit_offsets, bool final_keys) {
     const int P = passes_for(key_bits);
     if (n <= 1 || P == 0) return 0;
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     uint32_t* hist = static_cast<uint32_t*>(scratch);
     uint32_t* counters = hist + kMaxPasses * kRadix;
     uint32_t* status = counters + 32;
-    cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bits), s);
-    int hist_blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 4);
-    // the last digit covers only the bits below key_bits
-    const int last_bits = key_bits - 8 * (P - 1);
-    const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
-    hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n, P, last_mask, hist);
-    hist_scan_kernel<<<P, kRadix, 0, s>>>(hist);
+    const uint32_t last_mask = last_mask_for(key_bits);
+    const uint32_t* offs = hist;
+    if (digit_offsets) {
+        // exclusive digit offsets supplied: clear only counters and look-back words
+        cudaMemsetAsync(counters, 0,
+                        sort_scratch_bytes(n, key_bits) - sizeof(uint32_t) * kMaxPasses * kRadix, s);
+        offs = digit_offsets;
+    } else {
+        cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bits), s);
+        int hist_blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 4);
+        hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n, P, last_mask, hist);
+        hist_scan_kernel<<<P, kRadix, 0, s>>>(hist);
+    }
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
     for (int p = 0; p < P; ++p) {
-        onesweep_pass<<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, 8 * p, p == P - 1 ? last_mask : 0xffu, hist + p * kRadix, status + (size_t)p * ntiles * kRadix,
-            counters + p, err);
+        const uint32_t dm = p == P - 1 ? last_mask : 0xffu;
+        uint32_t* stp = status + (size_t)p * ntiles * kRadix;
+        if (p == P - 1 && !final_keys)
+            onesweep_pass<false><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+                ki, vi, ko, vo, n, 8 * p, dm, offs + p * kRadix, stp, counters + p, err);
+        else
+            onesweep_pass<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+                ki, vi, ko, vo, n, 8 * p, dm, offs + p * kRadix, stp, counters + p, err);
         std::swap(ki, ko);
         std::swap(vi, vo);
     }
     return (P & 1) ? 1 : 0;
+}
+
+int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied) {
+    const int P = passes_for(key_bits);
+    if (n <= 1 || P == 0) return 0;
+    return P + (offsets_supplied ? 0 : 2);
 }
 
 }  // namespace lodge

@@ -91,7 +91,8 @@ struct Saved {
 
 struct Workspace {
     DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
-        tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp;
+        tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp, koff, srec,
+        srect, doffs;
 };
 
 // small device/host words
@@ -120,6 +121,12 @@ struct lodge_ctx {
     uint32_t* h_small = nullptr;  // pinned
     std::map<int64_t, std::unique_ptr<Saved>> saved;
     int64_t next_handle = 1;
+    // stage profile (CUDA events on the render stream)
+    bool prof_on = false;
+    lodge_profile prof{};
+    cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};
+    cudaEvent_t ev_end[LODGE_NUM_STAGES] = {};
+    bool ev_pending[LODGE_NUM_STAGES] = {};
 };
 
 namespace lodge {
@@ -184,6 +191,27 @@ static void release(lodge_ctx* ctx, DBuf& b, cudaStream_t s) {
     }
     b.p = nullptr;
     b.cap = 0;
+}
+
+// stage profiling: events around each stage, read after the next sync
+static void prof_begin(lodge_ctx* ctx, int stage, cudaStream_t s) {
+    if (ctx->prof_on && !ctx->ev_pending[stage]) cudaEventRecord(ctx->ev_beg[stage], s);
+}
+static void prof_end(lodge_ctx* ctx, int stage, cudaStream_t s, int launches) {
+    ctx->prof.launches[stage] += launches;
+    if (ctx->prof_on && !ctx->ev_pending[stage]) {
+        cudaEventRecord(ctx->ev_end[stage], s);
+        ctx->ev_pending[stage] = true;
+    }
+}
+static void prof_collect(lodge_ctx* ctx) {
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
+        if (!ctx->ev_pending[k]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_beg[k], ctx->ev_end[k]) == cudaSuccess) ctx->prof.ms[k] += ms;
+        else cudaGetLastError();
+        ctx->ev_pending[k] = false;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -297,6 +325,7 @@ static lodge_status sync_small(lodge_ctx* ctx, cudaStream_t s) {
     CUDA_TRY(cudaMemcpyAsync(ctx->h_small, ctx->d_small, sizeof(uint32_t) * kSmWords,
                              cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    prof_collect(ctx);
     uint32_t err = ctx->h_small[kSmErr];
     if (err & kErrTimeout) return fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
     if (err & kErrOverflow) return fail(LODGE_E_OVERFLOW, "device output capacity exceeded (status 0x%x)", err);
@@ -319,8 +348,10 @@ static lodge_status run_lod_select(lodge_ctx* ctx, Scene* sc, const double* c, c
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
     CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    prof_begin(ctx, LODGE_STAGE_SELECT, s);
     launch_lod_select(sc->dev, c32, lo, hi, ws.list.as<uint32_t>(), ctx->d_small + kSmListCount,
                       ws.status.as<uint32_t>(), ctx->d_small + kSmCtrSelect, ctx->d_small + kSmErr, s);
+    prof_end(ctx, LODGE_STAGE_SELECT, s, ntiles > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
     TRY(sync_small(ctx, s));
     *n_out = ctx->h_small[kSmListCount];
@@ -368,10 +399,12 @@ static lodge_status select_active(lodge_ctx* ctx, Scene* sc, lodge_mode mode, co
         TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
         CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
         CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+        prof_begin(ctx, LODGE_STAGE_UNION, s);
         launch_chunk_union(a.list, a.n, b.list, b.n, sc->dev.n_total, ws.marks.as<uint8_t>(),
                            sc->ulist.as<uint32_t>(), ctx->d_small + kSmListCount,
                            ws.status.as<uint32_t>(), ctx->d_small + kSmCtrUnion,
                            ctx->d_small + kSmErr, s);
+        prof_end(ctx, LODGE_STAGE_UNION, s, (a.n > 0) + (b.n > 0) + (ntiles > 0));
         CUDA_TRY(cudaGetLastError());
         sc->ua = -2;
         TRY(sync_small(ctx, s));
@@ -421,8 +454,10 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     po.depth_key = ws.dkey.as<uint32_t>();
     po.depth_val = ws.dval.as<uint32_t>();
     po.counts = ctx->d_small + kSmProj;
+    prof_begin(ctx, LODGE_STAGE_PROJECT, s);
     launch_project(dsc, cam, act.list, na, (float)act.tA, (float)act.tB, po,
                    ws.status.as<uint32_t>(), ctx->d_small + kSmCtrProj, ctx->d_small + kSmErr, s);
+    prof_end(ctx, LODGE_STAGE_PROJECT, s, na > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
     TRY(sync_small(ctx, s));
     const int64_t n_vis = ctx->h_small[kSmProj];
@@ -437,8 +472,10 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     TRY(ensure(ctx, ws.dval2, sizeof(uint32_t) * nv1, s));
     const int tbits = bits_for((uint32_t)(ntiles_img - 1));
     TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_keys, tbits)), s));
+    prof_begin(ctx, LODGE_STAGE_DEPTH_SORT, s);
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
                              ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, ctx->d_small + kSmErr, s);
+    prof_end(ctx, LODGE_STAGE_DEPTH_SORT, s, onesweep_launches(n_vis, 32, false));
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
 
@@ -447,23 +484,36 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     TRY(ensure(ctx, ws.tval, sizeof(uint32_t) * nk1, s));
     TRY(ensure(ctx, ws.tkey2, sizeof(uint32_t) * nk1, s));
     TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * nk1, s));
+    TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 4 * 256, s));
+    CUDA_TRY(cudaMemsetAsync(ws.doffs.p, 0, sizeof(uint32_t) * 4 * 256, s));
+    TRY(ensure(ctx, ws.koff, sizeof(uint32_t) * (nv1 + 1), s));
+    TRY(ensure(ctx, ws.srec, sizeof(uint32_t) * nv1, s));
+    TRY(ensure(ctx, ws.srect, sizeof(uint2) * nv1, s));
     int64_t etiles = std::max<int64_t>((n_vis + kEmitThreads - 1) / kEmitThreads, 1);
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
-    launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), cam.tiles_x, ws.tkey.as<uint32_t>(),
-                ws.tval.as<uint32_t>(), n_keys, ws.status.as<uint32_t>(), ctx->d_small + kSmCtrEmit,
-                ctx->d_small + kSmErr, s);
+    prof_begin(ctx, LODGE_STAGE_EMIT, s);
+    launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), cam.tiles_x, cam.tiles_y,
+                ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_keys,
+                ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), tbits, ws.doffs.as<uint32_t>(),
+                ws.status.as<uint32_t>(), ctx->d_small + kSmCtrEmit, ctx->d_small + kSmErr, s);
+    prof_end(ctx, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_keys > 0 ? 2 : 0));
 
     // ---- K5 tile sort (stable: keeps depth order within a tile)
+    prof_begin(ctx, LODGE_STAGE_TILE_SORT, s);
     int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), ws.tkey2.as<uint32_t>(),
-                             ws.tval2.as<uint32_t>(), n_keys, tbits, ws.sort.p, ctx->d_small + kSmErr, s);
+                             ws.tval2.as<uint32_t>(), n_keys, tbits, ws.sort.p, ctx->d_small + kSmErr, s,
+                             ws.doffs.as<uint32_t>(), true);
+    prof_end(ctx, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_keys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
 
     // ---- K6 ranges, K7 blend
     TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
     CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
+    prof_begin(ctx, LODGE_STAGE_RANGES, s);
     launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, s);
+    prof_end(ctx, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
     BlendOut bo{d_rgb, nullptr, nullptr};
     if (save) {
         const size_t npix = (size_t)c.width * c.height;
@@ -472,11 +522,17 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
         bo.T_final = ws.T.as<float>();
         bo.last = ws.last.as<uint32_t>();
     }
+    prof_begin(ctx, LODGE_STAGE_BLEND, s);
     launch_blend(cam, ws.ranges.as<uint2>(), vs.as<uint32_t>(), n_keys, ws.rec_a.as<float4>(),
                  ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
+    prof_end(ctx, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
     TRY(sync_small(ctx, s));
 
+    ctx->prof.frames += 1;
+    ctx->prof.keys += n_keys;
+    ctx->prof.visible += n_vis;
+    ctx->prof.active += na;
     if (st) {
         st->n_active = na;
         st->n_visible = n_vis;
@@ -612,6 +668,10 @@ lodge_status lodge_create(int device, size_t hbm_budget_bytes, lodge_ctx** out) 
     TRY(dmalloc(ctx.get(), (void**)&ctx->d_small, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMemset(ctx->d_small, 0, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMallocHost((void**)&ctx->h_small, sizeof(uint32_t) * kSmWords));
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
+        CUDA_TRY(cudaEventCreate(&ctx->ev_beg[k]));
+        CUDA_TRY(cudaEventCreate(&ctx->ev_end[k]));
+    }
     *out = ctx.release();
     return LODGE_OK;
 }
@@ -635,10 +695,15 @@ lodge_status lodge_destroy(lodge_ctx* ctx) {
     Workspace& w = ctx->ws;
     for (DBuf* b : {&w.list, &w.marks, &w.status, &w.rec_a, &w.rec_b, &w.rec_c, &w.rec_rect, &w.rec_gid,
                     &w.dkey, &w.dval, &w.dkey2, &w.dval2, &w.tkey, &w.tval, &w.tkey2, &w.tval2,
-                    &w.ranges, &w.sort, &w.T, &w.last, &w.img, &w.act_so, &w.act_q, &w.mtmp})
+                    &w.ranges, &w.sort, &w.T, &w.last, &w.img, &w.act_so, &w.act_q, &w.mtmp, &w.koff,
+                    &w.srec, &w.srect, &w.doffs})
         if (b->p) cudaFree(b->p);
     if (ctx->d_small) cudaFree(ctx->d_small);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
+        if (ctx->ev_beg[k]) cudaEventDestroy(ctx->ev_beg[k]);
+        if (ctx->ev_end[k]) cudaEventDestroy(ctx->ev_end[k]);
+    }
     cudaDeviceSynchronize();
     delete ctx;
     return LODGE_OK;
@@ -1036,6 +1101,20 @@ lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals
     }
     CUDA_TRY(cudaGetLastError());
     return sync_small(ctx, s);
+}
+
+lodge_status lodge_profile_enable(lodge_ctx* ctx, int enable) {
+    if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
+    ctx->prof = lodge_profile{};
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) ctx->ev_pending[k] = false;
+    ctx->prof_on = enable != 0;
+    return LODGE_OK;
+}
+
+lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
+    if (!ctx || !out) return fail(LODGE_E_INVALID, "bad argument");
+    *out = ctx->prof;
+    return LODGE_OK;
 }
 
 }  // extern "C"
