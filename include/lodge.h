@@ -229,6 +229,27 @@ lodge_status lodge_debug_records(lodge_ctx* ctx, int64_t handle, uint32_t* d_gid
 lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals, int64_t n,
                               int32_t key_bits, void* stream);
 
+/* Allocation-free variant of lodge_sort_pairs (the paper has no counterpart:
+ * this is a convenience for callers that cannot allocate device memory, such
+ * as an application that owns every device allocation itself, or a loop that
+ * cannot afford an allocation's implicit synchronisation).  Same result as
+ * lodge_sort_pairs: d_keys / d_vals (device, caller-owned, n pairs) are
+ * sorted in place, stably, on key bits [0, key_bits).  No context is needed
+ * and nothing is allocated: scratch is a fixed array in the library's device
+ * memory, about 9.1 MB on every device that loads the library, kept until the
+ * process exits.
+ *   - n may be at most 1,048,576 (2^20); larger n returns LODGE_E_INVALID
+ *     before any device work.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before capturing any stream into a graph.
+ *   - Every call on a device shares the array: calls whose device work
+ *     overlaps (on different streams) race and give wrong results.  The call
+ *     synchronises `stream` before returning.
+ *   - Errors: LODGE_E_INVALID (arguments), LODGE_E_CUDA, LODGE_E_TIMEOUT (a
+ *     bounded device-side wait gave up). */
+lodge_status lodge_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n,
+                                      int32_t key_bits, void* stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stages of a frame, in launch order. */

@@ -84,6 +84,7 @@ _SIGS = {
     "lodge_debug_records": [P, C.c_int64, P, P, P, P, P, P, P, C.c_int64,
                             C.POINTER(C.c_int64), P],
     "lodge_sort_pairs": [P, P, P, C.c_int64, C.c_int32, P],
+    "lodge_sort_pairs_noalloc": [P, P, C.c_int64, C.c_int32, P],
     "lodge_profile_enable": [P, C.c_int],
     "lodge_profile_read": [P, C.POINTER(lodge_profile)],
 }

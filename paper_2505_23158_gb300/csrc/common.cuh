@@ -214,6 +214,9 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s);
 
+// records msg as the calling thread's lodge_last_error message; returns s
+lodge_status set_error(lodge_status s, const char* msg);
+
 // Q table for the opacity-aware extent (65 entries), host-computed.
 void fill_qtable(float* q65);
 

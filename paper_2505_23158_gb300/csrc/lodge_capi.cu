@@ -31,6 +31,12 @@ static lodge_status fail(lodge_status s, const char* fmt, ...) {
     return s;
 }
 
+// records a message for lodge_last_error from other translation units
+lodge_status set_error(lodge_status s, const char* msg) {
+    g_err = msg;
+    return s;
+}
+
 #define CUDA_TRY(x)                                                                          \
     do {                                                                                     \
         cudaError_t e_ = (x);                                                                \
