@@ -93,6 +93,7 @@ def _load():
             lib.orc_keys.argtypes = [P, P, C.c_int64, P, P, P, P, C.c_int64]
             lib.orc_keys.restype = C.c_int64
             lib.orc_sh_basis.argtypes = [C.c_double, C.c_double, C.c_double, P]
+            lib.orc_depth32.argtypes = [P, P, C.c_int64, P]
             _lib = lib
     return _lib
 
@@ -295,6 +296,16 @@ def keys(osc: OracleScene, cam, gids, mults=None):
     lib.orc_keys(osc.ptr, C.byref(cc), g.size, _p(g), None if m is None else _p(m),
                  _p(k), _p(gg), n)
     return k, gg
+
+
+def depth32(means, cam):
+    """FP32 key depth (camera z by the key spec) of each mean."""
+    lib = _load()
+    m = _c(means, np.float32)
+    z = np.empty(m.shape[0], np.float32)
+    cc = _cam(cam)
+    lib.orc_depth32(_p(m), C.byref(cc), m.shape[0], _p(z))
+    return z
 
 
 def sh_basis(d):

@@ -372,6 +372,12 @@ static int key_spec(const orc_scene* sc, const orc_camera* cam, int64_t g,
     return 1;
 }
 
+/* FP32 key depth of each listed Gaussian (the sort key and near-cull input). */
+void orc_depth32(const float* means, const orc_camera* cam, int64_t n, float* z)
+{
+    for (int64_t i = 0; i < n; ++i) z[i] = cam_depth32(cam, means + 3 * i);
+}
+
 /* ---------------------------------------------------------------------- */
 /* FP64 projection (EWA splatting, Zwicker et al. as used by 3DGS) and     */
 /* view-dependent colour (real spherical harmonics up to degree 3)         */
