@@ -237,3 +237,35 @@ class Lodge:
         assert keys.dtype == torch.int32 and vals.dtype == torch.int32
         A.call("lodge_sort_pairs", self._h, _ptr(keys), _ptr(vals), int(keys.numel()), int(key_bits),
                _stream(stream))
+
+
+class _RenderParams(torch.autograd.Function):
+    """Differentiable render of raw Gaussian parameters through the library's
+    forward (lodge_render_params) and hand-written adjoint
+    (lodge_render_backward)."""
+
+    @staticmethod
+    def forward(fctx, means, log_scales, quats, logits, sh, lodge, cam, sh_degree, filter_var):
+        img, stats, h = lodge.render_params(means, log_scales, quats, logits, sh, cam,
+                                            sh_degree=sh_degree, filter_var=filter_var, save=True)
+        fctx.lodge = lodge
+        fctx.handle = h
+        fctx.save_for_backward(means, log_scales, quats, logits, sh)
+        return img
+
+    @staticmethod
+    def backward(fctx, g_img):
+        means, log_scales, quats, logits, sh = fctx.saved_tensors
+        gs = [torch.zeros_like(t) for t in (means, log_scales, quats, logits, sh)]
+        try:
+            fctx.lodge.render_backward(fctx.handle, g_img.contiguous(), *gs)
+        finally:
+            fctx.lodge.release(fctx.handle)
+        return (*gs, None, None, None, None)
+
+
+def render_differentiable(lodge: Lodge, means, log_scales, quats, logits, sh, cam,
+                          sh_degree: int = 3, filter_var: float = 0.0):
+    """Image (H, W, 3) that backpropagates to the five parameter tensors."""
+    return _RenderParams.apply(means, log_scales, quats, logits, sh, lodge, cam, sh_degree,
+                               filter_var)

@@ -214,6 +214,18 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s);
 
+// K8 / K9: adjoint of compositing and projection (fine-tuning path).
+// grec: 9 x n_rec floats, zeroed: d(mean'x, mean'y, u00, u01, u11, o', r, g, b).
+void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+                      int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                      int64_t n_rec, const float* T_final, const uint32_t* last,
+                      const float* dL_drgb, float* grec, cudaStream_t s);
+void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec_gid,
+                        const float* grec, const float* means, const float4* act_so,
+                        const float4* act_q, const float* quats, const float* sh, int sh_degree,
+                        float filter_var, float* g_means, float* g_log_scales, float* g_quats,
+                        float* g_logits, float* g_sh, cudaStream_t s);
+
 // records msg as the calling thread's lodge_last_error message; returns s
 lodge_status set_error(lodge_status s, const char* msg);
 

@@ -98,7 +98,7 @@ struct Saved {
 struct Workspace {
     DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
         tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp, koff, srec,
-        srect, doffs;
+        srect, doffs, grec;
 };
 
 // small device/host words
@@ -702,7 +702,7 @@ lodge_status lodge_destroy(lodge_ctx* ctx) {
     for (DBuf* b : {&w.list, &w.marks, &w.status, &w.rec_a, &w.rec_b, &w.rec_c, &w.rec_rect, &w.rec_gid,
                     &w.dkey, &w.dval, &w.dkey2, &w.dval2, &w.tkey, &w.tval, &w.tkey2, &w.tval2,
                     &w.ranges, &w.sort, &w.T, &w.last, &w.img, &w.act_so, &w.act_q, &w.mtmp, &w.koff,
-                    &w.srec, &w.srect, &w.doffs})
+                    &w.srec, &w.srect, &w.doffs, &w.grec})
         if (b->p) cudaFree(b->p);
     if (ctx->d_small) cudaFree(ctx->d_small);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
@@ -1019,12 +1019,26 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
 lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* d_dL_drgb, float* d_g_means,
                                    float* d_g_log_scales, float* d_g_quats, float* d_g_opacity_logits,
                                    float* d_g_sh, void* stream) {
-    (void)d_dL_drgb; (void)d_g_means; (void)d_g_log_scales; (void)d_g_quats; (void)d_g_opacity_logits;
-    (void)d_g_sh; (void)stream;
-    if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
+    if (!ctx || !d_dL_drgb) return fail(LODGE_E_INVALID, "bad argument");
     auto it = ctx->saved.find(handle);
     if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
-    return fail(LODGE_E_INVALID, "backward pass not available in this build");
+    Saved& v = *it->second;
+    if (!v.params) return fail(LODGE_E_INVALID, "frame %lld was not rendered from parameters", (long long)handle);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace& ws = ctx->ws;
+    const size_t n9 = 9 * (size_t)std::max<int64_t>(v.n_vis, 1);
+    TRY(ensure(ctx, ws.grec, sizeof(float) * n9, s));
+    CUDA_TRY(cudaMemsetAsync(ws.grec.p, 0, sizeof(float) * n9, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    launch_blend_bwd(v.cam, v.ranges.as<uint2>(), v.tval.as<uint32_t>(), v.n_keys, v.rec_a.as<float4>(),
+                     v.rec_b.as<float4>(), v.rec_c.as<float>(), v.n_vis, v.T.as<float>(),
+                     v.last.as<uint32_t>(), d_dL_drgb, ws.grec.as<float>(), s);
+    launch_project_bwd(v.cam, v.n_vis, v.rec_gid.as<uint32_t>(), ws.grec.as<float>(), v.means,
+                       v.act_so.as<float4>(), v.act_q.as<float4>(), v.quats, v.sh, v.sh_degree,
+                       v.filter_var, d_g_means, d_g_log_scales, d_g_quats, d_g_opacity_logits, d_g_sh, s);
+    CUDA_TRY(cudaGetLastError());
+    return sync_small(ctx, s);
 }
 
 lodge_status lodge_release(lodge_ctx* ctx, int64_t handle) {
