@@ -126,6 +126,51 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
+# multi-rank protocol (weak scaling: every rank renders its own trajectory)
+def rank_trajectory_seed(seed: int, rank: int, world: int) -> int:
+    """Trajectory seed of a rank: rank 0 keeps the base trajectory at N = 1."""
+    return seed if world == 1 else seed + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value over ranks (the slowest rank bounds the job)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank: int, world: int, t_max: float) -> float:
+    """Whole-job frames/s: every rank's frames over the slowest rank's time."""
+    return frames_per_rank * world / t_max
+
+
+def timed_region(run, world: int, sync=None, clock=None, device=None):
+    """Barrier, sync, run(), sync, barrier; returns the max over ranks of
+    the time `clock` measured (default: host perf_counter around run)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if sync:
+        sync()
+    if clock is None:
+        t0 = time.perf_counter()
+        run()
+        if sync:
+            sync()
+        t = time.perf_counter() - t0
+    else:
+        t = clock(run)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    return max_over_ranks(t, world, device)
+
+
+# ---------------------------------------------------------------------------
 def stage_bytes(stage: str, prof: dict) -> float:
     """Algorithmic bytes of one stage summed over the profiled frames."""
     a, v, k = prof["active"], prof["visible"], prof["keys"]
@@ -136,9 +181,11 @@ def stage_bytes(stage: str, prof: dict) -> float:
     if stage == "depth_sort":
         return v * (4 + 4 * 16)          # histogram read + 4 passes of read/write key+value
     if stage == "emit":
-        return v * (4 + 8) + k * 8
+        # offsets pass: read record id + rect, write offset, id, rect (28 B per
+        # visible); key pass: stage offset/id/rect (16 B) and write 8 B per key
+        return v * (28 + 16) + k * 8
     if stage == "tile_sort":
-        return k * (4 + 2 * 16)          # 13-bit tile ids: histogram + 2 passes
+        return k * (2 * 16)              # 13-bit tile ids: 2 passes of read+write key+value
     if stage == "ranges":
         return k * 4
     return 0.0
@@ -159,8 +206,9 @@ def run_lodge(args, rank, world, local_rank):
                                          width=args.width, height_px=args.height)
     if world > 1:
         # weak scaling: every rank walks its own seeded trajectory of the same scene
-        cams = synth.outdoor_trajectory(scene, seed=args.seed + 1000 * rank, n_poses=args.n_poses,
-                                        width=args.width, height_px=args.height)
+        cams = synth.outdoor_trajectory(scene, seed=rank_trajectory_seed(args.seed, rank, world),
+                                        n_poses=args.n_poses, width=args.width,
+                                        height_px=args.height)
     t_gen = time.time() - t0
     ctx = Lodge(local_rank)
     t0 = time.time()
@@ -179,33 +227,30 @@ def run_lodge(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def timed(mode, steps, per_frame_events=True):
         evs = []
-        barrier()
-        torch.cuda.synchronize()
+
+        def run():
+            last = e0
+            for s in range(steps):
+                for cam in frames(s):
+                    ctx.render(sid, mode, cam, out=out)
+                    if per_frame_events:
+                        e = torch.cuda.Event(enable_timing=True)
+                        e.record(stream)
+                        evs.append((last, e))
+                        last = e
+
+        def clock(fn):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 1e3
+
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        last = e0
-        for s in range(steps):
-            for cam in frames(s):
-                ctx.render(sid, mode, cam, out=out)
-                if per_frame_events:
-                    e = torch.cuda.Event(enable_timing=True)
-                    e.record(stream)
-                    evs.append((last, e))
-                    last = e
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        t = e0.elapsed_time(e1) / 1e3
+        t = timed_region(run, world, sync=torch.cuda.synchronize, clock=clock, device=dev)
         lat = [a.elapsed_time(b) for a, b in evs]
         return t, lat
 
@@ -225,9 +270,8 @@ def run_lodge(args, rank, world, local_rank):
     clocks = clk.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    t_blend = max_over_ranks(t_blend)
     n_frames = args.steps * P
-    value = n_frames * world / t_blend
+    value = job_throughput(n_frames, world, t_blend)
 
     # ---- full detail on the same poses
     fsteps = args.full_steps if args.full_steps is not None else max(1, args.steps // 2)
@@ -235,22 +279,18 @@ def run_lodge(args, rank, world, local_rank):
     t_full, lat_full = timed(FULL, fsteps)
     prof_full = ctx.profile_read()
     ctx.profile_enable(False)
-    t_full = max_over_ranks(t_full)
-    full_fps = fsteps * P * world / t_full
+    full_fps = job_throughput(fsteps * P, world, t_full)
 
     # ---- end to end through the host-buffer entry point (camera H2D, image D2H)
     host = torch.empty(npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)
     e2e_steps = max(1, min(args.steps, 3))
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        for cam in frames(s):
-            ctx.render_host(sid, CHUNK_BLEND, [cam], host)
-    torch.cuda.synchronize()
-    t_e2e = max_over_ranks(time.perf_counter() - t0)
-    barrier()
-    e2e_fps = e2e_steps * P * world / t_e2e
+    def run_e2e():
+        for s in range(e2e_steps):
+            for cam in frames(s):
+                ctx.render_host(sid, CHUNK_BLEND, [cam], host)
+
+    t_e2e = timed_region(run_e2e, world, sync=torch.cuda.synchronize, device=dev)
+    e2e_fps = job_throughput(e2e_steps * P, world, t_e2e)
 
     # ---- roofline of the dominant kernel stage
     pk, pk_kind = peaks()
