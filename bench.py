@@ -191,6 +191,32 @@ def stage_bytes(stage: str, prof: dict) -> float:
     return 0.0
 
 
+def measured_traffic(kernel_stage: str, units_per_launch: float):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/traffic_*.txt), scaled to this run's units per launch;
+    None if there is no summary for it or its kernel source changed since."""
+    import hashlib
+    files = {"tile_sort": "traffic_onesweep_tile_sort.txt"}
+    f = files.get(kernel_stage)
+    if f is None:
+        return None
+    path = os.path.join(ROOT, "profiles", f)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#") and "=" in line:
+            k, v = line.split("=", 1)
+            kv[k] = v
+    src = os.path.join(ROOT, kv.get("source", ""))
+    if not os.path.exists(src):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv.get("source_sha256_16"):
+        return None
+    return float(kv["dram_bytes_per_key"]) * units_per_launch
+
+
 def run_lodge(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -312,9 +338,15 @@ def run_lodge(args, rank, world, local_rank):
         by = stage_bytes(dom, prof)
         ach = by / (ms[dom] / 1e3) / 1e9
         peak = pk["hbm_gbs"]
+        nl = max(prof["launches"][dom], 1)
+        # every tile-sort pass processes all of a frame's keys
+        per_launch_units = prof["keys"] / max(prof["frames"], 1) if dom == "tile_sort" else 0
+        tr = measured_traffic(dom, per_launch_units)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None, "kernel": dom,
-                "peak_source": f"{pk_kind} hbm_gbs"}
+                "frac": round(ach / peak, 4), "traffic": None if tr is None else round(tr),
+                "kernel": dom, "algorithmic_bytes_per_launch": round(by / nl),
+                "avg_launch_ms": round(ms[dom] / nl, 5),
+                "peak_source": f"{pk_kind} hbm_gbs (burst copy)"}
     stages = {k: round(v / max(prof["frames"], 1), 4) for k, v in ms.items()}
     stages_full = {k: round(v / max(prof_full["frames"], 1), 4) for k, v in prof_full["ms"].items()}
     stage_gbs = {}
