@@ -80,6 +80,16 @@ typedef struct {
     float pad_;
 } lodge_level_desc;
 
+/* Where a scene's Gaussians live (Sec. 3 "Chunk-based rendering": only the
+ * active sets of the chunks in use need GPU memory). */
+typedef enum {
+    LODGE_RESIDENT = 0,  /* every level in HBM; all four render modes */
+    LODGE_STREAMED = 1   /* levels in pinned host memory; each chunk's active
+                            set is gathered into an HBM block on first use and
+                            cached under the context's budget (LRU eviction);
+                            CHUNK and CHUNK_BLEND only */
+} lodge_residency_mode;
+
 typedef struct {
     int32_t num_levels;              /* L >= 1, at most 8 */
     int32_t sh_degree;               /* 0..3 */
@@ -87,7 +97,7 @@ typedef struct {
     const double* d_thresholds;      /* L - 1 ascending distances d_1..d_{L-1}
                                         (Eq. 2; d_0 = 0, d_L = inf) */
     int32_t num_chunks;              /* K >= 0 chunk centres (0: FULL/LOD only) */
-    int32_t pad_;
+    int32_t residency;               /* lodge_residency_mode */
     const double* chunk_centers;     /* K x 3 */
 } lodge_scene_desc;
 
@@ -145,9 +155,11 @@ lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int3
 lodge_status lodge_unload_scene(lodge_ctx* ctx, int32_t scene_id);
 
 /* Ensure the listed chunks' active sets are resident (Sec. 3 "Opacity
- * blending": sets are loaded in the background).  In this version every
- * chunk set is resident after lodge_load_scene, so this validates the ids
- * and returns. `blocking` is accepted for interface stability. */
+ * blending": sets are loaded in the background).  Resident scenes: nothing to
+ * do.  Streamed scenes: each missing chunk block is gathered into HBM on the
+ * context's side stream (evicting unreferenced blocks if the budget requires);
+ * blocking != 0 waits for the uploads.  Errors: LODGE_E_BUDGET if a block
+ * cannot fit, LODGE_E_CUDA on a failed upload. */
 lodge_status lodge_upload_chunks(lodge_ctx* ctx, int32_t scene_id, const int32_t* chunk_ids,
                                  int32_t n, int blocking);
 
@@ -249,6 +261,62 @@ lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals
  *     bounded device-side wait gave up). */
 lodge_status lodge_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n,
                                       int32_t key_bits, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* One render request: scene, mode, camera and its arrival time in seconds
+ * relative to the start of lodge_serve. */
+typedef struct {
+    int32_t scene;
+    int32_t mode;          /* lodge_mode */
+    lodge_camera cam;
+    double arrival_s;
+} lodge_request;
+
+typedef struct {
+    double start_s;        /* admitted: a slot picked it up */
+    double finish_s;       /* image rendered (and copied to the host if asked) */
+    int32_t status;        /* lodge_status of this request */
+    int32_t slot;
+    lodge_frame_stats stats;
+} lodge_request_result;
+
+typedef struct {
+    int32_t slots;         /* requests in flight at once, 1..64 */
+    int32_t realtime;      /* != 0: a request is not started before its arrival */
+    float* h_images;       /* optional host buffer: the images back to back in
+                              request order (H x W x 3 each) */
+    double wait_limit_s;   /* how long a request may wait for HBM (0: 10 s) */
+} lodge_serve_opts;
+
+/* Serve n requests with continuous batching (the serving loop built around
+ * the paper's renderer: chunk residency, sort buffers and images stay on the
+ * device).  Each slot is a worker with its own stream and scratch; requests
+ * are admitted in arrival order as slots free up and as their memory fits the
+ * HBM budget, and their work overlaps on the device.  results[i] (host)
+ * receives request i's times, status and frame counters; latency =
+ * finish_s - arrival_s.  Returns LODGE_E_INVALID if any request failed (its
+ * own status says why); the other requests still complete. */
+lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, int32_t n,
+                         const lodge_serve_opts* opts, lodge_request_result* results);
+
+/* Residency counters of the context (streamed scenes). */
+typedef struct {
+    int64_t resident_blocks;
+    int64_t block_hits, block_uploads, block_evictions;
+    int64_t upload_bytes;       /* attribute bytes gathered into HBM */
+    int64_t failed_uploads;
+    int64_t hbm_used, hbm_budget;
+} lodge_residency;
+
+/* Copy the context's residency counters to *out (host).  Errors:
+ * LODGE_E_INVALID for NULL arguments. */
+lodge_status lodge_residency_stats(lodge_ctx* ctx, lodge_residency* out);
+
+/* Fault injection for tests: the next n chunk uploads fail on the host side
+ * (LODGE_E_CUDA for the requests that need them) without touching the
+ * device. */
+lodge_status lodge_inject_upload_failures(lodge_ctx* ctx, int32_t n);
 
 /* ---------------------------------------------------------------- profiling */
 

@@ -32,9 +32,12 @@ class lodge_level_desc(C.Structure):
                 ("filter_var", C.c_float), ("pad_", C.c_float)]
 
 
+RESIDENT, STREAMED = 0, 1
+
+
 class lodge_scene_desc(C.Structure):
     _fields_ = [("num_levels", C.c_int32), ("sh_degree", C.c_int32), ("levels", C.c_void_p),
-                ("d_thresholds", C.c_void_p), ("num_chunks", C.c_int32), ("pad_", C.c_int32),
+                ("d_thresholds", C.c_void_p), ("num_chunks", C.c_int32), ("residency", C.c_int32),
                 ("chunk_centers", C.c_void_p)]
 
 
@@ -65,6 +68,28 @@ class lodge_frame_stats(C.Structure):
                 ("t_a", C.c_double), ("t_b", C.c_double)]
 
 
+class lodge_request(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("mode", C.c_int32), ("cam", lodge_camera),
+                ("arrival_s", C.c_double)]
+
+
+class lodge_request_result(C.Structure):
+    _fields_ = [("start_s", C.c_double), ("finish_s", C.c_double), ("status", C.c_int32),
+                ("slot", C.c_int32), ("stats", lodge_frame_stats)]
+
+
+class lodge_serve_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("realtime", C.c_int32), ("h_images", C.c_void_p),
+                ("wait_limit_s", C.c_double)]
+
+
+class lodge_residency(C.Structure):
+    _fields_ = [("resident_blocks", C.c_int64), ("block_hits", C.c_int64),
+                ("block_uploads", C.c_int64), ("block_evictions", C.c_int64),
+                ("upload_bytes", C.c_int64), ("failed_uploads", C.c_int64),
+                ("hbm_used", C.c_int64), ("hbm_budget", C.c_int64)]
+
+
 P = C.c_void_p
 _SIGS = {
     "lodge_create": [C.c_int, C.c_size_t, C.POINTER(P)],
@@ -85,6 +110,9 @@ _SIGS = {
                             C.POINTER(C.c_int64), P],
     "lodge_sort_pairs": [P, P, P, C.c_int64, C.c_int32, P],
     "lodge_sort_pairs_noalloc": [P, P, C.c_int64, C.c_int32, P],
+    "lodge_serve": [P, P, C.c_int32, C.POINTER(lodge_serve_opts), P],
+    "lodge_residency_stats": [P, C.POINTER(lodge_residency)],
+    "lodge_inject_upload_failures": [P, C.c_int32],
     "lodge_profile_enable": [P, C.c_int],
     "lodge_profile_read": [P, C.POINTER(lodge_profile)],
 }

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _capi as A
-from ._capi import CHUNK, CHUNK_BLEND, FULL, LOD, LodgeError  # noqa: F401
+from ._capi import CHUNK, CHUNK_BLEND, FULL, LOD, RESIDENT, STREAMED, LodgeError  # noqa: F401
 
 
 def camera_struct(cam) -> A.lodge_camera:
@@ -80,7 +80,9 @@ class Lodge:
         self.close()
 
     # -- scenes
-    def load_scene(self, scene) -> int:
+    def load_scene(self, scene, residency: int = 0) -> int:
+        """Copy a synth.Scene into the library.  residency=STREAMED keeps the
+        levels in pinned host memory and gathers chunk blocks into HBM on use."""
         levels = (A.lodge_level_desc * scene.num_levels)()
         keep = []
         for i, lv in enumerate(scene.levels):
@@ -100,6 +102,7 @@ class Lodge:
         desc.d_thresholds = d.ctypes.data if d.size else None
         desc.num_chunks = int(cc.shape[0])
         desc.chunk_centers = cc.ctypes.data if cc.size else None
+        desc.residency = int(residency)
         sid = C.c_int32()
         A.call("lodge_load_scene", self._h, C.byref(desc), C.byref(sid))
         return sid.value
@@ -221,6 +224,54 @@ class Lodge:
                _ptr(r["rect"]), _ptr(r["mean2"]), _ptr(r["conic"]), _ptr(r["opacity"]),
                _ptr(r["rgb"]), n.value, C.byref(n), _stream(stream))
         return {k: v[:n.value] for k, v in r.items()}
+
+    # -- serving and residency
+    def serve(self, requests, slots: int = 4, realtime: bool = True, images: bool = False,
+              wait_limit_s: float = 10.0):
+        """requests: list of (scene_id, mode, camera, arrival_s).  Returns
+        (results list of dicts, images list or None).  Raises LodgeError only
+        for invalid arguments; per-request failures are in each result."""
+        n = len(requests)
+        arr = (A.lodge_request * max(n, 1))()
+        for i, (sid, mode, cam, t) in enumerate(requests):
+            arr[i].scene = int(sid)
+            arr[i].mode = int(mode)
+            arr[i].cam = camera_struct(cam)
+            arr[i].arrival_s = float(t)
+        res = (A.lodge_request_result * max(n, 1))()
+        opts = A.lodge_serve_opts()
+        opts.slots = int(slots)
+        opts.realtime = int(realtime)
+        opts.wait_limit_s = float(wait_limit_s)
+        host = None
+        if images:
+            total = sum(c.width * c.height * 3 for _, _, c, _ in requests)
+            host = np.zeros(max(total, 1), np.float32)
+            opts.h_images = host.ctypes.data
+        st = A.lib().lodge_serve(self._h, arr, n, C.byref(opts), res)
+        if st not in (0, 1):
+            A.check(st)
+        out = []
+        for i in range(n):
+            r = res[i]
+            out.append(dict(start_s=r.start_s, finish_s=r.finish_s, status=r.status, slot=r.slot,
+                            latency_s=r.finish_s - requests[i][3], **stats_dict(r.stats)))
+        imgs = None
+        if images:
+            imgs, off = [], 0
+            for _, _, c, _ in requests:
+                k = c.width * c.height * 3
+                imgs.append(host[off:off + k].reshape(c.height, c.width, 3))
+                off += k
+        return out, imgs
+
+    def residency_stats(self) -> dict:
+        r = A.lodge_residency()
+        A.call("lodge_residency_stats", self._h, C.byref(r))
+        return {f: getattr(r, f) for f, _ in r._fields_}
+
+    def inject_upload_failures(self, n: int):
+        A.call("lodge_inject_upload_failures", self._h, int(n))
 
     def profile_enable(self, enable: bool = True):
         A.call("lodge_profile_enable", self._h, int(enable))

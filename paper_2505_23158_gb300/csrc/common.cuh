@@ -167,9 +167,18 @@ struct ProjectOut {
     uint32_t* counts;     // 8-byte aligned: [0] = visible (u32), [2..3] = keys (u64)
 };
 constexpr int kProjThreads = 256;
+// Attribute sources for streamed scenes: list entries index into chunk block
+// A (bit 31) or B, whose gid lists give the Gaussians' gids.
+struct ProjSources {
+    DevScene a, b;
+    const uint32_t* gid_a = nullptr;
+    const uint32_t* gid_b = nullptr;
+    int64_t n_a = 0, n_b = 0, npad_a = 0, npad_b = 0;
+};
 void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* list,
                     int64_t n_active, float tA, float tB, const ProjectOut& o, uint32_t* status,
-                    uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+                    uint32_t* tile_counter, uint32_t* err, cudaStream_t s,
+                    const ProjSources* src = nullptr);
 // copy the extent table to this device's constant memory (once per device)
 cudaError_t upload_qtable(const float* q65);
 

@@ -1,0 +1,172 @@
+// Host-side state of a context, shared by lodge_capi.cu (API, scenes, frame
+// orchestration), residency.cu (streamed chunk blocks) and serve.cu (the
+// request loop).
+#pragma once
+
+#include <condition_variable>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lodge {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct Chunk {
+    uint32_t* list = nullptr;  // resident: device list; streamed: pinned host list
+    int64_t n = 0;
+};
+
+// One chunk's active set resident in HBM (streamed scenes): the sorted gid
+// list and the attributes of its Gaussians as structure-of-arrays planes.
+struct Block {
+    int scene = -1, chunk = -1;
+    int64_t n = 0;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    uint32_t* gid = nullptr;
+    DevScene view;                 // planes with stride n_pad, scene level info
+    int64_t n_pad = 0;
+    int refs = 0;
+    uint64_t last_use = 0;
+    cudaEvent_t ready = nullptr;   // recorded on the upload stream after the gather
+};
+
+enum : int { kResident = 0, kStreamed = 1 };
+
+struct Scene {
+    int id = -1;
+    int residency = kResident;
+    DevScene dev;          // resident: device store; streamed: device-visible view of the host store
+    void* block = nullptr; // resident device store
+    size_t block_bytes = 0;
+    void* host_store = nullptr;  // streamed: pinned, mapped host store
+    size_t host_bytes = 0;
+    uint32_t* host_lists = nullptr;  // streamed: pinned chunk lists, back to back
+    int64_t n_pad = 0;
+    std::vector<double> d_inner;
+    std::vector<double> centers;
+    std::vector<double> radius;
+    std::vector<Chunk> chunks;
+    size_t chunk_bytes = 0;
+};
+
+struct Saved {
+    DevCamera cam{};
+    int64_t n_vis = 0, n_keys = 0;
+    DBuf rec_a, rec_b, rec_c, rec_rect, rec_gid, zsorted, rsorted, tkey, tval, ranges, T, last;
+    bool params = false;
+    int64_t n = 0;
+    const float *means = nullptr, *log_scales = nullptr, *quats = nullptr, *logits = nullptr,
+                *sh = nullptr;
+    int sh_degree = 3;
+    float filter_var = 0.f;
+    DBuf act_so, act_q;
+};
+
+struct Workspace {
+    DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
+        tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp, koff, srec,
+        srect, doffs, grec, bonly;
+    std::vector<DBuf*> all() {
+        return {&list, &marks, &status, &rec_a, &rec_b, &rec_c, &rec_rect, &rec_gid, &dkey, &dval,
+                &dkey2, &dval2, &tkey, &tval, &tkey2, &tval2, &ranges, &sort, &T, &last, &img,
+                &act_so, &act_q, &mtmp, &koff, &srec, &srect, &doffs, &grec, &bonly};
+    }
+};
+
+// small device/host words of a slot
+enum : int {
+    kSmErr = 0,
+    kSmListCount = 1,
+    kSmProj = 2,        // [2] visible, [4..5] keys (u64)
+    kSmCtrSelect = 8,
+    kSmCtrUnion = 9,
+    kSmCtrProj = 10,
+    kSmCtrEmit = 11,
+    kSmWords = 64
+};
+
+// Render state of one in-flight frame: scratch, status words, stage profile
+// and the union of the last chunk pair.  Slot 0 serves the single-threaded
+// API; the request loop adds one slot per concurrent request.
+struct Slot {
+    int index = 0;
+    cudaStream_t own = nullptr;   // stream created for this slot (request loop)
+    Workspace ws;
+    uint32_t* d_small = nullptr;
+    uint32_t* h_small = nullptr;  // pinned
+    bool prof_on = false;
+    lodge_profile prof{};
+    cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};
+    cudaEvent_t ev_end[LODGE_NUM_STAGES] = {};
+    bool ev_pending[LODGE_NUM_STAGES] = {};
+    int u_scene = -1, ua = -2, ub = -2;
+    int64_t un = 0;
+    DBuf ulist;
+    Block* held[2] = {nullptr, nullptr};
+};
+
+struct ResidencyStats {
+    int64_t hits = 0, uploads = 0, evictions = 0, upload_bytes = 0, failed_uploads = 0;
+};
+
+}  // namespace lodge
+
+struct lodge_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;                 // device bytes held; guarded by mu
+    std::recursive_mutex mu;         // budget, blocks, saved frames, slot list
+    std::condition_variable_any freed;  // signalled when device memory is released
+    std::vector<std::unique_ptr<lodge::Scene>> scenes;
+    std::vector<std::unique_ptr<lodge::Slot>> slots;
+    std::map<int64_t, std::unique_ptr<lodge::Saved>> saved;
+    int64_t next_handle = 1;
+    // streamed residency
+    std::map<std::pair<int, int>, std::unique_ptr<lodge::Block>> blocks;
+    uint64_t tick = 0;
+    cudaStream_t upload_stream = nullptr;
+    lodge::ResidencyStats res;
+    int fail_next_uploads = 0;       // host-side fault injection
+};
+
+namespace lodge {
+
+// errors (thread-local message)
+lodge_status fail(lodge_status s, const char* fmt, ...);
+
+// device memory with budget accounting (thread-safe)
+lodge_status dmalloc(lodge_ctx* ctx, void** p, size_t bytes);
+void dfree(lodge_ctx* ctx, void* p, size_t bytes);
+lodge_status ensure(lodge_ctx* ctx, DBuf& b, size_t bytes, cudaStream_t s);
+void release(lodge_ctx* ctx, DBuf& b, cudaStream_t s);
+// evict unreferenced blocks (least recently used first) until `bytes` more
+// fit in the budget; caller holds ctx->mu; returns false if they cannot
+bool make_room(lodge_ctx* ctx, size_t bytes);
+
+lodge_status sync_slot(lodge_ctx* ctx, Slot& sl, cudaStream_t s);
+const char* last_error();
+lodge_status create_slot(lodge_ctx* ctx, Slot** out);
+
+// residency (residency.cu)
+lodge_status acquire_block(lodge_ctx* ctx, Slot& sl, Scene* sc, int chunk, cudaStream_t s,
+                           Block** out);
+void release_blocks(lodge_ctx* ctx, Slot& sl);
+void free_scene_blocks(lodge_ctx* ctx, int scene);
+// union of two blocks' sorted gid lists into sl.ulist: entries are the index
+// into block A (bit 31 set) or block B (bit 30 only); bit 30 is also set on
+// A entries present in B.  b may be null (single block).
+lodge_status block_union(lodge_ctx* ctx, Slot& sl, const Block* a, const Block* b,
+                         cudaStream_t s, int64_t* n_out);
+
+}  // namespace lodge

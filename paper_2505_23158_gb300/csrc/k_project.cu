@@ -24,6 +24,7 @@ struct ProjParams {
     int64_t n_pad;          // plane stride of the SH planes
     float tA, tB;
     ProjectOut o;
+    ProjSources src;        // block sources (kBlocks only)
 };
 
 __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
@@ -65,6 +66,7 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
     Y[15] = kC3a * x * (xx - 3.f * yy);
 }
 
+template <bool kBlocks>
 __global__ void __launch_bounds__(kProjThreads)
 project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
                uint32_t* __restrict__ err) {
@@ -80,28 +82,52 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     const DevCamera& cam = P.cam;
 
     bool vis = false;
-    uint32_t g = 0;
+    uint32_t g = 0, idx = 0;
     float z = 0.f, mxp = 0.f, myp = 0.f, o = 0.f;
     float B0[3], B1[3];
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
     uint32_t rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
+    // attribute source of this entry: the scene store (indexed by gid) or a
+    // chunk block (indexed by position in the block)
+    const float* smx = sc.mx;
+    const float* smy = sc.my;
+    const float* smz = sc.mz;
+    const float4* sso = sc.scale_op;
+    const float4* sq = sc.quat;
+    const float4* ssh = sc.sh;
+    int64_t npad = P.n_pad;
     if (i < P.n_active) {
         uint32_t e = P.list ? P.list[i] : (uint32_t)i;
-        g = e & kGidMask;
+        idx = e & kGidMask;
         float mult = 1.f;
         if ((e & kFlagA) && !(e & kFlagB)) mult = P.tA;
         else if ((e & kFlagB) && !(e & kFlagA)) mult = P.tB;
-        if ((int64_t)g >= sc.n_total) { atomicOr(err, kErrBadIndex); g = 0; mult = 0.f; }
+        if (kBlocks) {
+            const bool fa = (e & kFlagA) != 0;
+            const int64_t nb = fa ? P.src.n_a : P.src.n_b;
+            if ((int64_t)idx >= nb) { atomicOr(err, kErrBadIndex); idx = 0; mult = 0.f; }
+            smx = fa ? P.src.a.mx : P.src.b.mx;
+            smy = fa ? P.src.a.my : P.src.b.my;
+            smz = fa ? P.src.a.mz : P.src.b.mz;
+            sso = fa ? P.src.a.scale_op : P.src.b.scale_op;
+            sq = fa ? P.src.a.quat : P.src.b.quat;
+            ssh = fa ? P.src.a.sh : P.src.b.sh;
+            npad = fa ? P.src.npad_a : P.src.npad_b;
+            g = (fa ? P.src.gid_a : P.src.gid_b)[idx];
+        } else {
+            if ((int64_t)idx >= sc.n_total) { atomicOr(err, kErrBadIndex); idx = 0; mult = 0.f; }
+            g = idx;
+        }
         const float* R = cam.R;
         // key spec: camera-space point relative to chat, summed left to right
-        d0 = fs(sc.mx[g], cam.chat[0]);
-        d1 = fs(sc.my[g], cam.chat[1]);
-        d2 = fs(sc.mz[g], cam.chat[2]);
+        d0 = fs(smx[idx], cam.chat[0]);
+        d1 = fs(smy[idx], cam.chat[1]);
+        d2 = fs(smz[idx], cam.chat[2]);
         float px = fa(fa(fa(fm(R[0], d0), fm(R[1], d1)), fm(R[2], d2)), cam.tp[0]);
         float py = fa(fa(fa(fm(R[3], d0), fm(R[4], d1)), fm(R[5], d2)), cam.tp[1]);
         float pz = fa(fa(fa(fm(R[6], d0), fm(R[7], d1)), fm(R[8], d2)), cam.tp[2]);
         if (pz > cam.znear) {
-            const float4 so = sc.scale_op[g];
+            const float4 so = sso[idx];
             int l = 0;
             while (l + 1 < sc.num_levels && (int64_t)g >= sc.level_off[l + 1]) ++l;
             const float v = sc.filter_var[l];
@@ -116,7 +142,7 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
             }
             if (op >= (float)(1.0 / 255.0)) {
                 const float Q = extent_q(op);
-                const float4 q = sc.quat[g];
+                const float4 q = sq[idx];
                 float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
                 float mx = fa(fm(cam.fx, u), cam.cx);
                 float my = fa(fm(cam.fy, w), cam.cy);
@@ -219,7 +245,7 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
         if (4 * j >= nf) break;
-        float4 v4 = __ldcs(sc.sh + (int64_t)j * P.n_pad + g);
+        float4 v4 = __ldcs(ssh + (int64_t)j * npad + idx);
         float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
@@ -245,7 +271,8 @@ cudaError_t upload_qtable(const float* q65) {
 
 void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* list,
                     int64_t n_active, float tA, float tB, const ProjectOut& o, uint32_t* status,
-                    uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
+                    uint32_t* tile_counter, uint32_t* err, cudaStream_t s,
+                    const ProjSources* src) {
     ProjParams P;
     P.sc = sc;
     P.cam = cam;
@@ -255,9 +282,13 @@ void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* li
     P.tA = tA;
     P.tB = tB;
     P.o = o;
+    if (src) P.src = *src;
     int64_t ntiles = (n_active + kProjThreads - 1) / kProjThreads;
     if (ntiles == 0) return;
-    project_kernel<<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
+    if (src)
+        project_kernel<true><<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
+    else
+        project_kernel<false><<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
 }
 
 }  // namespace lodge

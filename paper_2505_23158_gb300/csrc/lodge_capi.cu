@@ -6,13 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <map>
-#include <memory>
-#include <string>
 #include <thread>
-#include <vector>
 
-#include "common.cuh"
+#include "internal.cuh"
 
 namespace lodge {
 
@@ -21,7 +17,7 @@ namespace lodge {
 // ---------------------------------------------------------------------------
 static thread_local std::string g_err;
 
-static lodge_status fail(lodge_status s, const char* fmt, ...) {
+lodge_status fail(lodge_status s, const char* fmt, ...) {
     char buf[1024];
     va_list ap;
     va_start(ap, fmt);
@@ -31,11 +27,12 @@ static lodge_status fail(lodge_status s, const char* fmt, ...) {
     return s;
 }
 
-// records a message for lodge_last_error from other translation units
 lodge_status set_error(lodge_status s, const char* msg) {
     g_err = msg;
     return s;
 }
+
+const char* last_error() { return g_err.c_str(); }
 
 #define CUDA_TRY(x)                                                                          \
     do {                                                                                     \
@@ -52,100 +49,36 @@ lodge_status set_error(lodge_status s, const char* msg) {
     } while (0)
 
 // ---------------------------------------------------------------------------
-// device buffers with budget accounting
+// device memory with budget accounting
 // ---------------------------------------------------------------------------
-struct DBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-    template <class T> T* as() const { return static_cast<T*>(p); }
-};
-
-struct Chunk {
-    uint32_t* list = nullptr;
-    int64_t n = 0;
-};
-
-struct Scene {
-    DevScene dev;
-    void* block = nullptr;
-    size_t block_bytes = 0;
-    int64_t n_pad = 0;
-    std::vector<double> d_inner;
-    std::vector<double> centers;
-    std::vector<double> radius;
-    std::vector<Chunk> chunks;
-    size_t chunk_bytes = 0;
-    // union of the current chunk pair (recomputed when the pair changes)
-    int ua = -2, ub = -2;
-    DBuf ulist;
-    int64_t un = 0;
-};
-
-struct Saved {
-    DevCamera cam{};
-    int64_t n_vis = 0, n_keys = 0;
-    DBuf rec_a, rec_b, rec_c, rec_rect, rec_gid, zsorted, rsorted, tkey, tval, ranges, T, last;
-    // raw-parameter frames (fine-tuning path)
-    bool params = false;
-    int64_t n = 0;
-    const float *means = nullptr, *log_scales = nullptr, *quats = nullptr, *logits = nullptr,
-                *sh = nullptr;
-    int sh_degree = 3;
-    float filter_var = 0.f;
-    DBuf act_so, act_q;
-};
-
-struct Workspace {
-    DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
-        tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp, koff, srec,
-        srect, doffs, grec;
-};
-
-// small device/host words
-enum : int {
-    kSmErr = 0,
-    kSmListCount = 1,
-    kSmProj = 2,        // [2] visible, [4..5] keys (u64)
-    kSmCtrSelect = 8,
-    kSmCtrUnion = 9,
-    kSmCtrProj = 10,
-    kSmCtrEmit = 11,
-    kSmWords = 64
-};
-
-}  // namespace lodge
-
-using namespace lodge;
-
-struct lodge_ctx {
-    int device = 0;
-    size_t budget = 0;
-    size_t used = 0;
-    std::vector<std::unique_ptr<Scene>> scenes;
-    Workspace ws;
-    uint32_t* d_small = nullptr;
-    uint32_t* h_small = nullptr;  // pinned
-    std::map<int64_t, std::unique_ptr<Saved>> saved;
-    int64_t next_handle = 1;
-    // stage profile (CUDA events on the render stream)
-    bool prof_on = false;
-    lodge_profile prof{};
-    cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};
-    cudaEvent_t ev_end[LODGE_NUM_STAGES] = {};
-    bool ev_pending[LODGE_NUM_STAGES] = {};
-};
-
-namespace lodge {
-
-static lodge_status reserve(lodge_ctx* ctx, size_t bytes) {
-    if (ctx->budget && ctx->used + bytes > ctx->budget)
-        return fail(LODGE_E_BUDGET, "HBM budget exceeded: %zu in use + %zu requested > %zu",
-                    ctx->used, bytes, ctx->budget);
-    return LODGE_OK;
+bool make_room(lodge_ctx* ctx, size_t bytes) {
+    if (!ctx->budget) return true;
+    while (ctx->used + bytes > ctx->budget) {
+        Block* victim = nullptr;
+        std::pair<int, int> key;
+        for (auto& kv : ctx->blocks) {
+            Block* b = kv.second.get();
+            if (b->refs == 0 && (!victim || b->last_use < victim->last_use)) {
+                victim = b;
+                key = kv.first;
+            }
+        }
+        if (!victim) return false;
+        // the block is unreferenced: every frame that read it has completed
+        cudaFreeAsync(victim->mem, ctx->upload_stream);
+        if (victim->ready) cudaEventDestroy(victim->ready);
+        ctx->used -= victim->bytes;
+        ctx->res.evictions += 1;
+        ctx->blocks.erase(key);
+    }
+    return true;
 }
 
-static lodge_status dmalloc(lodge_ctx* ctx, void** p, size_t bytes) {
-    TRY(reserve(ctx, bytes));
+lodge_status dmalloc(lodge_ctx* ctx, void** p, size_t bytes) {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!make_room(ctx, bytes))
+        return fail(LODGE_E_BUDGET, "HBM budget exceeded: %zu in use + %zu requested > %zu",
+                    ctx->used, bytes, ctx->budget);
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -155,23 +88,27 @@ static lodge_status dmalloc(lodge_ctx* ctx, void** p, size_t bytes) {
     return LODGE_OK;
 }
 
-static void dfree(lodge_ctx* ctx, void* p, size_t bytes) {
-    if (p) {
-        cudaFree(p);
-        ctx->used -= bytes;
-    }
+void dfree(lodge_ctx* ctx, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->used -= bytes;
+    ctx->freed.notify_all();
 }
 
 // grow-only, stream-ordered
-static lodge_status ensure(lodge_ctx* ctx, DBuf& b, size_t bytes, cudaStream_t s) {
+lodge_status ensure(lodge_ctx* ctx, DBuf& b, size_t bytes, cudaStream_t s) {
     if (bytes <= b.cap && b.p) return LODGE_OK;
     size_t ncap = std::max<size_t>(bytes + bytes / 4, 4096);
     ncap = (ncap + 255) / 256 * 256;
-    size_t freed = b.p ? b.cap : 0;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    const size_t freed = b.p ? b.cap : 0;
     if (ctx->budget && ctx->used - freed + ncap > ctx->budget) {
-        ncap = (bytes + 255) / 256 * 256;
-        if (ctx->used - freed + ncap > ctx->budget)
-            return fail(LODGE_E_BUDGET, "HBM budget exceeded growing scratch to %zu bytes", ncap);
+        if (!make_room(ctx, ncap > freed ? ncap - freed : 0)) {
+            ncap = (bytes + 255) / 256 * 256;
+            if (!make_room(ctx, ncap > freed ? ncap - freed : 0))
+                return fail(LODGE_E_BUDGET, "HBM budget exceeded growing scratch to %zu bytes", ncap);
+        }
     }
     if (b.p) {
         cudaFreeAsync(b.p, s);
@@ -190,34 +127,69 @@ static lodge_status ensure(lodge_ctx* ctx, DBuf& b, size_t bytes, cudaStream_t s
     return LODGE_OK;
 }
 
-static void release(lodge_ctx* ctx, DBuf& b, cudaStream_t s) {
+void release(lodge_ctx* ctx, DBuf& b, cudaStream_t s) {
     if (b.p) {
         cudaFreeAsync(b.p, s);
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
         ctx->used -= b.cap;
+        ctx->freed.notify_all();
     }
     b.p = nullptr;
     b.cap = 0;
 }
 
 // stage profiling: events around each stage, read after the next sync
-static void prof_begin(lodge_ctx* ctx, int stage, cudaStream_t s) {
-    if (ctx->prof_on && !ctx->ev_pending[stage]) cudaEventRecord(ctx->ev_beg[stage], s);
+static void prof_begin(Slot& sl, int stage, cudaStream_t s) {
+    if (sl.prof_on && !sl.ev_pending[stage]) cudaEventRecord(sl.ev_beg[stage], s);
 }
-static void prof_end(lodge_ctx* ctx, int stage, cudaStream_t s, int launches) {
-    ctx->prof.launches[stage] += launches;
-    if (ctx->prof_on && !ctx->ev_pending[stage]) {
-        cudaEventRecord(ctx->ev_end[stage], s);
-        ctx->ev_pending[stage] = true;
+static void prof_end(Slot& sl, int stage, cudaStream_t s, int launches) {
+    sl.prof.launches[stage] += launches;
+    if (sl.prof_on && !sl.ev_pending[stage]) {
+        cudaEventRecord(sl.ev_end[stage], s);
+        sl.ev_pending[stage] = true;
     }
 }
-static void prof_collect(lodge_ctx* ctx) {
+static void prof_collect(Slot& sl) {
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
-        if (!ctx->ev_pending[k]) continue;
+        if (!sl.ev_pending[k]) continue;
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev_beg[k], ctx->ev_end[k]) == cudaSuccess) ctx->prof.ms[k] += ms;
+        if (cudaEventElapsedTime(&ms, sl.ev_beg[k], sl.ev_end[k]) == cudaSuccess) sl.prof.ms[k] += ms;
         else cudaGetLastError();
-        ctx->ev_pending[k] = false;
+        sl.ev_pending[k] = false;
     }
+}
+
+lodge_status create_slot(lodge_ctx* ctx, Slot** out) {
+    std::unique_ptr<Slot> sl(new Slot());
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        sl->index = (int)ctx->slots.size();
+    }
+    TRY(dmalloc(ctx, (void**)&sl->d_small, sizeof(uint32_t) * kSmWords));
+    CUDA_TRY(cudaMemset(sl->d_small, 0, sizeof(uint32_t) * kSmWords));
+    CUDA_TRY(cudaMallocHost((void**)&sl->h_small, sizeof(uint32_t) * kSmWords));
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
+        CUDA_TRY(cudaEventCreate(&sl->ev_beg[k]));
+        CUDA_TRY(cudaEventCreate(&sl->ev_end[k]));
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    *out = sl.get();
+    ctx->slots.emplace_back(std::move(sl));
+    return LODGE_OK;
+}
+
+static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
+    for (DBuf* b : sl.ws.all())
+        if (b->p) cudaFree(b->p);
+    if (sl.ulist.p) cudaFree(sl.ulist.p);
+    if (sl.d_small) cudaFree(sl.d_small);
+    if (sl.h_small) cudaFreeHost(sl.h_small);
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
+        if (sl.ev_beg[k]) cudaEventDestroy(sl.ev_beg[k]);
+        if (sl.ev_end[k]) cudaEventDestroy(sl.ev_end[k]);
+    }
+    if (sl.own) cudaStreamDestroy(sl.own);
+    (void)ctx;
 }
 
 // ---------------------------------------------------------------------------
@@ -327,12 +299,13 @@ static Scene* get_scene(lodge_ctx* ctx, int32_t id) {
     return ctx->scenes[id].get();
 }
 
-static lodge_status sync_small(lodge_ctx* ctx, cudaStream_t s) {
-    CUDA_TRY(cudaMemcpyAsync(ctx->h_small, ctx->d_small, sizeof(uint32_t) * kSmWords,
+lodge_status sync_slot(lodge_ctx* ctx, Slot& sl, cudaStream_t s) {
+    (void)ctx;
+    CUDA_TRY(cudaMemcpyAsync(sl.h_small, sl.d_small, sizeof(uint32_t) * kSmWords,
                              cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    prof_collect(ctx);
-    uint32_t err = ctx->h_small[kSmErr];
+    prof_collect(sl);
+    uint32_t err = sl.h_small[kSmErr];
     if (err & kErrTimeout) return fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
     if (err & kErrOverflow) return fail(LODGE_E_OVERFLOW, "device output capacity exceeded (status 0x%x)", err);
     if (err & kErrBadIndex) return fail(LODGE_E_INVALID, "out-of-range index in an active list (status 0x%x)", err);
@@ -342,25 +315,26 @@ static lodge_status sync_small(lodge_ctx* ctx, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // selection
 // ---------------------------------------------------------------------------
-// Eq. 2 at centre c with inner thresholds d into ctx->ws.list; returns count.
-static lodge_status run_lod_select(lodge_ctx* ctx, Scene* sc, const double* c, const double* d,
-                                   cudaStream_t s, int64_t* n_out) {
-    Workspace& ws = ctx->ws;
+// Eq. 2 at centre c with inner thresholds d over the device store `dev` into
+// the slot's list; returns count.
+static lodge_status run_lod_select(lodge_ctx* ctx, Slot& sl, const DevScene& dev, const double* c,
+                                   const double* d, cudaStream_t s, int64_t* n_out) {
+    Workspace& ws = sl.ws;
     float lo[kMaxLevels], hi[kMaxLevels];
-    bands(sc->dev.num_levels, d, lo, hi);
+    bands(dev.num_levels, d, lo, hi);
     float c32[3] = {(float)c[0], (float)c[1], (float)c[2]};
-    int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
-    TRY(ensure(ctx, ws.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(sc->dev.n_total, 1), s));
+    int64_t ntiles = (dev.n_total + kSelectTile - 1) / kSelectTile;
+    TRY(ensure(ctx, ws.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(dev.n_total, 1), s));
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
-    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
-    prof_begin(ctx, LODGE_STAGE_SELECT, s);
-    launch_lod_select(sc->dev, c32, lo, hi, ws.list.as<uint32_t>(), ctx->d_small + kSmListCount,
-                      ws.status.as<uint32_t>(), ctx->d_small + kSmCtrSelect, ctx->d_small + kSmErr, s);
-    prof_end(ctx, LODGE_STAGE_SELECT, s, ntiles > 0 ? 1 : 0);
+    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    prof_begin(sl, LODGE_STAGE_SELECT, s);
+    launch_lod_select(dev, c32, lo, hi, ws.list.as<uint32_t>(), sl.d_small + kSmListCount,
+                      ws.status.as<uint32_t>(), sl.d_small + kSmCtrSelect, sl.d_small + kSmErr, s);
+    prof_end(sl, LODGE_STAGE_SELECT, s, ntiles > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
-    TRY(sync_small(ctx, s));
-    *n_out = ctx->h_small[kSmListCount];
+    TRY(sync_slot(ctx, sl, s));
+    *n_out = sl.h_small[kSmListCount];
     return LODGE_OK;
 }
 
@@ -369,57 +343,102 @@ struct Active {
     int64_t n = 0;
     int A = -1, B = -1;
     double tA = 1.0, tB = 1.0;
+    bool blocks = false;       // entries index into chunk blocks (streamed scenes)
+    ProjSources src;
 };
 
-static lodge_status select_active(lodge_ctx* ctx, Scene* sc, lodge_mode mode, const lodge_camera& cam,
-                                  cudaStream_t s, Active* act) {
+static lodge_status select_streamed(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
+                                    cudaStream_t s, Active* act) {
+    const bool single = (mode == LODGE_CHUNK || act->B < 0);
+    if (single) { act->B = -1; if (mode == LODGE_CHUNK) act->tA = act->tB = 1.0; }
+    Block* a = nullptr;
+    Block* b = nullptr;
+    TRY(acquire_block(ctx, sl, sc, act->A, s, &a));
+    sl.held[0] = a;
+    if (!single) {
+        TRY(acquire_block(ctx, sl, sc, act->B, s, &b));
+        sl.held[1] = b;
+    }
+    if (sl.u_scene != sc->id || sl.ua != act->A || sl.ub != act->B) {
+        int64_t n;
+        sl.u_scene = -1;
+        prof_begin(sl, LODGE_STAGE_UNION, s);
+        TRY(block_union(ctx, sl, a, b, s, &n));
+        prof_end(sl, LODGE_STAGE_UNION, s, b ? 5 : 1);
+        sl.un = n;
+        sl.u_scene = sc->id;
+        sl.ua = act->A;
+        sl.ub = act->B;
+    }
+    act->list = sl.ulist.as<uint32_t>();
+    act->n = sl.un;
+    act->blocks = true;
+    act->src.a = a->view;
+    act->src.gid_a = a->gid;
+    act->src.n_a = a->n;
+    act->src.npad_a = a->n_pad;
+    const Block* bb = b ? b : a;
+    act->src.b = bb->view;
+    act->src.gid_b = bb->gid;
+    act->src.n_b = bb->n;
+    act->src.npad_b = bb->n_pad;
+    return LODGE_OK;
+}
+
+static lodge_status select_active(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
+                                  const lodge_camera& cam, cudaStream_t s, Active* act) {
     *act = Active{};
+    if (mode != LODGE_FULL && mode != LODGE_LOD && mode != LODGE_CHUNK && mode != LODGE_CHUNK_BLEND)
+        return fail(LODGE_E_INVALID, "unknown render mode %d", (int)mode);
+    if (sc->residency == kStreamed && (mode == LODGE_FULL || mode == LODGE_LOD))
+        return fail(LODGE_E_NOT_RESIDENT,
+                    "scene %d is streamed by chunk: only CHUNK and CHUNK_BLEND can render it", sc->id);
     if (mode == LODGE_FULL) {
         act->n = sc->dev.level_off[1];
         return LODGE_OK;
     }
     if (mode == LODGE_LOD) {
         int64_t n;
-        TRY(run_lod_select(ctx, sc, cam.center, sc->d_inner.data(), s, &n));
-        act->list = ctx->ws.list.as<uint32_t>();
+        TRY(run_lod_select(ctx, sl, sc->dev, cam.center, sc->d_inner.data(), s, &n));
+        act->list = sl.ws.list.as<uint32_t>();
         act->n = n;
         return LODGE_OK;
     }
-    if (mode != LODGE_CHUNK && mode != LODGE_CHUNK_BLEND)
-        return fail(LODGE_E_INVALID, "unknown render mode %d", (int)mode);
     if (sc->chunks.empty()) return fail(LODGE_E_INVALID, "scene has no chunks");
     chunk_pick(sc->centers, cam.center, &act->A, &act->B, &act->tA, &act->tB);
+    if (sc->residency == kStreamed) return select_streamed(ctx, sl, sc, mode, s, act);
     if (mode == LODGE_CHUNK || act->B < 0) {
         act->list = sc->chunks[act->A].list;
         act->n = sc->chunks[act->A].n;
         if (mode == LODGE_CHUNK) { act->B = -1; act->tA = act->tB = 1.0; }
         return LODGE_OK;
     }
-    if (sc->ua != act->A || sc->ub != act->B) {
+    if (sl.u_scene != sc->id || sl.ua != act->A || sl.ub != act->B) {
         const Chunk& a = sc->chunks[act->A];
         const Chunk& b = sc->chunks[act->B];
-        Workspace& ws = ctx->ws;
+        Workspace& ws = sl.ws;
         int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
-        TRY(ensure(ctx, sc->ulist, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
+        TRY(ensure(ctx, sl.ulist, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
         TRY(ensure(ctx, ws.marks, (size_t)((sc->dev.n_total + 63) / 64 * 64), s));
         TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
         CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
-        CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
-        prof_begin(ctx, LODGE_STAGE_UNION, s);
+        CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
+        prof_begin(sl, LODGE_STAGE_UNION, s);
         launch_chunk_union(a.list, a.n, b.list, b.n, sc->dev.n_total, ws.marks.as<uint8_t>(),
-                           sc->ulist.as<uint32_t>(), ctx->d_small + kSmListCount,
-                           ws.status.as<uint32_t>(), ctx->d_small + kSmCtrUnion,
-                           ctx->d_small + kSmErr, s);
-        prof_end(ctx, LODGE_STAGE_UNION, s, (a.n > 0) + (b.n > 0) + (ntiles > 0));
+                           sl.ulist.as<uint32_t>(), sl.d_small + kSmListCount,
+                           ws.status.as<uint32_t>(), sl.d_small + kSmCtrUnion,
+                           sl.d_small + kSmErr, s);
+        prof_end(sl, LODGE_STAGE_UNION, s, (a.n > 0) + (b.n > 0) + (ntiles > 0));
         CUDA_TRY(cudaGetLastError());
-        sc->ua = -2;
-        TRY(sync_small(ctx, s));
-        sc->un = ctx->h_small[kSmListCount];
-        sc->ua = act->A;
-        sc->ub = act->B;
+        sl.u_scene = -1;
+        TRY(sync_slot(ctx, sl, s));
+        sl.un = sl.h_small[kSmListCount];
+        sl.u_scene = sc->id;
+        sl.ua = act->A;
+        sl.ub = act->B;
     }
-    act->list = sc->ulist.as<uint32_t>();
-    act->n = sc->un;
+    act->list = sl.ulist.as<uint32_t>();
+    act->n = sl.un;
     return LODGE_OK;
 }
 
@@ -428,10 +447,10 @@ static lodge_status select_active(lodge_ctx* ctx, Scene* sc, lodge_mode mode, co
 // ---------------------------------------------------------------------------
 static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
 
-static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Active& act,
+static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, const Active& act,
                                  const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
                                  lodge_frame_stats* st) {
-    Workspace& ws = ctx->ws;
+    Workspace& ws = sl.ws;
     TRY(check_cam(c));
     DevCamera cam = make_cam(c);
     const int64_t ntiles_img = (int64_t)cam.tiles_x * cam.tiles_y;
@@ -450,7 +469,7 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     int64_t ptiles = std::max<int64_t>((na + kProjThreads - 1) / kProjThreads, 1);
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)ptiles, s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)ptiles, s));
-    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
     ProjectOut po;
     po.rec_a = ws.rec_a.as<float4>();
     po.rec_b = ws.rec_b.as<float4>();
@@ -459,16 +478,17 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     po.rec_gid = ws.rec_gid.as<uint32_t>();
     po.depth_key = ws.dkey.as<uint32_t>();
     po.depth_val = ws.dval.as<uint32_t>();
-    po.counts = ctx->d_small + kSmProj;
-    prof_begin(ctx, LODGE_STAGE_PROJECT, s);
+    po.counts = sl.d_small + kSmProj;
+    prof_begin(sl, LODGE_STAGE_PROJECT, s);
     launch_project(dsc, cam, act.list, na, (float)act.tA, (float)act.tB, po,
-                   ws.status.as<uint32_t>(), ctx->d_small + kSmCtrProj, ctx->d_small + kSmErr, s);
-    prof_end(ctx, LODGE_STAGE_PROJECT, s, na > 0 ? 1 : 0);
+                   ws.status.as<uint32_t>(), sl.d_small + kSmCtrProj, sl.d_small + kSmErr, s,
+                   act.blocks ? &act.src : nullptr);
+    prof_end(sl, LODGE_STAGE_PROJECT, s, na > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
-    TRY(sync_small(ctx, s));
-    const int64_t n_vis = ctx->h_small[kSmProj];
+    TRY(sync_slot(ctx, sl, s));
+    const int64_t n_vis = sl.h_small[kSmProj];
     uint64_t nk64;
-    std::memcpy(&nk64, ctx->h_small + kSmProj + 2, 8);
+    std::memcpy(&nk64, sl.h_small + kSmProj + 2, 8);
     const int64_t n_keys = (int64_t)nk64;
     if (n_keys >= (1ll << 30)) return fail(LODGE_E_OVERFLOW, "%lld tile keys exceed 2^30", (long long)n_keys);
     const size_t nv1 = (size_t)std::max<int64_t>(n_vis, 1), nk1 = (size_t)std::max<int64_t>(n_keys, 1);
@@ -478,14 +498,14 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     TRY(ensure(ctx, ws.dval2, sizeof(uint32_t) * nv1, s));
     const int tbits = bits_for((uint32_t)(ntiles_img - 1));
     TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_keys, tbits)), s));
-    prof_begin(ctx, LODGE_STAGE_DEPTH_SORT, s);
+    prof_begin(sl, LODGE_STAGE_DEPTH_SORT, s);
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
-                             ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, ctx->d_small + kSmErr, s);
-    prof_end(ctx, LODGE_STAGE_DEPTH_SORT, s, onesweep_launches(n_vis, 32, false));
+                             ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s);
+    prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, onesweep_launches(n_vis, 32, false));
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
 
-    // ---- K4 emit (tile, record) in depth order
+    // ---- K4 emit (tile, record) in depth order, with the tile sort's digit counts
     TRY(ensure(ctx, ws.tkey, sizeof(uint32_t) * nk1, s));
     TRY(ensure(ctx, ws.tval, sizeof(uint32_t) * nk1, s));
     TRY(ensure(ctx, ws.tkey2, sizeof(uint32_t) * nk1, s));
@@ -498,28 +518,28 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     int64_t etiles = std::max<int64_t>((n_vis + kEmitThreads - 1) / kEmitThreads, 1);
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
-    prof_begin(ctx, LODGE_STAGE_EMIT, s);
+    prof_begin(sl, LODGE_STAGE_EMIT, s);
     launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), cam.tiles_x, cam.tiles_y,
                 ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_keys,
                 ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), tbits, ws.doffs.as<uint32_t>(),
-                ws.status.as<uint32_t>(), ctx->d_small + kSmCtrEmit, ctx->d_small + kSmErr, s);
-    prof_end(ctx, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_keys > 0 ? 2 : 0));
+                ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
+    prof_end(sl, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_keys > 0 ? 2 : 0));
 
     // ---- K5 tile sort (stable: keeps depth order within a tile)
-    prof_begin(ctx, LODGE_STAGE_TILE_SORT, s);
+    prof_begin(sl, LODGE_STAGE_TILE_SORT, s);
     int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), ws.tkey2.as<uint32_t>(),
-                             ws.tval2.as<uint32_t>(), n_keys, tbits, ws.sort.p, ctx->d_small + kSmErr, s,
+                             ws.tval2.as<uint32_t>(), n_keys, tbits, ws.sort.p, sl.d_small + kSmErr, s,
                              ws.doffs.as<uint32_t>(), true);
-    prof_end(ctx, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_keys, tbits, true));
+    prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_keys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
 
     // ---- K6 ranges, K7 blend
     TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
     CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
-    prof_begin(ctx, LODGE_STAGE_RANGES, s);
+    prof_begin(sl, LODGE_STAGE_RANGES, s);
     launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, s);
-    prof_end(ctx, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
+    prof_end(sl, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
     BlendOut bo{d_rgb, nullptr, nullptr};
     if (save) {
         const size_t npix = (size_t)c.width * c.height;
@@ -528,17 +548,17 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
         bo.T_final = ws.T.as<float>();
         bo.last = ws.last.as<uint32_t>();
     }
-    prof_begin(ctx, LODGE_STAGE_BLEND, s);
+    prof_begin(sl, LODGE_STAGE_BLEND, s);
     launch_blend(cam, ws.ranges.as<uint2>(), vs.as<uint32_t>(), n_keys, ws.rec_a.as<float4>(),
                  ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
-    prof_end(ctx, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? 1 : 0);
+    prof_end(sl, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
-    TRY(sync_small(ctx, s));
+    TRY(sync_slot(ctx, sl, s));
 
-    ctx->prof.frames += 1;
-    ctx->prof.keys += n_keys;
-    ctx->prof.visible += n_vis;
-    ctx->prof.active += na;
+    sl.prof.frames += 1;
+    sl.prof.keys += n_keys;
+    sl.prof.visible += n_vis;
+    sl.prof.active += na;
     if (st) {
         st->n_active = na;
         st->n_visible = n_vis;
@@ -569,6 +589,21 @@ static lodge_status render_frame(lodge_ctx* ctx, const DevScene& dsc, const Acti
     return LODGE_OK;
 }
 
+// Select and render one camera of a scene on a slot; blocks of streamed
+// scenes are held for the frame and released after it.
+lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
+                        const lodge_camera& cam, float* d_rgb, cudaStream_t s, Saved* save,
+                        lodge_frame_stats* st) {
+    Active act;
+    lodge_status r = select_active(ctx, sl, sc, mode, cam, s, &act);
+    if (r == LODGE_OK) r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st);
+    if (sc->residency == kStreamed) {
+        if (r != LODGE_OK) cudaStreamSynchronize(s);
+        release_blocks(ctx, sl);
+    }
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // small kernels of the host API
 // ---------------------------------------------------------------------------
@@ -577,14 +612,24 @@ __global__ void iota_kernel(uint32_t* out, int64_t n) {
     if (i < n) out[i] = (uint32_t)i;
 }
 
+// gids of block-indexed union entries, flags kept
+__global__ void block_gid_kernel(const uint32_t* list, int64_t n, const uint32_t* gid_a,
+                                 const uint32_t* gid_b, uint32_t flag_mask, uint32_t* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t e = list[i];
+    const uint32_t g = ((e & kFlagA) ? gid_a : gid_b)[e & kGidMask];
+    out[i] = g | (e & flag_mask);
+}
+
 __global__ void zrec_kernel(const uint32_t* zsorted, const uint32_t* rsorted, int64_t n, uint32_t* zrec) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && (int64_t)rsorted[i] < n) zrec[rsorted[i]] = zsorted[i];
 }
 
 __global__ void debug_keys_kernel(const uint32_t* tkey, const uint32_t* tval, int64_t n,
-                                  int64_t n_rec, const uint32_t* zrec, const uint32_t* gid, uint64_t* keys,
-                                  uint32_t* gids) {
+                                  int64_t n_rec, const uint32_t* zrec, const uint32_t* gid,
+                                  uint64_t* keys, uint32_t* gids) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t r = tval[i];
@@ -649,14 +694,120 @@ __global__ void planes_kernel(int64_t n, const float* means, float* mx, float* m
     mx[i] = means[3 * i]; my[i] = means[3 * i + 1]; mz[i] = means[3 * i + 2];
 }
 
+static void free_saved(lodge_ctx* ctx, Saved& v, bool sync_free) {
+    for (DBuf* b : {&v.rec_a, &v.rec_b, &v.rec_c, &v.rec_rect, &v.rec_gid, &v.zsorted, &v.rsorted,
+                    &v.tkey, &v.tval, &v.ranges, &v.T, &v.last, &v.act_so, &v.act_q}) {
+        if (sync_free) { if (b->p) cudaFree(b->p); *b = DBuf{}; }
+        else release(ctx, *b, 0);
+    }
+}
+
+// Fill the structure-of-arrays store of a scene (activated in FP64, rounded
+// once) at `dst` (device or pinned host), plane stride NP.
+static lodge_status fill_store(const lodge_scene_desc* desc, const DevScene& d, int64_t NP,
+                               float* dst, bool dst_is_host) {
+    const int L = desc->num_levels;
+    auto put = [&](void* to, const void* from, size_t bytes) -> cudaError_t {
+        if (dst_is_host) { std::memcpy(to, from, bytes); return cudaSuccess; }
+        return cudaMemcpy(to, from, bytes, cudaMemcpyHostToDevice);
+    };
+    std::vector<float> plane;
+    std::vector<float4> plane4;
+    if (!dst_is_host) {
+        plane.assign((size_t)NP, 0.f);
+        plane4.assign((size_t)NP, make_float4(0, 0, 0, 0));
+    }
+    for (int axis = 0; axis < 3; ++axis) {
+        float* out = dst_is_host ? dst + axis * NP : plane.data();
+        for (int l = 0; l < L; ++l) {
+            const lodge_level_desc& lv = desc->levels[l];
+            const int64_t o = d.level_off[l];
+            parallel_for(lv.n, [&](int64_t a, int64_t b) {
+                for (int64_t i = a; i < b; ++i) out[o + i] = lv.means[3 * i + axis];
+            });
+        }
+        if (!dst_is_host) CUDA_TRY(put(dst + axis * NP, plane.data(), sizeof(float) * NP));
+    }
+    float4* f4 = reinterpret_cast<float4*>(dst + 3 * NP);
+    float4* out4 = dst_is_host ? f4 : plane4.data();
+    for (int l = 0; l < L; ++l) {
+        const lodge_level_desc& lv = desc->levels[l];
+        const int64_t o = d.level_off[l];
+        parallel_for(lv.n, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; ++i) {
+                float s0 = (float)std::exp((double)lv.log_scales[3 * i]);
+                float s1 = (float)std::exp((double)lv.log_scales[3 * i + 1]);
+                float s2 = (float)std::exp((double)lv.log_scales[3 * i + 2]);
+                float op = (float)(1.0 / (1.0 + std::exp(-(double)lv.opacity_logits[i])));
+                out4[o + i] = make_float4(s0, s1, s2, op);
+            }
+        });
+    }
+    if (!dst_is_host) CUDA_TRY(put(f4, plane4.data(), sizeof(float4) * NP));
+    out4 = dst_is_host ? f4 + NP : plane4.data();
+    for (int l = 0; l < L; ++l) {
+        const lodge_level_desc& lv = desc->levels[l];
+        const int64_t o = d.level_off[l];
+        parallel_for(lv.n, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; ++i) {
+                double w = lv.quats[4 * i], x = lv.quats[4 * i + 1], y = lv.quats[4 * i + 2], z = lv.quats[4 * i + 3];
+                double nrm = std::sqrt(((w * w + x * x) + y * y) + z * z);
+                out4[o + i] = make_float4((float)(w / nrm), (float)(x / nrm), (float)(y / nrm), (float)(z / nrm));
+            }
+        });
+    }
+    if (!dst_is_host) CUDA_TRY(put(f4 + NP, plane4.data(), sizeof(float4) * NP));
+    for (int j = 0; j < 12; ++j) {
+        out4 = dst_is_host ? f4 + (size_t)(2 + j) * NP : plane4.data();
+        for (int l = 0; l < L; ++l) {
+            const lodge_level_desc& lv = desc->levels[l];
+            const int64_t o = d.level_off[l];
+            parallel_for(lv.n, [&](int64_t a, int64_t b) {
+                for (int64_t i = a; i < b; ++i) {
+                    const float* p = lv.sh + 48 * i + 4 * j;
+                    out4[o + i] = make_float4(p[0], p[1], p[2], p[3]);
+                }
+            });
+        }
+        if (!dst_is_host) CUDA_TRY(put(f4 + (size_t)(2 + j) * NP, plane4.data(), sizeof(float4) * NP));
+    }
+    return LODGE_OK;
+}
+
+static void point_store(DevScene& d, float* base, int64_t NP) {
+    d.mx = base;
+    d.my = base + NP;
+    d.mz = base + 2 * NP;
+    float4* f4 = reinterpret_cast<float4*>(base + 3 * NP);
+    d.scale_op = f4;
+    d.quat = f4 + NP;
+    d.sh = f4 + 2 * NP;
+}
+
+static void free_scene(lodge_ctx* ctx, Scene& sc) {
+    free_scene_blocks(ctx, sc.id);
+    if (sc.block) dfree(ctx, sc.block, sc.block_bytes);
+    sc.block = nullptr;
+    if (sc.host_store) cudaFreeHost(sc.host_store);
+    sc.host_store = nullptr;
+    if (sc.host_lists) cudaFreeHost(sc.host_lists);
+    sc.host_lists = nullptr;
+    if (sc.residency == kResident)
+        for (auto& ch : sc.chunks)
+            if (ch.list) dfree(ctx, ch.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(ch.n, 1));
+    sc.chunks.clear();
+}
+
 }  // namespace lodge
+
+using namespace lodge;
 
 // ===========================================================================
 // extern "C"
 // ===========================================================================
 extern "C" {
 
-const char* lodge_last_error(void) { return lodge::g_err.c_str(); }
+const char* lodge_last_error(void) { return lodge::last_error(); }
 
 lodge_status lodge_create(int device, size_t hbm_budget_bytes, lodge_ctx** out) {
     if (!out) return fail(LODGE_E_INVALID, "out is NULL");
@@ -671,13 +822,9 @@ lodge_status lodge_create(int device, size_t hbm_budget_bytes, lodge_ctx** out) 
     float q[65];
     fill_qtable_host(q);
     CUDA_TRY(upload_qtable(q));
-    TRY(dmalloc(ctx.get(), (void**)&ctx->d_small, sizeof(uint32_t) * kSmWords));
-    CUDA_TRY(cudaMemset(ctx->d_small, 0, sizeof(uint32_t) * kSmWords));
-    CUDA_TRY(cudaMallocHost((void**)&ctx->h_small, sizeof(uint32_t) * kSmWords));
-    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
-        CUDA_TRY(cudaEventCreate(&ctx->ev_beg[k]));
-        CUDA_TRY(cudaEventCreate(&ctx->ev_end[k]));
-    }
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->upload_stream, cudaStreamNonBlocking));
+    Slot* s0 = nullptr;
+    TRY(create_slot(ctx.get(), &s0));
     *out = ctx.release();
     return LODGE_OK;
 }
@@ -686,30 +833,12 @@ lodge_status lodge_destroy(lodge_ctx* ctx) {
     if (!ctx) return LODGE_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (auto& kv : ctx->saved) {
-        Saved& v = *kv.second;
-        for (DBuf* b : {&v.rec_a, &v.rec_b, &v.rec_c, &v.rec_rect, &v.rec_gid, &v.zsorted, &v.rsorted,
-                        &v.tkey, &v.tval, &v.ranges, &v.T, &v.last, &v.act_so, &v.act_q})
-            if (b->p) cudaFree(b->p);
-    }
-    for (auto& sp : ctx->scenes) {
-        if (!sp) continue;
-        if (sp->block) cudaFree(sp->block);
-        for (auto& ch : sp->chunks) if (ch.list) cudaFree(ch.list);
-        if (sp->ulist.p) cudaFree(sp->ulist.p);
-    }
-    Workspace& w = ctx->ws;
-    for (DBuf* b : {&w.list, &w.marks, &w.status, &w.rec_a, &w.rec_b, &w.rec_c, &w.rec_rect, &w.rec_gid,
-                    &w.dkey, &w.dval, &w.dkey2, &w.dval2, &w.tkey, &w.tval, &w.tkey2, &w.tval2,
-                    &w.ranges, &w.sort, &w.T, &w.last, &w.img, &w.act_so, &w.act_q, &w.mtmp, &w.koff,
-                    &w.srec, &w.srect, &w.doffs, &w.grec})
-        if (b->p) cudaFree(b->p);
-    if (ctx->d_small) cudaFree(ctx->d_small);
-    if (ctx->h_small) cudaFreeHost(ctx->h_small);
-    for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
-        if (ctx->ev_beg[k]) cudaEventDestroy(ctx->ev_beg[k]);
-        if (ctx->ev_end[k]) cudaEventDestroy(ctx->ev_end[k]);
-    }
+    for (auto& kv : ctx->saved) free_saved(ctx, *kv.second, true);
+    ctx->saved.clear();
+    for (auto& sp : ctx->scenes)
+        if (sp) free_scene(ctx, *sp);
+    for (auto& sl : ctx->slots) destroy_slot(ctx, *sl);
+    if (ctx->upload_stream) cudaStreamDestroy(ctx->upload_stream);
     cudaDeviceSynchronize();
     delete ctx;
     return LODGE_OK;
@@ -727,8 +856,13 @@ lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int3
             return fail(LODGE_E_INVALID, "d_thresholds must be ascending");
     if (desc->num_chunks < 0 || (desc->num_chunks > 0 && !desc->chunk_centers))
         return fail(LODGE_E_INVALID, "bad chunk centres");
+    if (desc->residency != kResident && desc->residency != kStreamed)
+        return fail(LODGE_E_INVALID, "unknown residency %d", desc->residency);
+    if (desc->residency == kStreamed && desc->num_chunks < 1)
+        return fail(LODGE_E_INVALID, "a streamed scene needs chunk centres");
     CUDA_TRY(cudaSetDevice(ctx->device));
     std::unique_ptr<Scene> sc(new Scene());
+    sc->residency = desc->residency;
     DevScene& d = sc->dev;
     d.num_levels = L;
     d.sh_degree = desc->sh_degree;
@@ -747,74 +881,34 @@ lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int3
     d.n_total = N;
     const int64_t NP = std::max<int64_t>((N + 63) / 64 * 64, 64);
     sc->n_pad = NP;
-    // one allocation: 3 mean planes, scale_op, quat, 12 SH planes
+    // store: 3 mean planes, scale_op, quat, 12 SH planes
     const size_t bytes = sizeof(float) * 3 * NP + sizeof(float4) * (2 + 12) * NP;
-    TRY(dmalloc(ctx, &sc->block, bytes));
-    sc->block_bytes = bytes;
-    float* base = static_cast<float*>(sc->block);
-    d.mx = base;
-    d.my = base + NP;
-    d.mz = base + 2 * NP;
-    float4* f4 = reinterpret_cast<float4*>(base + 3 * NP);
-    d.scale_op = f4;
-    d.quat = f4 + NP;
-    d.sh = f4 + 2 * NP;
-
-    // host staging, one plane at a time (pageable)
-    std::vector<float> plane((size_t)NP, 0.f);
-    std::vector<float4> plane4((size_t)NP, make_float4(0, 0, 0, 0));
-    for (int axis = 0; axis < 3; ++axis) {
-        for (int l = 0; l < L; ++l) {
-            const lodge_level_desc& lv = desc->levels[l];
-            const int64_t o = d.level_off[l];
-            parallel_for(lv.n, [&](int64_t a, int64_t b) {
-                for (int64_t i = a; i < b; ++i) plane[o + i] = lv.means[3 * i + axis];
-            });
+    Slot& sl = *ctx->slots[0];
+    cudaStream_t s = 0;
+    void* means_tmp = nullptr;   // streamed: device copy of the mean planes for the precompute
+    size_t means_tmp_bytes = 0;
+    if (sc->residency == kResident) {
+        TRY(dmalloc(ctx, &sc->block, bytes));
+        sc->block_bytes = bytes;
+        point_store(d, static_cast<float*>(sc->block), NP);
+        lodge_status r = fill_store(desc, d, NP, static_cast<float*>(sc->block), false);
+        if (r != LODGE_OK) { dfree(ctx, sc->block, bytes); return r; }
+    } else {
+        cudaError_t e = cudaHostAlloc(&sc->host_store, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LODGE_E_OOM, "pinned host store of %zu bytes: %s", bytes, cudaGetErrorString(e));
         }
-        CUDA_TRY(cudaMemcpy(base + axis * NP, plane.data(), sizeof(float) * NP, cudaMemcpyHostToDevice));
+        sc->host_bytes = bytes;
+        lodge_status r = fill_store(desc, d, NP, static_cast<float*>(sc->host_store), true);
+        if (r != LODGE_OK) { cudaFreeHost(sc->host_store); return r; }
+        void* dview = nullptr;
+        CUDA_TRY(cudaHostGetDevicePointer(&dview, sc->host_store, 0));
+        point_store(d, static_cast<float*>(dview), NP);
+        means_tmp_bytes = sizeof(float) * 3 * NP;
+        TRY(dmalloc(ctx, &means_tmp, means_tmp_bytes));
+        CUDA_TRY(cudaMemcpy(means_tmp, sc->host_store, means_tmp_bytes, cudaMemcpyHostToDevice));
     }
-    // activation in FP64, rounded once: scale = exp, opacity = sigmoid, unit quaternion
-    for (int l = 0; l < L; ++l) {
-        const lodge_level_desc& lv = desc->levels[l];
-        const int64_t o = d.level_off[l];
-        parallel_for(lv.n, [&](int64_t a, int64_t b) {
-            for (int64_t i = a; i < b; ++i) {
-                float s0 = (float)std::exp((double)lv.log_scales[3 * i]);
-                float s1 = (float)std::exp((double)lv.log_scales[3 * i + 1]);
-                float s2 = (float)std::exp((double)lv.log_scales[3 * i + 2]);
-                float op = (float)(1.0 / (1.0 + std::exp(-(double)lv.opacity_logits[i])));
-                plane4[o + i] = make_float4(s0, s1, s2, op);
-            }
-        });
-    }
-    CUDA_TRY(cudaMemcpy((void*)d.scale_op, plane4.data(), sizeof(float4) * NP, cudaMemcpyHostToDevice));
-    for (int l = 0; l < L; ++l) {
-        const lodge_level_desc& lv = desc->levels[l];
-        const int64_t o = d.level_off[l];
-        parallel_for(lv.n, [&](int64_t a, int64_t b) {
-            for (int64_t i = a; i < b; ++i) {
-                double w = lv.quats[4 * i], x = lv.quats[4 * i + 1], y = lv.quats[4 * i + 2], z = lv.quats[4 * i + 3];
-                double nrm = std::sqrt(((w * w + x * x) + y * y) + z * z);
-                plane4[o + i] = make_float4((float)(w / nrm), (float)(x / nrm), (float)(y / nrm), (float)(z / nrm));
-            }
-        });
-    }
-    CUDA_TRY(cudaMemcpy((void*)d.quat, plane4.data(), sizeof(float4) * NP, cudaMemcpyHostToDevice));
-    for (int j = 0; j < 12; ++j) {
-        for (int l = 0; l < L; ++l) {
-            const lodge_level_desc& lv = desc->levels[l];
-            const int64_t o = d.level_off[l];
-            parallel_for(lv.n, [&](int64_t a, int64_t b) {
-                for (int64_t i = a; i < b; ++i) {
-                    const float* p = lv.sh + 48 * i + 4 * j;
-                    plane4[o + i] = make_float4(p[0], p[1], p[2], p[3]);
-                }
-            });
-        }
-        CUDA_TRY(cudaMemcpy((void*)(d.sh + (size_t)j * NP), plane4.data(), sizeof(float4) * NP,
-                            cudaMemcpyHostToDevice));
-    }
-    // thresholds and chunks
     sc->d_inner.assign(desc->d_thresholds, desc->d_thresholds + std::max(L - 1, 0));
     const int K = desc->num_chunks;
     sc->centers.assign(desc->chunk_centers, desc->chunk_centers + 3 * K);
@@ -828,26 +922,62 @@ lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int3
         }
         sc->radius[k] = K > 1 ? best : 0.0;
     }
-    ctx->scenes.emplace_back(std::move(sc));
-    Scene* S = ctx->scenes.back().get();
-    *scene_id = (int32_t)ctx->scenes.size() - 1;
     // per-chunk active sets: Eq. 2 at m_k with thresholds d_l + r_k
-    cudaStream_t s = 0;
-    S->chunks.assign(K, Chunk{});
+    DevScene dsel = d;
+    if (means_tmp) {
+        float* mp = static_cast<float*>(means_tmp);
+        dsel.mx = mp; dsel.my = mp + NP; dsel.mz = mp + 2 * NP;
+    }
+    sc->chunks.assign(K, Chunk{});
     std::vector<double> dd(std::max(L - 1, 1));
-    for (int k = 0; k < K; ++k) {
-        for (int l = 0; l + 1 < L; ++l) dd[l] = S->d_inner[l] + S->radius[k];
+    std::vector<std::vector<uint32_t>> host_lists;
+    if (sc->residency == kStreamed) host_lists.resize(K);
+    lodge_status r = LODGE_OK;
+    for (int k = 0; k < K && r == LODGE_OK; ++k) {
+        for (int l = 0; l + 1 < L; ++l) dd[l] = sc->d_inner[l] + sc->radius[k];
         int64_t n;
-        lodge_status st = run_lod_select(ctx, S, &S->centers[3 * k], dd.data(), s, &n);
-        if (st != LODGE_OK) return st;
-        void* p = nullptr;
-        TRY(dmalloc(ctx, &p, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1)));
-        if (n) CUDA_TRY(cudaMemcpy(p, ctx->ws.list.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice));
-        S->chunks[k].list = static_cast<uint32_t*>(p);
-        S->chunks[k].n = n;
-        S->chunk_bytes += sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1);
+        r = run_lod_select(ctx, sl, dsel, &sc->centers[3 * k], dd.data(), s, &n);
+        if (r != LODGE_OK) break;
+        sc->chunks[k].n = n;
+        if (sc->residency == kResident) {
+            void* p = nullptr;
+            r = dmalloc(ctx, &p, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1));
+            if (r != LODGE_OK) break;
+            if (n) cudaMemcpy(p, sl.ws.list.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice);
+            sc->chunks[k].list = static_cast<uint32_t*>(p);
+            sc->chunk_bytes += sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1);
+        } else {
+            host_lists[k].resize((size_t)n);
+            if (n) cudaMemcpy(host_lists[k].data(), sl.ws.list.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+        }
+    }
+    if (means_tmp) dfree(ctx, means_tmp, means_tmp_bytes);
+    if (r == LODGE_OK && sc->residency == kStreamed) {
+        size_t total = 0;
+        for (auto& v : host_lists) total += v.size();
+        cudaError_t e = cudaHostAlloc((void**)&sc->host_lists, sizeof(uint32_t) * std::max<size_t>(total, 1),
+                                      cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            r = fail(LODGE_E_OOM, "pinned chunk lists: %s", cudaGetErrorString(e));
+        } else {
+            size_t off = 0;
+            for (int k = 0; k < K; ++k) {
+                std::memcpy(sc->host_lists + off, host_lists[k].data(), sizeof(uint32_t) * host_lists[k].size());
+                sc->chunks[k].list = sc->host_lists + off;
+                off += host_lists[k].size();
+            }
+        }
+    }
+    if (r != LODGE_OK) {
+        free_scene(ctx, *sc);
+        return r;
     }
     CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    sc->id = (int)ctx->scenes.size();
+    *scene_id = sc->id;
+    ctx->scenes.emplace_back(std::move(sc));
     return LODGE_OK;
 }
 
@@ -857,9 +987,9 @@ lodge_status lodge_unload_scene(lodge_ctx* ctx, int32_t scene_id) {
     if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
     CUDA_TRY(cudaSetDevice(ctx->device));
     CUDA_TRY(cudaDeviceSynchronize());
-    dfree(ctx, sc->block, sc->block_bytes);
-    for (auto& ch : sc->chunks) dfree(ctx, ch.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(ch.n, 1));
-    release(ctx, sc->ulist, 0);
+    free_scene(ctx, *sc);
+    for (auto& sl : ctx->slots)
+        if (sl->u_scene == scene_id) sl->u_scene = -1;
     CUDA_TRY(cudaDeviceSynchronize());
     ctx->scenes[scene_id].reset();
     return LODGE_OK;
@@ -867,7 +997,6 @@ lodge_status lodge_unload_scene(lodge_ctx* ctx, int32_t scene_id) {
 
 lodge_status lodge_upload_chunks(lodge_ctx* ctx, int32_t scene_id, const int32_t* chunk_ids,
                                  int32_t n, int blocking) {
-    (void)blocking;
     if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
     Scene* sc = get_scene(ctx, scene_id);
     if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
@@ -875,6 +1004,17 @@ lodge_status lodge_upload_chunks(lodge_ctx* ctx, int32_t scene_id, const int32_t
     for (int i = 0; i < n; ++i)
         if (chunk_ids[i] < 0 || chunk_ids[i] >= (int32_t)sc->chunks.size())
             return fail(LODGE_E_INVALID, "chunk id %d out of range", chunk_ids[i]);
+    if (sc->residency == kResident) return LODGE_OK;  // every chunk set is resident
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    Slot& sl = *ctx->slots[0];
+    for (int i = 0; i < n; ++i) {
+        Block* b = nullptr;
+        lodge_status r = acquire_block(ctx, sl, sc, chunk_ids[i], ctx->upload_stream, &b);
+        if (r != LODGE_OK) { release_blocks(ctx, sl); return r; }
+        sl.held[0] = b;
+        release_blocks(ctx, sl);   // uploaded and cached, not pinned by a frame
+    }
+    if (blocking) CUDA_TRY(cudaStreamSynchronize(ctx->upload_stream));
     return LODGE_OK;
 }
 
@@ -886,24 +1026,42 @@ lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
     if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot& sl = *ctx->slots[0];
     for (int i = 0; i < n_cams; ++i) {
         Active act;
-        TRY(select_active(ctx, sc, mode, cams[i], s, &act));
-        out[i].chunk_a = act.A;
-        out[i].chunk_b = act.B;
-        out[i].t_a = act.tA;
-        out[i].t_b = act.tB;
-        out[i].n_active = act.n;
-        if (d_gids && n_cams == 1) {
-            if (act.n > gids_capacity) return fail(LODGE_E_OVERFLOW, "active set %lld > capacity %lld", (long long)act.n, (long long)gids_capacity);
-            if (act.list) {
-                if (act.n) CUDA_TRY(cudaMemcpyAsync(d_gids, act.list, sizeof(uint32_t) * act.n, cudaMemcpyDeviceToDevice, s));
-            } else if (act.n) {
-                iota_kernel<<<(unsigned)((act.n + 255) / 256), 256, 0, s>>>(d_gids, act.n);
-                CUDA_TRY(cudaGetLastError());
+        lodge_status r = select_active(ctx, sl, sc, mode, cams[i], s, &act);
+        if (r == LODGE_OK) {
+            out[i].chunk_a = act.A;
+            out[i].chunk_b = act.B;
+            out[i].t_a = act.tA;
+            out[i].t_b = act.tB;
+            out[i].n_active = act.n;
+            if (d_gids && n_cams == 1) {
+                if (act.n > gids_capacity) {
+                    r = fail(LODGE_E_OVERFLOW, "active set %lld > capacity %lld", (long long)act.n,
+                             (long long)gids_capacity);
+                } else if (act.n && act.blocks) {
+                    // membership flags are reported only when two chunks are blended
+                    block_gid_kernel<<<(unsigned)((act.n + 255) / 256), 256, 0, s>>>(
+                        act.list, act.n, act.src.gid_a, act.src.gid_b,
+                        act.B >= 0 ? (kFlagA | kFlagB) : 0u, d_gids);
+                } else if (act.n && act.list) {
+                    cudaMemcpyAsync(d_gids, act.list, sizeof(uint32_t) * act.n, cudaMemcpyDeviceToDevice, s);
+                } else if (act.n) {
+                    iota_kernel<<<(unsigned)((act.n + 255) / 256), 256, 0, s>>>(d_gids, act.n);
+                }
+                if (r == LODGE_OK) {
+                    cudaError_t e = cudaGetLastError();
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                    if (e != cudaSuccess) r = fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e));
+                }
             }
-            CUDA_TRY(cudaStreamSynchronize(s));
         }
+        if (sc->residency == kStreamed) {
+            cudaStreamSynchronize(s);
+            release_blocks(ctx, sl);
+        }
+        if (r != LODGE_OK) return r;
     }
     return LODGE_OK;
 }
@@ -918,15 +1076,15 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot& sl = *ctx->slots[0];
     size_t off = 0;
     for (int i = 0; i < n_cams; ++i) {
-        Active act;
-        TRY(select_active(ctx, sc, mode, cams[i], s, &act));
         std::unique_ptr<Saved> sv;
         if (save_for_backward) sv.reset(new Saved());
-        TRY(render_frame(ctx, sc->dev, act, cams[i], d_rgb + off, s, sv.get(), stats ? stats + i : nullptr));
+        TRY(render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, s, sv.get(), stats ? stats + i : nullptr));
         off += (size_t)cams[i].width * cams[i].height * 3;
         if (sv) {
+            std::lock_guard<std::recursive_mutex> lk(ctx->mu);
             int64_t h = ctx->next_handle++;
             ctx->saved[h] = std::move(sv);
             *handle_out = h;
@@ -945,9 +1103,10 @@ lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode
         TRY(check_cam(cams[i]));
         total += (size_t)cams[i].width * cams[i].height * 3;
     }
-    TRY(ensure(ctx, ctx->ws.img, sizeof(float) * std::max<size_t>(total, 1), s));
-    TRY(lodge_render(ctx, scene_id, mode, cams, n_cams, ctx->ws.img.as<float>(), stream, 0, nullptr, stats));
-    if (total) CUDA_TRY(cudaMemcpyAsync(h_rgb, ctx->ws.img.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+    Slot& sl = *ctx->slots[0];
+    TRY(ensure(ctx, sl.ws.img, sizeof(float) * std::max<size_t>(total, 1), s));
+    TRY(lodge_render(ctx, scene_id, mode, cams, n_cams, sl.ws.img.as<float>(), stream, 0, nullptr, stats));
+    if (total) CUDA_TRY(cudaMemcpyAsync(h_rgb, sl.ws.img.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return LODGE_OK;
 }
@@ -962,19 +1121,18 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
     if (n > 0 && (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh))
         return fail(LODGE_E_INVALID, "NULL parameter array");
     if (sh_degree < 0 || sh_degree > 3) return fail(LODGE_E_INVALID, "sh_degree outside 0..3");
-    if ((uintptr_t)d_sh % 16 != 0)
-        return fail(LODGE_E_INVALID, "d_sh must be 16-byte aligned");
+    if ((uintptr_t)d_sh % 16 != 0) return fail(LODGE_E_INVALID, "d_sh must be 16-byte aligned");
     if (save_for_backward && !handle_out) return fail(LODGE_E_INVALID, "handle_out is NULL");
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Workspace& ws = ctx->ws;
+    Slot& sl = *ctx->slots[0];
+    Workspace& ws = sl.ws;
     const size_t n1 = (size_t)std::max<int64_t>(n, 1);
-    const int64_t np = (n + 63) / 64 * 64;
+    const int64_t NP = std::max<int64_t>((n + 63) / 64 * 64, 64);
     TRY(ensure(ctx, ws.act_so, sizeof(float4) * n1, s));
     TRY(ensure(ctx, ws.act_q, sizeof(float4) * n1, s));
-    TRY(ensure(ctx, ws.mtmp, sizeof(float) * 3 * (size_t)std::max<int64_t>(np, 64) + sizeof(float4) * 12 * (size_t)std::max<int64_t>(np, 64), s));
+    TRY(ensure(ctx, ws.mtmp, sizeof(float) * 3 * (size_t)NP + sizeof(float4) * 12 * (size_t)NP, s));
     float* mp = ws.mtmp.as<float>();
-    const int64_t NP = std::max<int64_t>(np, 64);
     float4* shp = reinterpret_cast<float4*>(mp + 3 * NP);
     if (n) {
         unsigned nb = (unsigned)((n + 255) / 256);
@@ -998,8 +1156,7 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
     act.n = n;
     std::unique_ptr<Saved> sv;
     if (save_for_backward) sv.reset(new Saved());
-    // the projection kernel strides SH planes by the padded count of the scene
-    TRY(render_frame(ctx, d, act, *cam, d_rgb, s, sv.get(), stats));
+    TRY(render_frame(ctx, sl, d, act, *cam, d_rgb, s, sv.get(), stats));
     if (sv) {
         sv->params = true;
         sv->n = n;
@@ -1009,6 +1166,7 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
         sv->filter_var = filter_var;
         take(sv->act_so, ws.act_so);
         take(sv->act_q, ws.act_q);
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
         int64_t h = ctx->next_handle++;
         ctx->saved[h] = std::move(sv);
         *handle_out = h;
@@ -1026,11 +1184,12 @@ lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* 
     if (!v.params) return fail(LODGE_E_INVALID, "frame %lld was not rendered from parameters", (long long)handle);
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Workspace& ws = ctx->ws;
+    Slot& sl = *ctx->slots[0];
+    Workspace& ws = sl.ws;
     const size_t n9 = 9 * (size_t)std::max<int64_t>(v.n_vis, 1);
     TRY(ensure(ctx, ws.grec, sizeof(float) * n9, s));
     CUDA_TRY(cudaMemsetAsync(ws.grec.p, 0, sizeof(float) * n9, s));
-    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
     launch_blend_bwd(v.cam, v.ranges.as<uint2>(), v.tval.as<uint32_t>(), v.n_keys, v.rec_a.as<float4>(),
                      v.rec_b.as<float4>(), v.rec_c.as<float>(), v.n_vis, v.T.as<float>(),
                      v.last.as<uint32_t>(), d_dL_drgb, ws.grec.as<float>(), s);
@@ -1038,19 +1197,21 @@ lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* 
                        v.act_so.as<float4>(), v.act_q.as<float4>(), v.quats, v.sh, v.sh_degree,
                        v.filter_var, d_g_means, d_g_log_scales, d_g_quats, d_g_opacity_logits, d_g_sh, s);
     CUDA_TRY(cudaGetLastError());
-    return sync_small(ctx, s);
+    return sync_slot(ctx, sl, s);
 }
 
 lodge_status lodge_release(lodge_ctx* ctx, int64_t handle) {
     if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
-    auto it = ctx->saved.find(handle);
-    if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
+    std::unique_ptr<Saved> v;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        auto it = ctx->saved.find(handle);
+        if (it == ctx->saved.end()) return fail(LODGE_E_INVALID, "no saved frame %lld", (long long)handle);
+        v = std::move(it->second);
+        ctx->saved.erase(it);
+    }
     CUDA_TRY(cudaSetDevice(ctx->device));
-    Saved& v = *it->second;
-    for (DBuf* b : {&v.rec_a, &v.rec_b, &v.rec_c, &v.rec_rect, &v.rec_gid, &v.zsorted, &v.rsorted, &v.tkey,
-                    &v.tval, &v.ranges, &v.T, &v.last, &v.act_so, &v.act_q})
-        release(ctx, *b, 0);
-    ctx->saved.erase(it);
+    free_saved(ctx, *v, false);
     return LODGE_OK;
 }
 
@@ -1107,33 +1268,56 @@ lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals
     if (n > 0 && (!d_keys || !d_vals)) return fail(LODGE_E_INVALID, "NULL key or value array");
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Workspace& ws = ctx->ws;
+    Slot& sl = *ctx->slots[0];
+    Workspace& ws = sl.ws;
     const size_t n1 = (size_t)std::max<int64_t>(n, 1);
     TRY(ensure(ctx, ws.tkey2, sizeof(uint32_t) * n1, s));
     TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * n1, s));
     TRY(ensure(ctx, ws.sort, sort_scratch_bytes(n, key_bits), s));
-    CUDA_TRY(cudaMemsetAsync(ctx->d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
     int w = launch_onesweep(d_keys, d_vals, ws.tkey2.as<uint32_t>(), ws.tval2.as<uint32_t>(), n, key_bits,
-                            ws.sort.p, ctx->d_small + kSmErr, s);
+                            ws.sort.p, sl.d_small + kSmErr, s);
     if (w) {
         CUDA_TRY(cudaMemcpyAsync(d_keys, ws.tkey2.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
         CUDA_TRY(cudaMemcpyAsync(d_vals, ws.tval2.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
     CUDA_TRY(cudaGetLastError());
-    return sync_small(ctx, s);
+    return sync_slot(ctx, sl, s);
 }
 
 lodge_status lodge_profile_enable(lodge_ctx* ctx, int enable) {
     if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
-    ctx->prof = lodge_profile{};
-    for (int k = 0; k < LODGE_NUM_STAGES; ++k) ctx->ev_pending[k] = false;
-    ctx->prof_on = enable != 0;
+    Slot& sl = *ctx->slots[0];
+    sl.prof = lodge_profile{};
+    for (int k = 0; k < LODGE_NUM_STAGES; ++k) sl.ev_pending[k] = false;
+    sl.prof_on = enable != 0;
     return LODGE_OK;
 }
 
 lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
     if (!ctx || !out) return fail(LODGE_E_INVALID, "bad argument");
-    *out = ctx->prof;
+    *out = ctx->slots[0]->prof;
+    return LODGE_OK;
+}
+
+lodge_status lodge_residency_stats(lodge_ctx* ctx, lodge_residency* out) {
+    if (!ctx || !out) return fail(LODGE_E_INVALID, "bad argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    out->resident_blocks = (int64_t)ctx->blocks.size();
+    out->block_hits = ctx->res.hits;
+    out->block_uploads = ctx->res.uploads;
+    out->block_evictions = ctx->res.evictions;
+    out->upload_bytes = ctx->res.upload_bytes;
+    out->failed_uploads = ctx->res.failed_uploads;
+    out->hbm_used = (int64_t)ctx->used;
+    out->hbm_budget = (int64_t)ctx->budget;
+    return LODGE_OK;
+}
+
+lodge_status lodge_inject_upload_failures(lodge_ctx* ctx, int32_t n) {
+    if (!ctx || n < 0) return fail(LODGE_E_INVALID, "bad argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->fail_next_uploads = n;
     return LODGE_OK;
 }
 

@@ -40,7 +40,9 @@ def test_struct_layouts_match_header(tmp_path):
     prog = tmp_path / "probe.c"
     structs = {"lodge_level_desc": A.lodge_level_desc, "lodge_scene_desc": A.lodge_scene_desc,
                "lodge_camera": A.lodge_camera, "lodge_selection": A.lodge_selection,
-               "lodge_frame_stats": A.lodge_frame_stats, "lodge_profile": A.lodge_profile}
+               "lodge_frame_stats": A.lodge_frame_stats, "lodge_profile": A.lodge_profile,
+               "lodge_request": A.lodge_request, "lodge_request_result": A.lodge_request_result,
+               "lodge_serve_opts": A.lodge_serve_opts, "lodge_residency": A.lodge_residency}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
