@@ -54,6 +54,13 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=60.0)
+    ap.add_argument("--serve-scale", type=float, default=1.0,
+                    help="scene size factor of the serving scenes (1.0 = 2M/8M/16M/30M)")
     return ap.parse_args()
 
 
@@ -387,9 +394,14 @@ def run_lodge(args, rank, world, local_rank):
         "clocks": clocks,
         "setup_s": {"generate": round(t_gen, 1), "load_scene": round(t_load, 1)},
     }
+    ctx.close()
+    del out
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args, scene, cams)
-    ctx.close()
+    del scene, cams
+    if not args.no_serve:
+        torch.cuda.empty_cache()
+        res["serve_latency"] = run_serve(args, local_rank)
     return res
 
 
@@ -418,6 +430,85 @@ def cpu_baseline(args, scene, cams, budget_s=None, max_frames=None):
     return {"value": round(done / spent, 4), "unit": UNIT, "cores": ncores, "kind": "oracle",
             "sample": f"{done} whole CHUNK_BLEND {args.width}x{args.height} frames of the trajectory "
                       f"(FP64 binned oracle, OpenMP over tiles), chunk sets precomputed"}
+
+
+SERVE_LEVEL0 = (2_000_000, 8_000_000, 16_000_000, 30_000_000)
+SERVE_RES = ((640, 360), (1280, 720), (1920, 1080), (3840, 2160))
+
+
+def serve_requests(rng, scenes, sids, n, rate, t0=0.0):
+    """Poisson arrivals at `rate`, uniform scene, street-height pose in the
+    inner 80% of the scene (uniform yaw, 10 degree down pitch), resolution
+    uniform over SERVE_RES."""
+    from paper_2505_23158_gb300 import synth
+    from paper_2505_23158_gb300.api import CHUNK_BLEND
+    t = t0 + np.cumsum(rng.exponential(1.0 / rate, size=n))
+    which = rng.integers(0, len(scenes), size=n)
+    res = rng.integers(0, len(SERVE_RES), size=n)
+    seeds = rng.integers(0, 2 ** 31, size=n)
+    reqs = []
+    for i in range(n):
+        w, h = SERVE_RES[res[i]]
+        cam = synth.random_street_cameras(scenes[which[i]], int(seeds[i]), 1, w, h)[0]
+        reqs.append((sids[which[i]], CHUNK_BLEND, cam, float(t[i])))
+    return reqs
+
+
+def run_serve(args, local_rank):
+    """Serving stream over four streamed scenes under an HBM budget."""
+    from paper_2505_23158_gb300 import synth
+    from paper_2505_23158_gb300.api import STREAMED, Lodge
+    t0 = time.time()
+    scenes = []
+    for i, n0 in enumerate(SERVE_LEVEL0):
+        n = int(n0 * args.serve_scale)
+        side = math.sqrt(n / 16.0)          # constant density: 16 level-0 Gaussians per m^2
+        scenes.append(synth.outdoor_scene(seed=args.seed + 10 + i, n0=n, num_levels=4, extent=side,
+                                          grid=16))
+    t_gen = time.time() - t0
+    budget = int(args.serve_budget_gb * (1 << 30))
+    with Lodge(local_rank, hbm_budget_bytes=budget) as ctx:
+        t0 = time.time()
+        sids = [ctx.load_scene(sc, STREAMED) for sc in scenes]
+        t_load = time.time() - t0
+        rng = np.random.default_rng(args.seed + 77)
+        warm = serve_requests(rng, scenes, sids, int(2 * args.serve_rate), args.serve_rate)
+        ctx.serve(warm, slots=args.serve_slots, realtime=True)
+        r0 = ctx.residency_stats()
+        reqs = serve_requests(rng, scenes, sids, int(args.serve_seconds * args.serve_rate),
+                              args.serve_rate)
+        clk = ClockSampler(local_rank)
+        clk.start()
+        results, _ = ctx.serve(reqs, slots=args.serve_slots, realtime=True)
+        clocks = clk.stop()
+        r1 = ctx.residency_stats()
+    ok = [r for r in results if r["status"] == 0]
+    lat = np.array([r["latency_s"] for r in ok]) * 1e3
+    t_end = max(r["finish_s"] for r in results)
+    by_res = {}
+    for (sid, mode, cam, _), r in zip(reqs, results):
+        if r["status"] == 0:
+            by_res.setdefault(f"{cam.width}x{cam.height}", []).append(r["latency_s"] * 1e3)
+    uploads = r1["block_uploads"] - r0["block_uploads"]
+    hits = r1["block_hits"] - r0["block_hits"]
+    return {
+        "rate_rps": args.serve_rate, "requests": len(reqs), "completed": len(ok),
+        "duration_s": round(t_end, 3), "throughput_rps": round(len(ok) / t_end, 2),
+        "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat.size else None,
+        "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat.size else None,
+        "p99_ms_by_resolution": {k: round(float(np.percentile(v, 99)), 3) for k, v in sorted(by_res.items())},
+        "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+        "scenes_level0": [int(n * args.serve_scale) for n in SERVE_LEVEL0],
+        "residency": {"block_uploads": uploads, "block_hits": hits,
+                      "hit_rate": round(hits / max(hits + uploads, 1), 3),
+                      "evictions": r1["block_evictions"] - r0["block_evictions"],
+                      "upload_gb": round((r1["upload_bytes"] - r0["upload_bytes"]) / 1e9, 2),
+                      "hbm_used_gb": round(r1["hbm_used"] / (1 << 30), 2)},
+        "clocks": clocks, "setup_s": {"generate": round(t_gen, 1), "load": round(t_load, 1)},
+        "workload": "4 streamed outdoor LOD scenes (4 levels, constant density, 16x16 chunks), "
+                    "Poisson arrivals, uniform scene, random street-height pose, resolution "
+                    "uniform over 640x360/1280x720/1920x1080/3840x2160, CHUNK_BLEND",
+    }
 
 
 def run_reference(args, rank, world):
