@@ -17,6 +17,10 @@ so these synthetic scenes stand in for them):
                          N0 / 4^l Gaussians, scales doubling per level), a
                          regular chunk grid and a camera trajectory.
 * ``finetune_scene``   - one chunk cell of the outdoor generator.
+* ``large_scene``      - 80M Gaussians over 6 levels: the outdoor heightfield
+                         with room-like indoor blocks (walls, floors) on a
+                         quarter of the chunk cells, 32x32 chunks, viewed by
+                         batches of 3840x2160 street cameras.
 
 Raw parameter layout (host, float32, C-contiguous), per level:
   means           (N, 3)   world position, metres (outdoor) or units (plain)
@@ -377,4 +381,88 @@ def workload_outdoor(seed: int = 0, n_poses: int = 300, scale: float = 1.0,
                           extent=side, grid=grid)
     cams = outdoor_trajectory(scene, seed=seed, n_poses=n_poses, width=width,
                               height_px=height_px)
+    return scene, cams
+
+
+# --------------------------------------------------------------------------
+# large indoor + outdoor scene
+# --------------------------------------------------------------------------
+def _room_surface_points(r: np.random.Generator, n: int, x0: float, y0: float, side: float,
+                         room: float, spacing: float, hp: dict):
+    """n points uniform on the faces of room-sized boxes laid out on a grid of
+    pitch `spacing` inside the square [x0, x0 + side]^2 (floors on the
+    heightfield): floor, ceiling and four walls, all of equal area."""
+    per = int(side // spacing)
+    k = r.integers(0, per * per, size=n)
+    cx = x0 + (k % per + 0.5) * spacing
+    cy = y0 + (k // per + 0.5) * spacing
+    face = r.integers(0, 6, size=n)
+    u = r.uniform(-0.5, 0.5, size=n) * room
+    v = r.uniform(-0.5, 0.5, size=n) * room
+    half = 0.5 * room
+    base = height(hp, cx, cy)
+    x = np.where(face == 2, cx - half, np.where(face == 3, cx + half, cx + u))
+    y = np.where(face == 4, cy - half, np.where(face == 5, cy + half,
+                                                np.where(face < 2, cy + v, cy + u)))
+    z = np.where(face == 0, base, np.where(face == 1, base + room, base + half + v))
+    return x, y, z
+
+
+def large_scene(seed: int = 0, n0: int = 60_000_000, num_levels: int = 6, extent: float = 1000.0,
+                grid: int = 32, indoor_fraction: float = 0.25,
+                d_thresholds: Sequence[float] = (10.0, 20.0, 40.0, 80.0, 160.0),
+                log_scale_mean0: float = math.log(0.125), jitter0: float = 0.5,
+                sh_std: float = 0.2, cam_height: float = 2.0) -> Scene:
+    """Outdoor heightfield world with an indoor quadrant: level l holds
+    n0 / 4^l Gaussians, of which `indoor_fraction` sit on the faces of 10 m
+    rooms (20 m pitch) filling the quadrant [0, extent/2]^2 and the rest on
+    the terrain as in outdoor_scene.  Chunk grid grid x grid."""
+    hp = height_params(seed)
+    levels = []
+    for l in range(num_levels):
+        n = max(int(n0 // (4 ** l)), 1)
+        n_in = int(n * indoor_fraction)
+        n_out = n - n_in
+        r = _rng(seed, 11, l)
+        ox = r.uniform(0.0, extent, size=n_out)
+        oy = r.uniform(0.0, extent, size=n_out)
+        oz = height(hp, ox, oy)
+        ix, iy, iz = _room_surface_points(r, n_in, 0.0, 0.0, extent / 2, 10.0, 20.0, hp)
+        x = np.concatenate([ox, ix]); y = np.concatenate([oy, iy]); z = np.concatenate([oz, iz])
+        del ox, oy, oz, ix, iy, iz
+        jit = r.normal(0.0, jitter0 * 2.0 ** l, size=(n, 3))
+        means = np.empty((n, 3), np.float32)
+        means[:, 0] = x + jit[:, 0]
+        means[:, 1] = y + jit[:, 1]
+        means[:, 2] = z + jit[:, 2]
+        del x, y, z, jit
+        log_scales = r.normal(log_scale_mean0 + l * math.log(2.0), 0.5, size=(n, 3)).astype(np.float32)
+        quats = r.normal(0.0, 1.0, size=(n, 4)).astype(np.float32)
+        logits = r.normal(1.0, 1.0, size=(n,)).astype(np.float32)
+        sh = r.standard_normal(size=(n, SH_COEFFS, 3), dtype=np.float32)
+        sh *= np.float32(sh_std)
+        perm = _morton_order(means[:, 0].astype(np.float64), means[:, 1].astype(np.float64), extent)
+        levels.append(Level(np.ascontiguousarray(means[perm]), np.ascontiguousarray(log_scales[perm]),
+                            np.ascontiguousarray(quats[perm]), np.ascontiguousarray(logits[perm]),
+                            np.ascontiguousarray(sh[perm]), 0.0))
+        del means, log_scales, quats, logits, sh, perm
+    cell = extent / grid
+    cc = (np.arange(grid) + 0.5) * cell
+    gx, gy = np.meshgrid(cc, cc, indexing="xy")
+    centers = np.stack([gx.ravel(), gy.ravel(),
+                        height(hp, gx.ravel(), gy.ravel()) + cam_height], axis=1)
+    return Scene(levels=levels, d_thresholds=np.asarray(d_thresholds[:num_levels - 1], np.float64),
+                 chunk_centers=centers.astype(np.float64), sh_degree=3, extent=float(extent),
+                 height_params=hp)
+
+
+def workload_large(seed: int = 0, n_cams: int = 64, scale: float = 1.0, width: int = 3840,
+                   height_px: int = 2160):
+    """60M level-0 Gaussians over 6 levels (indoor quadrant + outdoor), 32x32
+    chunks, a batch of n_cams street-height cameras at 3840x2160.  ``scale``
+    shrinks the world at constant density."""
+    side = 1000.0 * math.sqrt(scale)
+    grid = max(1, int(round(32 * math.sqrt(scale))))
+    scene = large_scene(seed=seed, n0=int(60_000_000 * scale), extent=side, grid=grid)
+    cams = random_street_cameras(scene, seed + 5, n_cams, width, height_px)
     return scene, cams

@@ -1,0 +1,243 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (resident scene, one render call per camera):
+
+* outdoor LOD scene, 21.25M Gaussians (16M/4M/1M/250k), 16x16 chunks,
+  1920x1080 trajectory: selected sets and sorted tile keys bit-exact against
+  the oracle; pixels on sampled tiles within the pixel bars;
+* fine-tuning of one chunk cell (2M Gaussians, 32 views at 1280x720):
+  gradients on an image crop against the FP64 gradient oracle (restricted to
+  the Gaussians that reach the crop), and the loss falls over Adam steps;
+* large indoor+outdoor scene, 80M Gaussians over 6 levels, 32x32 chunks,
+  64 cameras at 3840x2160 in one call: selection bit-exact, sampled pixels,
+  and a frame of the batch equals the same camera rendered alone.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2505_23158_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MAX_ABS = 2e-4
+MEAN_ABS = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_23158_gb300 import build
+    build.build()
+    from paper_2505_23158_gb300 import api
+    return torch, api
+
+
+def tiles_of(cam, k, seed):
+    tx = (cam.width + 15) // 16
+    ty = (cam.height + 15) // 16
+    return np.sort(np.random.default_rng(seed).choice(tx * ty, size=k, replace=False)).astype(np.int32)
+
+
+def compare_tiles(img, ref, cam, tiles, tag):
+    tx = (cam.width + 15) // 16
+    mask = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        x, y = (t % tx) * 16, (t // tx) * 16
+        mask[y:y + 16, x:x + 16] = True
+    g = np.clip(img.astype(np.float64), 0, 1)[mask]
+    r = np.clip(ref["rgb"], 0, 1)[mask]
+    kn = ref["knife"][mask]
+    d = np.abs(g - r)
+    worst = d[~kn].max() if (~kn).any() else 0.0
+    assert worst <= MAX_ABS, f"{tag}: max-abs {worst:.3g}"
+    assert d.mean() <= MEAN_ABS, f"{tag}: mean-abs {d.mean():.3g}"
+    assert kn.sum() <= max(3, 0.01 * kn.size), f"{tag}: {kn.sum()} knife-edge pixels"
+
+
+# ---------------------------------------------------------------------------
+# outdoor LOD scene at full size
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def outdoor_full(env):
+    torch, api = env
+    scene, cams = synth.workload_outdoor(seed=0, n_poses=300)
+    ctx = api.Lodge(0)
+    sid = ctx.load_scene(scene)
+    osc = O.OracleScene(scene)
+    yield torch, api, ctx, sid, scene, cams, osc
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode_name", ["LOD", "CHUNK", "CHUNK_BLEND"])
+def test_outdoor_full_selection(outdoor_full, mode_name):
+    torch, api, ctx, sid, scene, cams, osc = outdoor_full
+    mode = getattr(api, mode_name)
+    for pi in (0, 150, 299):
+        sel, gids = ctx.select(sid, mode, cams[pi], want_gids=True)
+        g_ref, m_ref, info = O.active_set(osc, mode, cams[pi])
+        raw = gids.cpu().numpy().view(np.uint32)
+        assert np.array_equal((raw & 0x3FFFFFFF).astype(np.int64), g_ref), f"pose {pi}"
+        if mode_name == "CHUNK_BLEND" and info["B"] >= 0:
+            a = O.chunk_select(osc, info["A"])
+            b = O.chunk_select(osc, info["B"])
+            assert np.array_equal((raw >> 31) & 1, np.isin(g_ref, a).astype(np.uint32))
+            assert np.array_equal((raw >> 30) & 1, np.isin(g_ref, b).astype(np.uint32))
+            assert (sel["chunk_a"], sel["chunk_b"]) == (info["A"], info["B"])
+            assert (sel["t_a"], sel["t_b"]) == (info["tA"], info["tB"])
+
+
+def test_outdoor_full_keys_bit_exact(outdoor_full):
+    torch, api, ctx, sid, scene, cams, osc = outdoor_full
+    cam = cams[150]
+    img, st, h = ctx.render(sid, api.CHUNK_BLEND, cam, save=True)
+    try:
+        keys, kg = ctx.debug_keys(h)
+    finally:
+        ctx.release(h)
+    g_ref, m_ref, _ = O.active_set(osc, O.MODE_CHUNK_BLEND, cam)
+    k_ref, kg_ref = O.keys(osc, cam, g_ref, m_ref)
+    assert st["n_keys"] == k_ref.size > 1_000_000
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref)
+    assert np.array_equal(kg.cpu().numpy().astype(np.int64), kg_ref)
+
+
+@pytest.mark.parametrize("mode_name,pose", [("CHUNK_BLEND", 0), ("CHUNK_BLEND", 150),
+                                            ("FULL", 0), ("LOD", 299)])
+def test_outdoor_full_sampled_pixels(outdoor_full, mode_name, pose):
+    torch, api, ctx, sid, scene, cams, osc = outdoor_full
+    mode = getattr(api, mode_name)
+    cam = cams[pose]
+    img, st = ctx.render(sid, mode, cam)
+    g_ref, m_ref, _ = O.active_set(osc, mode, cam)
+    tiles = tiles_of(cam, 48, pose)
+    ref = O.render(osc, cam, g_ref, m_ref, tiles=tiles)
+    compare_tiles(img.cpu().numpy(), ref, cam, tiles, f"{mode_name} pose {pose}")
+    assert st["n_keys"] == ref["n_keys"] and st["n_visible"] == ref["n_visible"]
+
+
+# ---------------------------------------------------------------------------
+# fine-tuning of one chunk cell (2M Gaussians, 32 views at 1280x720)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def finetune(env):
+    torch, api = env
+    scene = synth.finetune_scene(seed=0, n=2_000_000)
+    target = synth.perturb_scene(scene, seed=1)
+    cams = synth.finetune_cameras(scene, seed=0, n=32)
+    return torch, api, scene, target, cams
+
+
+def _crop(cam, x0, y0, w, h):
+    return synth.Camera(R=cam.R, t=cam.t, fx=cam.fx, fy=cam.fy, cx=float(np.float32(cam.cx - x0)),
+                        cy=float(np.float32(cam.cy - y0)), width=w, height=h, znear=cam.znear,
+                        center=cam.center)
+
+
+def test_finetune_gradients_on_crop(finetune):
+    torch, api, scene, target, cams = finetune
+    from oracle import grad as G
+    lv = scene.levels[0]
+    n = lv.n
+    cam = _crop(cams[0], 608, 344, 32, 24)
+    osc = O.OracleScene(scene)
+    pr = O.project(osc, cam, np.arange(n))
+    sub = np.flatnonzero(pr["visible"])
+    assert 10 < sub.size < 30000
+    sub_lv = synth.Level(lv.means[sub], lv.log_scales[sub], lv.quats[sub], lv.opacity_logits[sub],
+                         lv.sh[sub])
+    w = np.random.default_rng(4).normal(size=(cam.height, cam.width, 3))
+    g_ref, img_ref = G.grads(sub_lv, cam, w)
+    dev = torch.device("cuda")
+    ps = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+          for a in (lv.means, lv.log_scales, lv.quats, lv.opacity_logits, lv.sh.reshape(n, 48))]
+    with api.Lodge(0) as ctx:
+        img, st, h = ctx.render_params(*ps, cam, save=True)
+        gs = [torch.zeros_like(p) for p in ps]
+        ctx.render_backward(h, torch.from_numpy(w.astype(np.float32)).to(dev), *gs)
+        ctx.release(h)
+    assert np.abs(img.cpu().numpy() - img_ref).max() < 2e-4
+    rest = np.ones(n, bool)
+    rest[sub] = False
+    for name, g, r in zip(["means", "log_scales", "quats", "opacity_logits", "sh"], gs, g_ref):
+        gn = g.cpu().numpy().reshape(n, -1).astype(np.float64)
+        e = np.linalg.norm(gn[sub] - r.reshape(sub.size, -1)) / max(np.linalg.norm(r), 1e-30)
+        assert e < 1e-3, f"{name}: relative L2 error {e:.3g}"
+        assert not gn[rest].any(), f"{name}: gradient outside the crop's Gaussians"
+
+
+def test_finetune_fit_steps_full_views(finetune):
+    """Adam on all five parameter groups, L1 against the perturbed target over
+    the 32 views at 1280x720: the loss falls."""
+    torch, api, scene, target, cams = finetune
+    from paper_2505_23158_gb300.api import render_differentiable
+    lv, tl = scene.levels[0], target.levels[0]
+    n = lv.n
+    dev = torch.device("cuda")
+
+    def params(l, grad):
+        return [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev).requires_grad_(grad)
+                for a in (l.means, l.log_scales, l.quats, l.opacity_logits, l.sh.reshape(n, 48))]
+
+    with api.Lodge(0) as ctx:
+        tps = params(tl, False)
+        targets = []
+        for cam in cams:
+            img, _, _ = ctx.render_params(*tps, cam, save=False)
+            targets.append(img.clone())
+        ps = params(lv, True)
+        opt = torch.optim.Adam(ps, lr=1e-3)
+        losses = []
+        for step in range(4):
+            opt.zero_grad()
+            total = 0.0
+            for cam, tgt in zip(cams, targets):
+                img = render_differentiable(ctx, *ps, cam)
+                loss = (img - tgt).abs().mean() / len(cams)
+                loss.backward()
+                total += float(loss.detach())
+            opt.step()
+            losses.append(total)
+        assert losses[-1] < losses[0], losses
+
+
+# ---------------------------------------------------------------------------
+# large indoor+outdoor scene (80M Gaussians, 6 levels, 64 cameras at 4K)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def large(env):
+    torch, api = env
+    scene, cams = synth.workload_large(seed=0, n_cams=64)
+    ctx = api.Lodge(0)
+    sid = ctx.load_scene(scene)
+    osc = O.OracleScene(scene)
+    yield torch, api, ctx, sid, scene, cams, osc
+    ctx.close()
+
+
+def test_large_selection_and_pixels(large):
+    torch, api, ctx, sid, scene, cams, osc = large
+    assert scene.n_total == sum(60_000_000 // 4 ** l for l in range(6))
+    for ci in (3, 40):
+        cam = cams[ci]
+        sel, gids = ctx.select(sid, api.CHUNK_BLEND, cam, want_gids=True)
+        g_ref, m_ref, info = O.active_set(osc, O.MODE_CHUNK_BLEND, cam)
+        raw = gids.cpu().numpy().view(np.uint32)
+        assert np.array_equal((raw & 0x3FFFFFFF).astype(np.int64), g_ref)
+        img, st = ctx.render(sid, api.CHUNK_BLEND, cam)
+        tiles = tiles_of(cam, 32, ci)
+        ref = O.render(osc, cam, g_ref, m_ref, tiles=tiles)
+        compare_tiles(img.cpu().numpy(), ref, cam, tiles, f"large camera {ci}")
+        assert st["n_keys"] == ref["n_keys"]
+
+
+def test_large_batch_of_64_cameras(large):
+    torch, api, ctx, sid, scene, cams, osc = large
+    imgs, stats = ctx.render(sid, api.CHUNK_BLEND, cams)
+    assert len(imgs) == 64 and all(s["n_visible"] > 0 for s in stats)
+    assert all(bool(torch.isfinite(im).all()) for im in imgs)
+    one, _ = ctx.render(sid, api.CHUNK_BLEND, cams[7])
+    assert bool((one == imgs[7]).all())
