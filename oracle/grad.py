@@ -65,10 +65,13 @@ def quat_to_rot(q: torch.Tensor) -> torch.Tensor:
 
 def render_t(means, log_scales, quats, logits, sh, cam, sh_degree=3, filter_var=0.0,
              mults=None, order=None, pix_chunk=1024, return_aux=False):
-    """Image (H, W, 3) in FP64 from raw parameters (torch tensors, FP64,
-    possibly requiring grad).  `order`: Gaussian indices in compositing order
+    """Image (H, W, 3) from raw parameters (torch tensors, FP64 -- or FP32
+    to measure how much rounding at that precision moves a result -- possibly
+    requiring grad).  `order`: Gaussian indices in compositing order
     (default: by FP32 key depth then index, near-culled ones dropped)."""
     H, W = int(cam.height), int(cam.width)
+    ft = means.dtype
+    nf = np.float64 if ft == torch.float64 else np.float32
     if order is None:
         z32 = depth32(means.detach().to(torch.float32).numpy(), cam)
         idx = np.arange(z32.size)
@@ -82,15 +85,15 @@ def render_t(means, log_scales, quats, logits, sh, cam, sh_degree=3, filter_var=
     q = qr / torch.linalg.norm(qr, dim=1, keepdim=True)
     op = torch.sigmoid(logits[order_t])
     if mults is not None:
-        op = op * torch.as_tensor(np.asarray(mults, np.float64)[order], dtype=torch.float64)
+        op = op * torch.as_tensor(np.asarray(mults, np.float64)[order], dtype=ft)
     v = float(filter_var)
     s2 = s * s + v
     if v > 0:
         op = op * torch.prod(s / torch.sqrt(s2), dim=1)
     Rq = quat_to_rot(q)
     Sig = Rq @ torch.diag_embed(s2) @ Rq.transpose(1, 2)
-    R = torch.as_tensor(np.asarray(cam.R, np.float32).astype(np.float64))
-    t = torch.as_tensor(np.asarray(cam.t, np.float32).astype(np.float64))
+    R = torch.as_tensor(np.asarray(cam.R, np.float32).astype(nf))
+    t = torch.as_tensor(np.asarray(cam.t, np.float32).astype(nf))
     p = mu @ R.T + t
     fx, fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
     cx, cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
@@ -107,15 +110,15 @@ def render_t(means, log_scales, quats, logits, sh, cam, sh_degree=3, filter_var=
     ca, cb, cc = c / det, -b / det, a / det
     mx = fx * px / pz + cx
     my = fy * py / pz + cy
-    center = torch.as_tensor(np.asarray(cam.center, np.float64))
+    center = torch.as_tensor(np.asarray(cam.center, np.float64).astype(nf))
     d = mu - center
     d = d / torch.linalg.norm(d, dim=1, keepdim=True)
     nk = (sh_degree + 1) ** 2
     Y = sh_basis_t(d)[:, :nk]
     rgb = torch.clamp(torch.einsum("nk,nkc->nc", Y, sh[order_t][:, :nk, :]) + 0.5, min=0.0)
 
-    ys, xs = torch.meshgrid(torch.arange(H, dtype=torch.float64) + 0.5,
-                            torch.arange(W, dtype=torch.float64) + 0.5, indexing="ij")
+    ys, xs = torch.meshgrid(torch.arange(H, dtype=ft) + 0.5,
+                            torch.arange(W, dtype=ft) + 0.5, indexing="ij")
     P = torch.stack([xs.reshape(-1), ys.reshape(-1)], 1)
     out = []
     Tfin = []
@@ -128,9 +131,9 @@ def render_t(means, log_scales, quats, logits, sh, cam, sh_degree=3, filter_var=
         qf = ca[None] * dx * dx + 2 * cb[None] * dx * dy + cc[None] * dy * dy
         alpha = torch.clamp(op[None] * torch.exp(-0.5 * qf), max=0.99)
         with torch.no_grad():
-            used = (alpha >= 1.0 / 255.0).to(torch.float64)
+            used = (alpha >= 1.0 / 255.0).to(ft)
             Tinc = torch.cumprod(1.0 - alpha * used, dim=1)
-            incl = (Tinc >= 1e-4).to(torch.float64) * used
+            incl = (Tinc >= 1e-4).to(ft) * used
         sig[0] += float(used.sum())
         sig[1] += float(incl.sum())
         am = alpha * incl
@@ -146,19 +149,23 @@ def render_t(means, log_scales, quats, logits, sh, cam, sh_degree=3, filter_var=
     return img
 
 
-def params_t(level, requires_grad=True):
-    """FP64 torch copies of a synth.Level's raw parameters."""
+def params_t(level, requires_grad=True, dtype=torch.float64):
+    """Torch copies (FP64 by default) of a synth.Level's raw parameters."""
+    nf = np.float64 if dtype == torch.float64 else np.float32
+
     def t(a):
-        x = torch.as_tensor(np.asarray(a, np.float32).astype(np.float64))
+        x = torch.as_tensor(np.asarray(a, np.float32).astype(nf))
         return x.requires_grad_(requires_grad)
     return (t(level.means), t(level.log_scales), t(level.quats), t(level.opacity_logits), t(level.sh))
 
 
-def grads(level, cam, weight, sh_degree=3, filter_var=0.0):
+def grads(level, cam, weight, sh_degree=3, filter_var=0.0, dtype=torch.float64):
     """Gradients of L = sum(weight * image) w.r.t. (means, log_scales, quats,
-    opacity_logits, sh), FP64 numpy arrays."""
-    ps = params_t(level)
+    opacity_logits, sh) as numpy arrays.  dtype=torch.float32 evaluates the
+    same definition with FP32 rounding: its distance to the FP64 result is
+    the error that FP32 arithmetic alone makes on these inputs."""
+    ps = params_t(level, dtype=dtype)
     img = render_t(*ps, cam, sh_degree=sh_degree, filter_var=filter_var)
-    L = (img * torch.as_tensor(np.asarray(weight, np.float64))).sum()
+    L = (img * torch.as_tensor(np.asarray(weight, np.float64), dtype=dtype)).sum()
     L.backward()
     return [p.grad.numpy().copy() for p in ps], img.detach().numpy()

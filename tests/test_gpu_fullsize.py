@@ -151,6 +151,9 @@ def test_finetune_gradients_on_crop(finetune):
                          lv.sh[sub])
     w = np.random.default_rng(4).normal(size=(cam.height, cam.width, 3))
     g_ref, img_ref = G.grads(sub_lv, cam, w)
+    # the same definition evaluated with FP32 rounding: how far FP32
+    # arithmetic alone moves each gradient group on this input
+    g_32, _ = G.grads(sub_lv, cam, w, dtype=torch.float32)
     dev = torch.device("cuda")
     ps = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
           for a in (lv.means, lv.log_scales, lv.quats, lv.opacity_logits, lv.sh.reshape(n, 48))]
@@ -162,10 +165,18 @@ def test_finetune_gradients_on_crop(finetune):
     assert np.abs(img.cpu().numpy() - img_ref).max() < 2e-4
     rest = np.ones(n, bool)
     rest[sub] = False
-    for name, g, r in zip(["means", "log_scales", "quats", "opacity_logits", "sh"], gs, g_ref):
+    for name, g, r, r32 in zip(["means", "log_scales", "quats", "opacity_logits", "sh"], gs, g_ref,
+                               g_32):
         gn = g.cpu().numpy().reshape(n, -1).astype(np.float64)
-        e = np.linalg.norm(gn[sub] - r.reshape(sub.size, -1)) / max(np.linalg.norm(r), 1e-30)
-        assert e < 1e-3, f"{name}: relative L2 error {e:.3g}"
+        rn = max(np.linalg.norm(r), 1e-30)
+        e = np.linalg.norm(gn[sub] - r.reshape(sub.size, -1)) / rn
+        e32 = np.linalg.norm(r32.astype(np.float64) - r) / rn
+        # relative L2 bar: 1e-3, or three times the FP32 evaluation's own
+        # error where the input is that ill-conditioned (sums of many
+        # pixel terms of both signs); the adjoint's sequential evaluation
+        # with division-based T adds a few roundings per term
+        tol = max(1e-3, 3.0 * e32)
+        assert e < tol, f"{name}: relative L2 error {e:.3g} (FP32 evaluation {e32:.3g})"
         assert not gn[rest].any(), f"{name}: gradient outside the crop's Gaussians"
 
 
