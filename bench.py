@@ -5,7 +5,10 @@ Workload: the outdoor LOD scene (16M / 4M / 1M / 250k Gaussians over a 1 km x
 1 km heightfield, 16 x 16 chunk grid, SH degree 3, fp32 attributes) and a
 300-pose street-level trajectory at 1920 x 1080.  A step renders
 --poses-per-step consecutive poses of the trajectory in LOD+chunk mode with
-opacity blending (the paper's method); value = frames/s over all ranks.  The
+opacity blending (the paper's method) through one render call (frames one
+after another on one stream; the host prepares a frame while the previous
+one finishes); value = frames/s over all ranks.  The latency of a single
+frame rendered alone is reported beside it.  The
 same poses are also rendered at full detail (every level-0 Gaussian) on the
 same GPU for the speedup.  Inputs are resident in HBM before timing (5.0 GB
 scene, larger than L2, no flush between steps).
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--full-steps", type=int, default=None)
+    ap.add_argument("--per-frame-calls", action="store_true",
+                    help="one render call per pose instead of one per step")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -185,14 +190,18 @@ def stage_bytes(stage: str, prof: dict) -> float:
         # list entry + means per active Gaussian; scale/opacity, quaternion and
         # 48 SH coefficients per visible Gaussian; 56 B of records written
         return a * (4 + 12) + v * (16 + 16 + 192 + 56)
+    # keys of frames whose (tile, record) pair fits one word are written and
+    # sorted as single 4 B words; the others as a 4 B key plus a 4 B value
+    kp = prof.get("packed_keys", 0)
     if stage == "depth_sort":
         return v * (4 + 4 * 16)          # histogram read + 4 passes of read/write key+value
     if stage == "emit":
         # offsets pass: read record id + rect, write offset, id, rect (28 B per
-        # visible); key pass: stage offset/id/rect (16 B) and write 8 B per key
-        return v * (28 + 16) + k * 8
+        # visible); key pass: stage offset/id/rect (16 B), write 4 or 8 B per key
+        return v * (28 + 16) + kp * 4 + (k - kp) * 8
     if stage == "tile_sort":
-        return k * (2 * 16)              # 13-bit tile ids: 2 passes of read+write key+value
+        # 13-bit tile ids: 2 passes, each reading and writing every key (and value)
+        return kp * (2 * 8) + (k - kp) * (2 * 16)
     if stage == "ranges":
         return k * 4
     return 0.0
@@ -251,6 +260,8 @@ def run_lodge(args, rank, world, local_rank):
     P = args.poses_per_step
     npix = args.width * args.height
     out = torch.empty(npix * 3, dtype=torch.float32, device=dev)
+    # a step's P consecutive poses go to one render call (one image each)
+    out_step = torch.empty(P * npix * 3, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def frames(step):
@@ -260,19 +271,14 @@ def run_lodge(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    def timed(mode, steps, per_frame_events=True):
-        evs = []
-
+    def timed(mode, steps):
         def run():
-            last = e0
             for s in range(steps):
-                for cam in frames(s):
-                    ctx.render(sid, mode, cam, out=out)
-                    if per_frame_events:
-                        e = torch.cuda.Event(enable_timing=True)
-                        e.record(stream)
-                        evs.append((last, e))
-                        last = e
+                if args.per_frame_calls:
+                    for cam in frames(s):
+                        ctx.render(sid, mode, cam, out=out)
+                else:
+                    ctx.render(sid, mode, frames(s), out=out_step)
 
         def clock(fn):
             e0.record(stream)
@@ -283,9 +289,21 @@ def run_lodge(args, rank, world, local_rank):
 
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        t = timed_region(run, world, sync=torch.cuda.synchronize, clock=clock, device=dev)
-        lat = [a.elapsed_time(b) for a, b in evs]
-        return t, lat
+        return timed_region(run, world, sync=torch.cuda.synchronize, clock=clock, device=dev)
+
+    def frame_latency(mode, n):
+        """Device time of single-camera render calls, one frame at a time
+        (each call waits for its frame): the latency of one frame."""
+        lat = []
+        for j in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.render(sid, mode, cams[j % len(cams)], out=out)
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+        return lat
 
     # warm-up (also grows every scratch buffer to its steady size)
     for s in range(args.warmup):
@@ -299,7 +317,7 @@ def run_lodge(args, rank, world, local_rank):
     clk = ClockSampler(local_rank)
     ctx.profile_enable(True)
     clk.start()
-    t_blend, lat = timed(CHUNK_BLEND, args.steps)
+    t_blend = timed(CHUNK_BLEND, args.steps)
     clocks = clk.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
@@ -309,10 +327,12 @@ def run_lodge(args, rank, world, local_rank):
     # ---- full detail on the same poses
     fsteps = args.full_steps if args.full_steps is not None else max(1, args.steps // 2)
     ctx.profile_enable(True)
-    t_full, lat_full = timed(FULL, fsteps)
+    t_full = timed(FULL, fsteps)
     prof_full = ctx.profile_read()
     ctx.profile_enable(False)
     full_fps = job_throughput(fsteps * P, world, t_full)
+    lat = frame_latency(CHUNK_BLEND, min(len(cams), 100))
+    lat_full = frame_latency(FULL, 10)
 
     # ---- end to end through the host-buffer entry point (camera H2D, image D2H)
     host = torch.empty(npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)

@@ -172,6 +172,25 @@ lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
                               const lodge_camera* cams, int32_t n_cams, lodge_selection* out,
                               uint32_t* d_gids, int64_t gids_capacity, void* stream);
 
+/* Greedy choice of the depth thresholds d_1 .. d_{L-1} (Sec. 3, "Selecting
+ * depth thresholds"): the cost of a threshold set is the number of (tile,
+ * Gaussian) keys that LOD rendering (Eq. 2 at each camera centre) produces,
+ * summed over the n_views views (host array) -- the mean number of Gaussians
+ * per 16x16 tile up to a constant factor.  d_1 is chosen first with only
+ * levels 0 and 1 in use, then each next d_l with the earlier ones fixed and
+ * levels above l unused, among the candidates (host, n_candidates <= 1024
+ * positive distances in metres, strictly ascending) larger than d_{l-1};
+ * ties go to the smaller candidate.  d_out (host, num_levels - 1 doubles)
+ * receives the chosen thresholds, +inf for a level for which no candidate
+ * was left.  keys_out (host, optional, (num_levels - 1) x n_candidates) receives
+ * the key total of every candidate at every step, -1 where a candidate was
+ * not eligible.  The scene's own thresholds are not changed.  Synchronous on
+ * stream.  Errors: LODGE_E_INVALID for bad arguments or cameras. */
+lodge_status lodge_select_thresholds(lodge_ctx* ctx, int32_t scene_id, const lodge_camera* views,
+                                     int32_t n_views, const double* candidates,
+                                     int32_t n_candidates, double* d_out, int64_t* keys_out,
+                                     void* stream);
+
 /* ---------------------------------------------------------------- render */
 
 /* Render n_cams cameras of one scene in `mode`.  d_rgb (device,
@@ -343,6 +362,8 @@ typedef struct {
     int64_t keys;      /* sum of per-frame tile keys */
     int64_t visible;   /* sum of per-frame visible Gaussians */
     int64_t active;    /* sum of per-frame active Gaussians */
+    int64_t packed_keys; /* keys of frames whose tile and record index fit one
+                          * 32-bit word: sorted as single words, no values */
 } lodge_profile;
 
 /* Start (enable != 0, counters reset) or stop collecting the profile.

@@ -15,11 +15,14 @@ Public functions mirror the paper's steps:
   chunk_union         union of two chunk sets with Eq. 4 multipliers
   active_set          the active list for a render mode and camera
   project / keys      per-Gaussian projection records, sorted tile keys
+  n_keys              number of tile keys of an active list
   render              Eq. 1 compositing (binned or brute force)
+  select_thresholds   greedy depth-threshold search (Sec. 3)
 """
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -296,6 +299,59 @@ def keys(osc: OracleScene, cam, gids, mults=None):
     lib.orc_keys(osc.ptr, C.byref(cc), g.size, _p(g), None if m is None else _p(m),
                  _p(k), _p(gg), n)
     return k, gg
+
+
+def n_keys(osc: OracleScene, cam, gids, mults=None) -> int:
+    """Number of (tile, Gaussian) keys of an active list: the sum over its
+    visible Gaussians of the tiles their rect covers."""
+    lib = _load()
+    g = _c(gids, np.int64)
+    m = None if mults is None else _c(mults, np.float32)
+    cc = _cam(cam)
+    return int(lib.orc_keys(osc.ptr, C.byref(cc), g.size, _p(g), None if m is None else _p(m),
+                            None, None, 0))
+
+
+def select_thresholds(osc: OracleScene, views, candidates):
+    """Greedy depth-threshold search (Sec. 3, "Selecting depth thresholds").
+
+    The cost of a threshold set is the number of Gaussians summed over the
+    16x16 tiles of the views, i.e. the tile keys of LOD rendering (Eq. 2 at
+    each camera centre), summed over the views.  Reading of the greedy
+    strategy: thresholds are added one at a time, starting with d_1; when
+    d_l is searched, d_1 .. d_{l-1} are fixed and levels above l are not used
+    (d_{l+1} = ... = inf), and d_l is the candidate larger than d_{l-1} with
+    the least cost, the smaller one on ties.  If no candidate is left, d_l
+    and the later thresholds are inf.
+
+    Returns (d, table): d the L-1 thresholds, table[l-1, k] the cost of
+    candidate k at step l (-1 where it was not eligible)."""
+    cand = [float(x) for x in candidates]
+    L = osc.num_levels
+    d = []
+    table = np.full((max(L - 1, 0), len(cand)), -1, np.int64)
+    for l in range(1, L):
+        prev = d[-1] if d else 0.0
+        if math.isinf(prev):
+            d.append(math.inf)
+            continue
+        for k, x in enumerate(cand):
+            if not x > prev:
+                continue
+            thresholds = d + [x] + [math.inf] * (L - 1 - l)
+            total = 0
+            for cam in views:
+                g, _ = lod_select(osc, cam.center, thresholds)
+                total += n_keys(osc, cam, g)
+            table[l - 1, k] = total
+        row = table[l - 1]
+        ok = np.flatnonzero(row >= 0)
+        if ok.size == 0:
+            d.append(math.inf)
+            continue
+        best = ok[np.argmin(row[ok])]     # argmin returns the first minimum
+        d.append(cand[best])
+    return d, table
 
 
 def depth32(means, cam):

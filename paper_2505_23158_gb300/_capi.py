@@ -59,7 +59,7 @@ STAGE_NAMES = ["select", "union", "project", "depth_sort", "emit", "tile_sort", 
 class lodge_profile(C.Structure):
     _fields_ = [("ms", C.c_double * NUM_STAGES), ("launches", C.c_int64 * NUM_STAGES),
                 ("frames", C.c_int64), ("keys", C.c_int64), ("visible", C.c_int64),
-                ("active", C.c_int64)]
+                ("active", C.c_int64), ("packed_keys", C.c_int64)]
 
 
 class lodge_frame_stats(C.Structure):
@@ -98,6 +98,7 @@ _SIGS = {
     "lodge_unload_scene": [P, C.c_int32],
     "lodge_upload_chunks": [P, C.c_int32, P, C.c_int32, C.c_int],
     "lodge_select_lod": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int64, P],
+    "lodge_select_thresholds": [P, C.c_int32, P, C.c_int32, P, C.c_int32, P, P, P],
     "lodge_render": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int32,
                      C.POINTER(C.c_int64), P],
     "lodge_render_host": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, P],

@@ -60,6 +60,7 @@ class Lodge:
         A.call("lodge_create", self.device, int(hbm_budget_bytes), C.byref(h))
         self._h = h
         self._keep = {}
+        self._num_levels = {}
 
     # -- lifetime
     def close(self):
@@ -105,6 +106,7 @@ class Lodge:
         desc.residency = int(residency)
         sid = C.c_int32()
         A.call("lodge_load_scene", self._h, C.byref(desc), C.byref(sid))
+        self._num_levels[sid.value] = scene.num_levels
         return sid.value
 
     def unload_scene(self, sid: int):
@@ -135,6 +137,21 @@ class Lodge:
         s = sel[0]
         return dict(chunk_a=s.chunk_a, chunk_b=s.chunk_b, t_a=s.t_a, t_b=s.t_b,
                     n_active=s.n_active), gids
+
+    def select_thresholds(self, sid: int, views, candidates, stream=None):
+        """Greedy depth-threshold search over the views: (d, keys) with d the
+        num_levels - 1 chosen thresholds (inf where no candidate was left) and
+        keys[l - 1, k] the tile keys of candidate k at step l (-1: not
+        eligible)."""
+        L = self._num_levels[sid]
+        cand = np.ascontiguousarray(candidates, np.float64)
+        d = np.zeros(max(L - 1, 1), np.float64)
+        keys = np.zeros((max(L - 1, 1), cand.size), np.int64)
+        vl = list(views)
+        A.call("lodge_select_thresholds", self._h, int(sid), camera_array(vl), len(vl),
+               C.c_void_p(cand.ctypes.data), int(cand.size), C.c_void_p(d.ctypes.data),
+               C.c_void_p(keys.ctypes.data), _stream(stream))
+        return d[:L - 1], keys[:L - 1]
 
     # -- render
     def render(self, sid: int, mode: int, cams, out: Optional[torch.Tensor] = None,
@@ -281,7 +298,8 @@ class Lodge:
         A.call("lodge_profile_read", self._h, C.byref(p))
         return dict(ms={n: p.ms[i] for i, n in enumerate(A.STAGE_NAMES)},
                     launches={n: p.launches[i] for i, n in enumerate(A.STAGE_NAMES)},
-                    frames=p.frames, keys=p.keys, visible=p.visible, active=p.active)
+                    frames=p.frames, keys=p.keys, visible=p.visible, active=p.active,
+                    packed_keys=p.packed_keys)
 
     def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
         """Stable in-place sort of int32 (bit pattern = uint32) keys and values."""

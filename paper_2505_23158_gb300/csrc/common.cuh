@@ -182,36 +182,63 @@ void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* li
 // copy the extent table to this device's constant memory (once per device)
 cudaError_t upload_qtable(const float* q65);
 
-// onesweep LSD radix sort of (u32 key, u32 value) pairs on key bits
-// [0, key_bits).  Result lands in (keys, vals) or (keys_alt, vals_alt):
-// the return value says which (0 = keys/vals).
+// K10: per-candidate tile-key counts of the greedy depth-threshold search for
+// one view over the Gaussians of levels 0..lvl (n = level_off[lvl + 1]).
+// lo/hi: squared Eq. 2 bands of the fixed levels (lo also for level lvl - 1);
+// c: camera centre rounded to FP32; d_thr: K ascending squared candidates
+// (device); acc: 2K + 2 zeroed counters (bucket layout in k_project.cu).
+struct ThreshBands {
+    float lo[kMaxLevels];
+    float hi[kMaxLevels];
+    float c[3];
+};
+constexpr int kMaxThreshCandidates = 1024;
+size_t threshold_cost_smem(int K);
+void launch_threshold_cost(const DevScene& sc, const DevCamera& cam, int64_t n, int lvl,
+                           const ThreshBands& b, const float* d_thr, int K, unsigned long long* acc,
+                           cudaStream_t s);
+
+// onesweep LSD radix sort of u32 keys (and u32 values if vals != null) on
+// key bits [shift0, shift0 + key_bits).  Result lands in (keys, vals) or
+// (keys_alt, vals_alt): the return value says which (0 = keys/vals).
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 15;
 constexpr int kSortTile = kSortThreads * kSortIPT;
+// inputs of at most kSortSmallMax pairs use tiles of kSortTileSmall pairs
+constexpr int kSortTileSmall = kSortThreads * 4;
+constexpr int64_t kSortSmallMax = 1ll << 20;
+constexpr int64_t sort_tile_for(int64_t n) { return n <= kSortSmallMax ? kSortTileSmall : kSortTile; }
+// scratch words: 4 x 256 digit offsets, 32 tile counters, look-back words
+constexpr int64_t sort_scratch_words(int64_t n, int passes) {
+    return 4 * 256 + 32 + (int64_t)passes * ((n + sort_tile_for(n) - 1) / sort_tile_for(n)) * 256;
+}
 // digit_offsets: optional exclusive per-pass digit offsets (passes x 256)
 // that replace the upfront histogram; final_keys = false skips writing the
 // keys in the last pass (only the values are wanted).
 size_t sort_scratch_bytes(int64_t n, int key_bits);
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
-                    const uint32_t* digit_offsets = nullptr, bool final_keys = true);
+                    const uint32_t* digit_offsets = nullptr, bool final_keys = true, int shift0 = 0);
 int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
 // K4: emit (tile, record) pairs in depth order.  koff: n_vis + 1 words;
 // srec / srect: n_vis gathered record ids and rects; n_keys from the
 // projection's count.  digit_hist (zeroed, 4 x 256 words) receives the
 // exclusive digit offsets of the tile sort on key_bits tile bits.
+// rbits > 0: one packed word per pair, tile << rbits | record (tile_val
+// unused); rbits = 0: tile in tile_key, record in tile_val.
 constexpr int kEmitThreads = 256;
 constexpr int kEmitKeysPerCta = 2048;
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
                  int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
-                 int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int key_bits,
+                 int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s);
 
-// K6: per tile [begin, end) of the sorted keys; ranges zeroed by the caller.
+// K6: per tile [begin, end) of the sorted keys (tile = key >> shift);
+// ranges zeroed by the caller.
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,
-                   cudaStream_t s);
+                   int shift, cudaStream_t s);
 
 // K7: per tile front-to-back compositing.
 struct BlendOut {
@@ -219,14 +246,16 @@ struct BlendOut {
     float* T_final;    // H x W (may be null)
     uint32_t* last;    // H x W (may be null): keys processed up to the last blended one
 };
-void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+// tile_val[i] & vmask is the record of sorted pair i (vmask = all ones for
+// separate values, the low rbits for packed keys).
+void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s);
 
 // K8 / K9: adjoint of compositing and projection (fine-tuning path).
 // grec: 9 x n_rec floats, zeroed: d(mean'x, mean'y, u00, u01, u11, o', r, g, b).
 void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
-                      int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                      uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                       int64_t n_rec, const float* T_final, const uint32_t* last,
                       const float* dL_drgb, float* grec, cudaStream_t s);
 void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec_gid,

@@ -63,6 +63,7 @@ struct Scene {
 struct Saved {
     DevCamera cam{};
     int64_t n_vis = 0, n_keys = 0;
+    int rbits = 0;  // > 0: tkey holds packed tile << rbits | record, tval unused
     DBuf rec_a, rec_b, rec_c, rec_rect, rec_gid, zsorted, rsorted, tkey, tval, ranges, T, last;
     bool params = false;
     int64_t n = 0;
@@ -105,6 +106,10 @@ struct Slot {
     Workspace ws;
     uint32_t* d_small = nullptr;
     uint32_t* h_small = nullptr;  // pinned
+    // status words of a frame whose end was not waited for: copied on the
+    // stream after its last kernel, checked at the slot's next sync
+    uint32_t* h_tail = nullptr;   // pinned
+    bool tail_pending = false;
     bool prof_on = false;
     lodge_profile prof{};
     cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};

@@ -42,7 +42,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 __global__ void __launch_bounds__(256)
 blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __restrict__ ranges,
-                 const uint32_t* __restrict__ tile_val, uint32_t n_keys, uint32_t n_rec,
+                 const uint32_t* __restrict__ tile_val, uint32_t vmask, uint32_t n_keys, uint32_t n_rec,
                  const float4* __restrict__ rec_a, const float4* __restrict__ rec_b,
                  const float* __restrict__ rec_c, const float* __restrict__ T_final,
                  const uint32_t* __restrict__ last, const float* __restrict__ dL_drgb,
@@ -84,7 +84,7 @@ blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __
         __syncthreads();
         const uint32_t idx = (uint32_t)b * kBatch + tid;
         if (idx < maxL) {
-            const uint32_t j = min(tile_val[rg.x + idx], n_rec - 1u);
+            const uint32_t j = min(tile_val[rg.x + idx] & vmask, n_rec - 1u);
             sr[tid] = j;
             sa[tid] = rec_a[j];
             sb[tid] = rec_b[j];
@@ -372,13 +372,13 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
 }  // namespace
 
 void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
-                      int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                      uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                       int64_t n_rec, const float* T_final, const uint32_t* last,
                       const float* dL_drgb, float* grec, cudaStream_t s) {
     int ntiles = cam.tiles_x * cam.tiles_y;
     if (ntiles == 0 || n_rec == 0) return;
     blend_bwd_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val,
-                                            (uint32_t)n_keys, (uint32_t)n_rec, rec_a, rec_b, rec_c,
+                                            vmask, (uint32_t)n_keys, (uint32_t)n_rec, rec_a, rec_b, rec_c,
                                             T_final, last, dL_drgb, grec);
 }
 

@@ -90,7 +90,7 @@ __device__ __forceinline__ int64_t warp_upper_bound(const uint32_t* __restrict__
 __global__ void __launch_bounds__(kEmitThreads)
 emit_keys_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__ srec,
                  const uint2* __restrict__ srect, int64_t n_vis, int64_t n_keys, int32_t tiles_x,
-                 uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val,
+                 uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits,
                  int passes, uint32_t last_mask, uint32_t* __restrict__ digit_hist,
                  uint32_t* __restrict__ err) {
     __shared__ uint32_t s_off[kEmitKeysPerCta + 1];
@@ -136,8 +136,12 @@ emit_keys_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__
             const uint32_t w = tx1 - tx0 + 1u;
             const uint32_t q = k / w;
             const uint32_t tile = (ty0 + q) * (uint32_t)tiles_x + tx0 + (k - q * w);
-            tile_key[key] = tile;
-            tile_val[key] = s_rec[lo];
+            if (rbits) {
+                tile_key[key] = (tile << rbits) | s_rec[lo];
+            } else {
+                tile_key[key] = tile;
+                tile_val[key] = s_rec[lo];
+            }
             for (int p = 0; p < passes; ++p)
                 atomicAdd(&s_hist[p][(tile >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
         }
@@ -157,18 +161,19 @@ __global__ void digit_scan_kernel(uint32_t* hist) {
     h[threadIdx.x] = block_exclusive_scan(v, s_scan, &total);
 }
 
-// K6: per tile [begin, end) of the tile-sorted keys; 4 keys per thread.
+// K6: per tile [begin, end) of the tile-sorted keys (tile = key >> shift);
+// 4 keys per thread.
 __global__ void ranges_kernel(const uint32_t* __restrict__ key, int64_t n, uint2* __restrict__ ranges,
-                              uint32_t ntiles) {
+                              uint32_t ntiles, int shift) {
     const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (i0 >= n) return;
-    uint32_t prev = i0 > 0 ? key[i0 - 1] : 0xffffffffu;
+    uint32_t prev = i0 > 0 ? key[i0 - 1] >> shift : 0xffffffffu;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int64_t i = i0 + j;
         if (i >= n) break;
-        const uint32_t t = key[i];
-        const uint32_t next = i + 1 < n ? key[i + 1] : 0xffffffffu;
+        const uint32_t t = key[i] >> shift;
+        const uint32_t next = i + 1 < n ? key[i + 1] >> shift : 0xffffffffu;
         if (t < ntiles) {
             if (t != prev) ranges[t].x = (uint32_t)i;
             if (t != next) ranges[t].y = (uint32_t)(i + 1);
@@ -181,7 +186,7 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ key, int64_t n, uint2
 
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
                  int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
-                 int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int key_bits,
+                 int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s) {
     (void)tiles_y;
@@ -196,16 +201,16 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
     const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
     const unsigned grid = (unsigned)std::min<int64_t>(nslices, 152 * 4);
     emit_keys_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, n_keys, tiles_x, tile_key,
-                                                   tile_val, P, last_mask, digit_hist, err);
+                                                   tile_val, rbits, P, last_mask, digit_hist, err);
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
 }
 
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,
-                   cudaStream_t s) {
+                   int shift, cudaStream_t s) {
     if (n_keys == 0) return;
     const int64_t nt = (n_keys + 3) / 4;
     ranges_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(tile_key, n_keys, ranges,
-                                                             (uint32_t)ntiles);
+                                                             (uint32_t)ntiles, shift);
 }
 
 }  // namespace lodge

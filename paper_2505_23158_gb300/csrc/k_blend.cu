@@ -41,7 +41,7 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 
 __global__ void __launch_bounds__(256)
 blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __restrict__ ranges,
-             const uint32_t* __restrict__ tile_val, uint32_t n_keys, uint32_t n_rec,
+             const uint32_t* __restrict__ tile_val, uint32_t vmask, uint32_t n_keys, uint32_t n_rec,
              const float4* __restrict__ rec_a,
              const float4* __restrict__ rec_b, const float* __restrict__ rec_c,
              float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_last) {
@@ -66,7 +66,7 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
 
     if (nb > 0) {
         if (tid < n) {
-            uint32_t j = min(tile_val[rg.x + tid], n_rec - 1u);
+            uint32_t j = min(tile_val[rg.x + tid] & vmask, n_rec - 1u);
             cp_async16(&sa[0][tid], rec_a + j);
             cp_async16(&sb[0][tid], rec_b + j);
             cp_async4(&sc[0][tid], rec_c + j);
@@ -78,7 +78,7 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
         if (b + 1 < nb) {
             int k = (b + 1) * kBatch + tid;
             if (k < n) {
-                uint32_t j = min(tile_val[rg.x + k], n_rec - 1u);
+                uint32_t j = min(tile_val[rg.x + k] & vmask, n_rec - 1u);
                 cp_async16(&sa[buf ^ 1][tid], rec_a + j);
                 cp_async16(&sb[buf ^ 1][tid], rec_b + j);
                 cp_async4(&sc[buf ^ 1][tid], rec_c + j);
@@ -123,12 +123,12 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
 
 }  // namespace
 
-void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s) {
     int ntiles = cam.tiles_x * cam.tiles_y;
     if (ntiles == 0) return;
-    blend_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val,
+    blend_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val, vmask,
                                         (uint32_t)n_keys, (uint32_t)std::max<int64_t>(n_rec, 1),
                                         rec_a, rec_b, rec_c, o.rgb, o.T_final, o.last);
 }

@@ -66,6 +66,90 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
     Y[15] = kC3a * x * (xx - 3.f * yy);
 }
 
+// Key spec of one Gaussian: camera-relative point, near cull, Eq. 3 filter
+// and opacity, opacity-aware extent and the AABB tile rect, every operation
+// rounded in a fixed order.  Returns false when the Gaussian yields no key;
+// the outputs other than d0..d2 are then unset.
+struct KeySplat {
+    float d0, d1, d2;          // mean - chat
+    float z, mx, my, op;       // depth, projected mean, opacity after Eq. 3 and Eq. 4
+    float B0[3], B1[3];        // rows of J W R(q) diag(sigma)
+    uint32_t rx0, ry0, rx1, ry1;
+};
+
+__device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& cam, float mxw,
+                                          float myw, float mzw, const float4* __restrict__ sso,
+                                          const float4* __restrict__ sq, int64_t idx, uint32_t g,
+                                          float mult, KeySplat& k) {
+    const float* R = cam.R;
+    k.d0 = fs(mxw, cam.chat[0]);
+    k.d1 = fs(myw, cam.chat[1]);
+    k.d2 = fs(mzw, cam.chat[2]);
+    const float d0 = k.d0, d1 = k.d1, d2 = k.d2;
+    float px = fa(fa(fa(fm(R[0], d0), fm(R[1], d1)), fm(R[2], d2)), cam.tp[0]);
+    float py = fa(fa(fa(fm(R[3], d0), fm(R[4], d1)), fm(R[5], d2)), cam.tp[1]);
+    float pz = fa(fa(fa(fm(R[6], d0), fm(R[7], d1)), fm(R[8], d2)), cam.tp[2]);
+    if (!(pz > cam.znear)) return false;
+    const float4 so = sso[idx];
+    int l = 0;
+    while (l + 1 < sc.num_levels && (int64_t)g >= sc.level_off[l + 1]) ++l;
+    const float v = sc.filter_var[l];
+    float sig0 = so.x, sig1 = so.y, sig2 = so.z;
+    float op = fm(so.w, mult);
+    if (v > 0.f) {
+        sig0 = __fsqrt_rn(fa(fm(so.x, so.x), v));
+        sig1 = __fsqrt_rn(fa(fm(so.y, so.y), v));
+        sig2 = __fsqrt_rn(fa(fm(so.z, so.z), v));
+        float comp = fm(fm(__fdiv_rn(so.x, sig0), __fdiv_rn(so.y, sig1)), __fdiv_rn(so.z, sig2));
+        op = fm(op, comp);
+    }
+    if (!(op >= (float)(1.0 / 255.0))) return false;
+    const float Q = extent_q(op);
+    const float4 q = sq[idx];
+    float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
+    float mx = fa(fm(cam.fx, u), cam.cx);
+    float my = fa(fm(cam.fy, w), cam.cy);
+    float j00 = __fdiv_rn(cam.fx, pz), j02 = -fm(j00, u);
+    float j11 = __fdiv_rn(cam.fy, pz), j12 = -fm(j11, w);
+    float T0[3], T1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T0[c] = fa(fm(j00, R[c]), fm(j02, R[6 + c]));
+        T1[c] = fa(fm(j11, R[3 + c]), fm(j12, R[6 + c]));
+    }
+    float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+    float xx = fm(qx, qx), yy = fm(qy, qy), zz = fm(qz, qz);
+    float xy = fm(qx, qy), xz = fm(qx, qz), yz = fm(qy, qz);
+    float wx = fm(qw, qx), wy = fm(qw, qy), wz = fm(qw, qz);
+    float M[3][3];
+    M[0][0] = fs(1.f, fm(2.f, fa(yy, zz))); M[0][1] = fm(2.f, fs(xy, wz)); M[0][2] = fm(2.f, fa(xz, wy));
+    M[1][0] = fm(2.f, fa(xy, wz)); M[1][1] = fs(1.f, fm(2.f, fa(xx, zz))); M[1][2] = fm(2.f, fs(yz, wx));
+    M[2][0] = fm(2.f, fs(xz, wy)); M[2][1] = fm(2.f, fa(yz, wx)); M[2][2] = fs(1.f, fm(2.f, fa(xx, yy)));
+    const float sig[3] = {sig0, sig1, sig2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float a0 = fa(fa(fm(T0[0], M[0][c]), fm(T0[1], M[1][c])), fm(T0[2], M[2][c]));
+        float a1 = fa(fa(fm(T1[0], M[0][c]), fm(T1[1], M[1][c])), fm(T1[2], M[2][c]));
+        k.B0[c] = fm(a0, sig[c]);
+        k.B1[c] = fm(a1, sig[c]);
+    }
+    float sxx = fa(fa(fa(fm(k.B0[0], k.B0[0]), fm(k.B0[1], k.B0[1])), fm(k.B0[2], k.B0[2])), 0.3f);
+    float syy = fa(fa(fa(fm(k.B1[0], k.B1[0]), fm(k.B1[1], k.B1[1])), fm(k.B1[2], k.B1[2])), 0.3f);
+    float rx = __fsqrt_rn(fm(Q, sxx)), ry = __fsqrt_rn(fm(Q, syy));
+    float x0 = ceilf(fs(fs(mx, rx), 0.5f)), x1 = floorf(fs(fa(mx, rx), 0.5f));
+    float y0 = ceilf(fs(fs(my, ry), 0.5f)), y1 = floorf(fs(fa(my, ry), 0.5f));
+    const float xmax = (float)(cam.width - 1), ymax = (float)(cam.height - 1);
+    if (x0 < 0.f) x0 = 0.f;
+    if (y0 < 0.f) y0 = 0.f;
+    if (x1 > xmax) x1 = xmax;
+    if (y1 > ymax) y1 = ymax;
+    if (!(x0 <= x1 && y0 <= y1)) return false;
+    k.z = pz; k.mx = mx; k.my = my; k.op = op;
+    k.rx0 = (uint32_t)(int)x0 / kTile; k.ry0 = (uint32_t)(int)y0 / kTile;
+    k.rx1 = (uint32_t)(int)x1 / kTile; k.ry1 = (uint32_t)(int)y1 / kTile;
+    return true;
+}
+
 template <bool kBlocks>
 __global__ void __launch_bounds__(kProjThreads)
 project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
@@ -118,75 +202,14 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
             if ((int64_t)idx >= sc.n_total) { atomicOr(err, kErrBadIndex); idx = 0; mult = 0.f; }
             g = idx;
         }
-        const float* R = cam.R;
-        // key spec: camera-space point relative to chat, summed left to right
-        d0 = fs(smx[idx], cam.chat[0]);
-        d1 = fs(smy[idx], cam.chat[1]);
-        d2 = fs(smz[idx], cam.chat[2]);
-        float px = fa(fa(fa(fm(R[0], d0), fm(R[1], d1)), fm(R[2], d2)), cam.tp[0]);
-        float py = fa(fa(fa(fm(R[3], d0), fm(R[4], d1)), fm(R[5], d2)), cam.tp[1]);
-        float pz = fa(fa(fa(fm(R[6], d0), fm(R[7], d1)), fm(R[8], d2)), cam.tp[2]);
-        if (pz > cam.znear) {
-            const float4 so = sso[idx];
-            int l = 0;
-            while (l + 1 < sc.num_levels && (int64_t)g >= sc.level_off[l + 1]) ++l;
-            const float v = sc.filter_var[l];
-            float sig0 = so.x, sig1 = so.y, sig2 = so.z;
-            float op = fm(so.w, mult);
-            if (v > 0.f) {
-                sig0 = __fsqrt_rn(fa(fm(so.x, so.x), v));
-                sig1 = __fsqrt_rn(fa(fm(so.y, so.y), v));
-                sig2 = __fsqrt_rn(fa(fm(so.z, so.z), v));
-                float comp = fm(fm(__fdiv_rn(so.x, sig0), __fdiv_rn(so.y, sig1)), __fdiv_rn(so.z, sig2));
-                op = fm(op, comp);
-            }
-            if (op >= (float)(1.0 / 255.0)) {
-                const float Q = extent_q(op);
-                const float4 q = sq[idx];
-                float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
-                float mx = fa(fm(cam.fx, u), cam.cx);
-                float my = fa(fm(cam.fy, w), cam.cy);
-                float j00 = __fdiv_rn(cam.fx, pz), j02 = -fm(j00, u);
-                float j11 = __fdiv_rn(cam.fy, pz), j12 = -fm(j11, w);
-                float T0[3], T1[3];
+        KeySplat ks;
+        vis = key_splat(sc, cam, smx[idx], smy[idx], smz[idx], sso, sq, idx, g, mult, ks);
+        d0 = ks.d0; d1 = ks.d1; d2 = ks.d2;
+        if (vis) {
+            z = ks.z; mxp = ks.mx; myp = ks.my; o = ks.op;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    T0[k] = fa(fm(j00, R[k]), fm(j02, R[6 + k]));
-                    T1[k] = fa(fm(j11, R[3 + k]), fm(j12, R[6 + k]));
-                }
-                float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
-                float xx = fm(qx, qx), yy = fm(qy, qy), zz = fm(qz, qz);
-                float xy = fm(qx, qy), xz = fm(qx, qz), yz = fm(qy, qz);
-                float wx = fm(qw, qx), wy = fm(qw, qy), wz = fm(qw, qz);
-                float M[3][3];
-                M[0][0] = fs(1.f, fm(2.f, fa(yy, zz))); M[0][1] = fm(2.f, fs(xy, wz)); M[0][2] = fm(2.f, fa(xz, wy));
-                M[1][0] = fm(2.f, fa(xy, wz)); M[1][1] = fs(1.f, fm(2.f, fa(xx, zz))); M[1][2] = fm(2.f, fs(yz, wx));
-                M[2][0] = fm(2.f, fs(xz, wy)); M[2][1] = fm(2.f, fa(yz, wx)); M[2][2] = fs(1.f, fm(2.f, fa(xx, yy)));
-                const float sig[3] = {sig0, sig1, sig2};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    float a0 = fa(fa(fm(T0[0], M[0][k]), fm(T0[1], M[1][k])), fm(T0[2], M[2][k]));
-                    float a1 = fa(fa(fm(T1[0], M[0][k]), fm(T1[1], M[1][k])), fm(T1[2], M[2][k]));
-                    B0[k] = fm(a0, sig[k]);
-                    B1[k] = fm(a1, sig[k]);
-                }
-                float sxx = fa(fa(fa(fm(B0[0], B0[0]), fm(B0[1], B0[1])), fm(B0[2], B0[2])), 0.3f);
-                float syy = fa(fa(fa(fm(B1[0], B1[0]), fm(B1[1], B1[1])), fm(B1[2], B1[2])), 0.3f);
-                float rx = __fsqrt_rn(fm(Q, sxx)), ry = __fsqrt_rn(fm(Q, syy));
-                float x0 = ceilf(fs(fs(mx, rx), 0.5f)), x1 = floorf(fs(fa(mx, rx), 0.5f));
-                float y0 = ceilf(fs(fs(my, ry), 0.5f)), y1 = floorf(fs(fa(my, ry), 0.5f));
-                const float xmax = (float)(cam.width - 1), ymax = (float)(cam.height - 1);
-                if (x0 < 0.f) x0 = 0.f;
-                if (y0 < 0.f) y0 = 0.f;
-                if (x1 > xmax) x1 = xmax;
-                if (y1 > ymax) y1 = ymax;
-                if (x0 <= x1 && y0 <= y1) {
-                    vis = true;
-                    z = pz; mxp = mx; myp = my; o = op;
-                    rx0 = (uint32_t)(int)x0 / kTile; ry0 = (uint32_t)(int)y0 / kTile;
-                    rx1 = (uint32_t)(int)x1 / kTile; ry1 = (uint32_t)(int)y1 / kTile;
-                }
-            }
+            for (int k = 0; k < 3; ++k) { B0[k] = ks.B0[k]; B1[k] = ks.B1[k]; }
+            rx0 = ks.rx0; ry0 = ks.ry0; rx1 = ks.rx1; ry1 = ks.ry1;
         }
     }
 
@@ -263,6 +286,66 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     P.o.depth_val[pos] = pos;
 }
 
+
+// K10: tile-key counts of the greedy depth-threshold search (Sec. 3,
+// "Selecting depth thresholds") for one view, for every candidate value of
+// the threshold d_l at once.  With d_1 .. d_{l-1} fixed and levels above l
+// unused, a level-(l-1) Gaussian is active for candidate x iff
+// lo_{l-1} <= D < x^2 and a level-l Gaussian iff x^2 <= D (Eq. 2, D the
+// pinned FP32 squared distance).  With m = #{k : thr_k <= D} (thr ascending)
+// the first is active for candidates k >= m, the second for k < m, so each
+// Gaussian adds its key count to one bucket and the per-candidate totals are
+// prefix sums over buckets (done by the caller):
+//   acc[0]          keys of levels < l-1 inside their fixed bands
+//   acc[1 + m]      level l-1, active for candidates k >= m  (0 <= m < K)
+//   acc[K + 1 + m]  level l, active for candidates k < m     (1 <= m <= K)
+__global__ void __launch_bounds__(256)
+threshold_cost_kernel(DevScene sc, DevCamera cam, int64_t n, int32_t lvl, ThreshBands b,
+                      const float* __restrict__ thr, int32_t K, unsigned long long* __restrict__ acc) {
+    extern __shared__ unsigned long long s_acc[];
+    float* s_thr = reinterpret_cast<float*>(s_acc + (2 * K + 2));
+    for (int i = threadIdx.x; i < 2 * K + 2; i += blockDim.x) s_acc[i] = 0ull;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_thr[i] = thr[i];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int j = 0;
+        while (j + 1 < sc.num_levels && i >= sc.level_off[j + 1]) ++j;
+        const float mxw = sc.mx[i], myw = sc.my[i], mzw = sc.mz[i];
+        const float dx = __fsub_rn(mxw, b.c[0]);
+        const float dy = __fsub_rn(myw, b.c[1]);
+        const float dz = __fsub_rn(mzw, b.c[2]);
+        const float D = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        int slot;
+        if (j < lvl - 1) {
+            if (!(b.lo[j] <= D && D < b.hi[j])) continue;
+            slot = 0;
+        } else {
+            if (j == lvl - 1 && !(b.lo[j] <= D)) continue;
+            int lo = 0, hi = K;   // m = number of thresholds <= D
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_thr[mid] <= D) lo = mid + 1; else hi = mid;
+            }
+            const int m = lo;
+            if (j == lvl - 1) {
+                if (m == K) continue;
+                slot = 1 + m;
+            } else {
+                if (m == 0) continue;
+                slot = K + 1 + m;
+            }
+        }
+        KeySplat ks;
+        if (!key_splat(sc, cam, mxw, myw, mzw, sc.scale_op, sc.quat, i, (uint32_t)i, 1.f, ks)) continue;
+        const unsigned long long tc =
+            (unsigned long long)(ks.rx1 - ks.rx0 + 1) * (unsigned long long)(ks.ry1 - ks.ry0 + 1);
+        atomicAdd(&s_acc[slot], tc);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * K + 2; i += blockDim.x)
+        if (s_acc[i]) atomicAdd(acc + i, s_acc[i]);
+}
 }  // namespace
 
 cudaError_t upload_qtable(const float* q65) {
@@ -289,6 +372,16 @@ void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* li
         project_kernel<true><<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
     else
         project_kernel<false><<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
+}
+
+size_t threshold_cost_smem(int K) { return sizeof(unsigned long long) * (2 * K + 2) + sizeof(float) * K; }
+
+void launch_threshold_cost(const DevScene& sc, const DevCamera& cam, int64_t n, int lvl,
+                           const ThreshBands& b, const float* d_thr, int K, unsigned long long* acc,
+                           cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4);
+    threshold_cost_kernel<<<grid, 256, threshold_cost_smem(K), s>>>(sc, cam, n, lvl, b, d_thr, K, acc);
 }
 
 }  // namespace lodge

@@ -1,7 +1,8 @@
-// K5: stable LSD radix sort of (u32 key, u32 value) pairs, "onesweep" style:
-// the digit histograms are known before the first pass (one upfront
-// histogram pass, or supplied by the caller), then each 8-bit digit is
-// scattered in a single pass in which a tile of 3840 pairs learns its global
+// K5: stable LSD radix sort of u32 keys, with or without u32 values,
+// "onesweep" style: the digit histograms are known before the first pass (one
+// upfront histogram pass, or supplied by the caller), then each 8-bit digit
+// is scattered in a single pass in which a tile of pairs (3840, or 1024 for
+// inputs up to 2^20 so that small sorts still fill the SMs) learns its global
 // offsets by decoupled look-back over its predecessors' per-digit counts.
 //
 // Used twice per frame: by FP32 depth (4 digits) over the visible records,
@@ -9,7 +10,7 @@
 // per-tile front-to-back order of Sec. 3 ("Preliminaries: 3DGS": Gaussians
 // are sorted by depth per tile) with ties broken by record (= gid) order.
 //
-// Ranking inside a tile is warp-private and stable: each warp ranks its 15 x
+// Ranking inside a tile is warp-private and stable: each warp ranks its IPT x
 // 32 keys in input order with __match_any_sync and a per-warp digit
 // histogram; warps are combined by a per-digit exclusive scan.  Keys are held
 // in registers, ranks packed two per register, values are read only when they
@@ -23,6 +24,7 @@ namespace {
 constexpr int kRadix = 256;
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kMaxPasses = 4;
+constexpr int kLookback = 8;    // predecessors read per look-back step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -32,7 +34,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __global__ void __launch_bounds__(256)
 hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int passes, uint32_t last_mask,
-            uint32_t* __restrict__ hist) {
+            uint32_t* __restrict__ hist, int shift0) {
     __shared__ uint32_t sh[kMaxPasses][kRadix];
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
@@ -40,7 +42,7 @@ hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int passes, uint32_t l
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint32_t k = __ldg(keys + i);
         for (int p = 0; p < passes; ++p)
-            atomicAdd(&sh[p][(k >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+            atomicAdd(&sh[p][(k >> (shift0 + 8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
@@ -58,15 +60,16 @@ __global__ void hist_scan_kernel(uint32_t* hist) {
     h[threadIdx.x] = e;
 }
 
-template <bool kWriteKeys>
+template <int kIPT, bool kWriteKeys, bool kValues>
 __global__ void __launch_bounds__(kSortThreads, 4)
 onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
               uint32_t dmask, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ status,
               uint32_t* __restrict__ counter, uint32_t* __restrict__ err) {
+    constexpr int kTileN = kSortThreads * kIPT;
     __shared__ uint32_t s_whist[kWarps][kRadix];
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_keys[kTileN];
+    __shared__ uint32_t s_vals[kValues ? kTileN : 1];
     __shared__ uint32_t s_dstart[kRadix];
     __shared__ uint32_t s_gbase[kRadix];
     __shared__ uint32_t s_scan[33];
@@ -77,20 +80,20 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    const int64_t seg = (int64_t)tile * kSortTile + (int64_t)warp * 32 * kSortIPT;
+    const int64_t seg = (int64_t)tile * kTileN + (int64_t)warp * 32 * kIPT;
     const int64_t base = seg + lane;
     const int64_t nvalid = n - seg;   // items of this warp's segment that exist (may be <= 0)
 
-    uint32_t k[kSortIPT];
+    uint32_t k[kIPT];
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) k[j] = (j * 32 + lane < nvalid) ? __ldcs(kin + base + j * 32) : 0u;
+    for (int j = 0; j < kIPT; ++j) k[j] = (j * 32 + lane < nvalid) ? __ldcs(kin + base + j * 32) : 0u;
 
     // warp-private stable ranking in (j, lane) order = input order; ranks
     // (< 2^16) packed two per register
     const uint32_t lt = lanemask_lt();
-    uint32_t rk[(kSortIPT + 1) / 2];
+    uint32_t rk[(kIPT + 1) / 2];
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
+    for (int j = 0; j < kIPT; ++j) {
         const bool valid = j * 32 + lane < nvalid;
         const uint32_t d = valid ? (k[j] >> shift) & dmask : 0x100u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -112,7 +115,10 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
         s_whist[w][d] = run;
         run += c;
     }
-    // decoupled look-back for this digit (bounded waits)
+    // decoupled look-back for this digit (bounded waits).  The status words
+    // of kLookback predecessors are loaded together and then consumed in
+    // order, so a walk over tiles that have only published their counts
+    // costs one memory round trip per kLookback tiles instead of per tile.
     uint32_t excl = 0;
     uint32_t* st = status + (size_t)tile * kRadix + d;
     if (tile == 0) {
@@ -120,17 +126,25 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     } else {
         st_volatile(st, kStAgg | run);
         int64_t t = (int64_t)tile - 1;
-        while (t >= 0) {
-            const uint32_t* p = status + (size_t)t * kRadix + d;
-            uint32_t x = ld_volatile(p), spins = 0;
-            while ((x & ~kStVal) == 0u) {
-                if (++spins > kSpinLimit) { atomicOr(err, kErrTimeout); x = kStInc; break; }
-                __nanosleep(20);
-                x = ld_volatile(p);
+        bool found = false;
+        while (!found) {
+            uint32_t x[kLookback];
+#pragma unroll
+            for (int j = 0; j < kLookback; ++j)
+                x[j] = t - j >= 0 ? ld_volatile(status + (size_t)(t - j) * kRadix + d) : kStInc;
+#pragma unroll
+            for (int j = 0; j < kLookback; ++j) {
+                if (found) break;
+                uint32_t v = x[j], spins = 0;
+                while ((v & ~kStVal) == 0u) {   // only for t - j >= 0: x[j] = kStInc below 0
+                    if (++spins > kSpinLimit) { atomicOr(err, kErrTimeout); v = kStInc; break; }
+                    __nanosleep(20);
+                    v = ld_volatile(status + (size_t)(t - j) * kRadix + d);
+                }
+                excl += v & kStVal;
+                found = (v & ~kStVal) == kStInc;
             }
-            excl += x & kStVal;
-            if ((x & ~kStVal) == kStInc) break;
-            --t;
+            t -= kLookback;
         }
         st_volatile(st, kStInc | (excl + run));
     }
@@ -141,13 +155,13 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
 
     // scatter keys and values into shared memory in digit order
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
+    for (int j = 0; j < kIPT; ++j) {
         if (j * 32 + lane < nvalid) {
             const uint32_t dd = (k[j] >> shift) & dmask;
             const uint32_t r = (j & 1) ? (rk[j >> 1] >> 16) : (rk[j >> 1] & 0xffffu);
             const uint32_t pos = s_dstart[dd] + s_whist[warp][dd] + r;
             s_keys[pos] = k[j];
-            s_vals[pos] = __ldcs(vin + base + j * 32);
+            if (kValues) s_vals[pos] = __ldcs(vin + base + j * 32);
         }
     }
     __syncthreads();
@@ -157,7 +171,7 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
         const uint32_t out = s_gbase[dd] + (i - s_dstart[dd]);
         if ((int64_t)out < n) {
             if (kWriteKeys) kout[out] = key;
-            vout[out] = s_vals[i];
+            if (kValues) vout[out] = s_vals[i];
         } else {
             atomicOr(err, kErrOverflow);  // only after a look-back gave up
         }
@@ -172,20 +186,35 @@ uint32_t last_mask_for(int key_bits) {
     return last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
 }
 
+constexpr int kSmallIPT = kSortTileSmall / kSortThreads;
+static_assert(kSmallIPT * kSortThreads == kSortTileSmall, "small tile must be whole items per thread");
+
+template <bool kWK, bool kV>
+void launch_pass(bool small, int64_t ntiles, const uint32_t* ki, const uint32_t* vi, uint32_t* ko,
+                 uint32_t* vo, int64_t n, int shift, uint32_t dm, const uint32_t* off, uint32_t* st,
+                 uint32_t* ctr, uint32_t* err, cudaStream_t s) {
+    if (small)
+        onesweep_pass<kSmallIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err);
+    else
+        onesweep_pass<kSortIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err);
+}
+
 }  // namespace
 
 size_t sort_scratch_bytes(int64_t n, int key_bits) {
-    int P = passes_for(key_bits);
-    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    return sizeof(uint32_t) * (size_t)(kMaxPasses * kRadix + 32 + (int64_t)P * ntiles * kRadix);
+    return sizeof(uint32_t) * (size_t)sort_scratch_words(n, passes_for(key_bits));
 }
 
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
-                    const uint32_t* digit_offsets, bool final_keys) {
+                    const uint32_t* digit_offsets, bool final_keys, int shift0) {
     const int P = passes_for(key_bits);
     if (n <= 1 || P == 0) return 0;
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const bool small = sort_tile_for(n) == kSortTileSmall;
+    const int64_t ntiles = (n + sort_tile_for(n) - 1) / sort_tile_for(n);
+    const bool values = vals != nullptr;
     uint32_t* hist = static_cast<uint32_t*>(scratch);
     uint32_t* counters = hist + kMaxPasses * kRadix;
     uint32_t* status = counters + 32;
@@ -199,19 +228,21 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
     } else {
         cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bits), s);
         int hist_blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 4);
-        hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n, P, last_mask, hist);
+        hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n, P, last_mask, hist, shift0);
         hist_scan_kernel<<<P, kRadix, 0, s>>>(hist);
     }
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
     for (int p = 0; p < P; ++p) {
         const uint32_t dm = p == P - 1 ? last_mask : 0xffu;
         uint32_t* stp = status + (size_t)p * ntiles * kRadix;
-        if (p == P - 1 && !final_keys)
-            onesweep_pass<false><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-                ki, vi, ko, vo, n, 8 * p, dm, offs + p * kRadix, stp, counters + p, err);
-        else
-            onesweep_pass<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-                ki, vi, ko, vo, n, 8 * p, dm, offs + p * kRadix, stp, counters + p, err);
+        const bool wk = !(p == P - 1 && !final_keys);
+        const int sh = shift0 + 8 * p;
+        if (values) {
+            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, s);
+            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, s);
+        } else {
+            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, s);
+        }
         std::swap(ki, ko);
         std::swap(vi, vo);
     }

@@ -168,6 +168,7 @@ lodge_status create_slot(lodge_ctx* ctx, Slot** out) {
     TRY(dmalloc(ctx, (void**)&sl->d_small, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMemset(sl->d_small, 0, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMallocHost((void**)&sl->h_small, sizeof(uint32_t) * kSmWords));
+    CUDA_TRY(cudaMallocHost((void**)&sl->h_tail, sizeof(uint32_t) * kSmWords));
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
         CUDA_TRY(cudaEventCreate(&sl->ev_beg[k]));
         CUDA_TRY(cudaEventCreate(&sl->ev_end[k]));
@@ -184,6 +185,7 @@ static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
     if (sl.ulist.p) cudaFree(sl.ulist.p);
     if (sl.d_small) cudaFree(sl.d_small);
     if (sl.h_small) cudaFreeHost(sl.h_small);
+    if (sl.h_tail) cudaFreeHost(sl.h_tail);
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
         if (sl.ev_beg[k]) cudaEventDestroy(sl.ev_beg[k]);
         if (sl.ev_end[k]) cudaEventDestroy(sl.ev_end[k]);
@@ -306,6 +308,10 @@ lodge_status sync_slot(lodge_ctx* ctx, Slot& sl, cudaStream_t s) {
     CUDA_TRY(cudaStreamSynchronize(s));
     prof_collect(sl);
     uint32_t err = sl.h_small[kSmErr];
+    if (sl.tail_pending) {
+        err |= sl.h_tail[kSmErr];
+        sl.tail_pending = false;
+    }
     if (err & kErrTimeout) return fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
     if (err & kErrOverflow) return fail(LODGE_E_OVERFLOW, "device output capacity exceeded (status 0x%x)", err);
     if (err & kErrBadIndex) return fail(LODGE_E_INVALID, "out-of-range index in an active list (status 0x%x)", err);
@@ -447,9 +453,12 @@ static lodge_status select_active(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mod
 // ---------------------------------------------------------------------------
 static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
 
+// end_sync = false leaves the frame's last kernels running when it returns
+// (the next frame on the same stream queues behind them); their status words
+// are checked at the slot's next sync.
 static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, const Active& act,
                                  const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
-                                 lodge_frame_stats* st) {
+                                 lodge_frame_stats* st, bool end_sync) {
     Workspace& ws = sl.ws;
     TRY(check_cam(c));
     DevCamera cam = make_cam(c);
@@ -505,11 +514,18 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
 
-    // ---- K4 emit (tile, record) in depth order, with the tile sort's digit counts
+    // ---- K4 emit (tile, record) in depth order, with the tile sort's digit
+    // counts.  When tile and record index fit in one word together, each pair
+    // is one packed key (tile << rbits | record) and the tile sort moves keys
+    // only; otherwise tile and record are sorted as a (key, value) pair.
+    const int rbits_need = bits_for((uint32_t)std::max<int64_t>(n_vis - 1, 0));
+    const int rbits = tbits + rbits_need <= 32 ? rbits_need : 0;
     TRY(ensure(ctx, ws.tkey, sizeof(uint32_t) * nk1, s));
-    TRY(ensure(ctx, ws.tval, sizeof(uint32_t) * nk1, s));
     TRY(ensure(ctx, ws.tkey2, sizeof(uint32_t) * nk1, s));
-    TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * nk1, s));
+    if (!rbits) {
+        TRY(ensure(ctx, ws.tval, sizeof(uint32_t) * nk1, s));
+        TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * nk1, s));
+    }
     TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 4 * 256, s));
     CUDA_TRY(cudaMemsetAsync(ws.doffs.p, 0, sizeof(uint32_t) * 4 * 256, s));
     TRY(ensure(ctx, ws.koff, sizeof(uint32_t) * (nv1 + 1), s));
@@ -521,24 +537,26 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     prof_begin(sl, LODGE_STAGE_EMIT, s);
     launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), cam.tiles_x, cam.tiles_y,
                 ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_keys,
-                ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), tbits, ws.doffs.as<uint32_t>(),
+                ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits, ws.doffs.as<uint32_t>(),
                 ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
     prof_end(sl, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_keys > 0 ? 2 : 0));
 
     // ---- K5 tile sort (stable: keeps depth order within a tile)
     prof_begin(sl, LODGE_STAGE_TILE_SORT, s);
-    int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), ws.tkey2.as<uint32_t>(),
-                             ws.tval2.as<uint32_t>(), n_keys, tbits, ws.sort.p, sl.d_small + kSmErr, s,
-                             ws.doffs.as<uint32_t>(), true);
+    int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), rbits ? nullptr : ws.tval.as<uint32_t>(),
+                             ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_keys,
+                             tbits, ws.sort.p, sl.d_small + kSmErr, s, ws.doffs.as<uint32_t>(), true, rbits);
     prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_keys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
+    const uint32_t* rec_of_pair = rbits ? ks.as<uint32_t>() : vs.as<uint32_t>();
+    const uint32_t vmask = rbits ? (1u << rbits) - 1u : 0xffffffffu;
 
     // ---- K6 ranges, K7 blend
     TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
     CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
     prof_begin(sl, LODGE_STAGE_RANGES, s);
-    launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, s);
+    launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, rbits, s);
     prof_end(sl, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
     BlendOut bo{d_rgb, nullptr, nullptr};
     if (save) {
@@ -549,14 +567,21 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         bo.last = ws.last.as<uint32_t>();
     }
     prof_begin(sl, LODGE_STAGE_BLEND, s);
-    launch_blend(cam, ws.ranges.as<uint2>(), vs.as<uint32_t>(), n_keys, ws.rec_a.as<float4>(),
+    launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
                  ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
     prof_end(sl, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
-    TRY(sync_slot(ctx, sl, s));
+    if (end_sync || save) {
+        TRY(sync_slot(ctx, sl, s));
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(sl.h_tail, sl.d_small, sizeof(uint32_t) * kSmWords,
+                                 cudaMemcpyDeviceToHost, s));
+        sl.tail_pending = true;
+    }
 
     sl.prof.frames += 1;
     sl.prof.keys += n_keys;
+    if (rbits) sl.prof.packed_keys += n_keys;
     sl.prof.visible += n_vis;
     sl.prof.active += na;
     if (st) {
@@ -573,6 +598,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         save->cam = cam;
         save->n_vis = n_vis;
         save->n_keys = n_keys;
+        save->rbits = rbits;
         take(save->rec_a, ws.rec_a);
         take(save->rec_b, ws.rec_b);
         take(save->rec_c, ws.rec_c);
@@ -581,7 +607,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         take(save->zsorted, zs);
         take(save->rsorted, rs);
         take(save->tkey, ks);
-        take(save->tval, vs);
+        if (!rbits) take(save->tval, vs);
         take(save->ranges, ws.ranges);
         take(save->T, ws.T);
         take(save->last, ws.last);
@@ -593,10 +619,12 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
 // scenes are held for the frame and released after it.
 lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
                         const lodge_camera& cam, float* d_rgb, cudaStream_t s, Saved* save,
-                        lodge_frame_stats* st) {
+                        lodge_frame_stats* st, bool end_sync) {
     Active act;
     lodge_status r = select_active(ctx, sl, sc, mode, cam, s, &act);
-    if (r == LODGE_OK) r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st);
+    // blocks of a streamed scene are released after the frame: wait for it
+    if (sc->residency == kStreamed) end_sync = true;
+    if (r == LODGE_OK) r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st, end_sync);
     if (sc->residency == kStreamed) {
         if (r != LODGE_OK) cudaStreamSynchronize(s);
         release_blocks(ctx, sl);
@@ -627,14 +655,16 @@ __global__ void zrec_kernel(const uint32_t* zsorted, const uint32_t* rsorted, in
     if (i < n && (int64_t)rsorted[i] < n) zrec[rsorted[i]] = zsorted[i];
 }
 
-__global__ void debug_keys_kernel(const uint32_t* tkey, const uint32_t* tval, int64_t n,
+__global__ void debug_keys_kernel(const uint32_t* tkey, const uint32_t* tval, int rbits, int64_t n,
                                   int64_t n_rec, const uint32_t* zrec, const uint32_t* gid,
                                   uint64_t* keys, uint32_t* gids) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t r = tval[i];
+    const uint32_t k = tkey[i];
+    uint32_t r = rbits ? k & ((1u << rbits) - 1u) : tval[i];
+    const uint32_t tile = rbits ? k >> rbits : k;
     if ((int64_t)r >= n_rec) r = 0;
-    if (keys) keys[i] = ((uint64_t)tkey[i] << 32) | zrec[r];
+    if (keys) keys[i] = ((uint64_t)tile << 32) | zrec[r];
     if (gids) gids[i] = gid[r];
 }
 
@@ -1018,6 +1048,92 @@ lodge_status lodge_upload_chunks(lodge_ctx* ctx, int32_t scene_id, const int32_t
     return LODGE_OK;
 }
 
+// Greedy depth-threshold search (Sec. 3, "Selecting depth thresholds"): for
+// l = 1 .. L-1 in turn, d_l is the candidate above d_{l-1} that minimises the
+// tile keys summed over the views, with d_1 .. d_{l-1} fixed and levels above
+// l unused; ties go to the smaller candidate.  The keys of every candidate
+// come from one K10 pass per view and step.
+lodge_status lodge_select_thresholds(lodge_ctx* ctx, int32_t scene_id, const lodge_camera* views,
+                                     int32_t n_views, const double* candidates, int32_t n_candidates,
+                                     double* d_out, int64_t* keys_out, void* stream) {
+    if (!ctx || !views || !candidates || !d_out || n_views < 1 || n_candidates < 1)
+        return fail(LODGE_E_INVALID, "bad argument");
+    if (n_candidates > kMaxThreshCandidates)
+        return fail(LODGE_E_INVALID, "more than %d candidates", kMaxThreshCandidates);
+    for (int k = 0; k < n_candidates; ++k) {
+        if (!(std::isfinite(candidates[k]) && candidates[k] > 0.0))
+            return fail(LODGE_E_INVALID, "candidate %d is not a positive finite distance", k);
+        if (k && !(candidates[k] > candidates[k - 1]))
+            return fail(LODGE_E_INVALID, "candidates must be strictly ascending");
+    }
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    for (int v = 0; v < n_views; ++v) TRY(check_cam(views[v]));
+    const int L = sc->dev.num_levels;
+    const int K = n_candidates;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<float> thr(K);
+    for (int k = 0; k < K; ++k) thr[k] = (float)(candidates[k] * candidates[k]);
+    DBuf d_thr, d_acc;
+    TRY(ensure(ctx, d_thr, sizeof(float) * K, s));
+    TRY(ensure(ctx, d_acc, sizeof(unsigned long long) * (2 * K + 2), s));
+    lodge_status r = LODGE_OK;
+    std::vector<unsigned long long> acc(2 * K + 2);
+    std::vector<double> d;  // thresholds chosen so far
+    cudaError_t e = cudaMemcpyAsync(d_thr.p, thr.data(), sizeof(float) * K, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) r = fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e));
+    for (int l = 1; l < L && r == LODGE_OK; ++l) {
+        const double prev = d.empty() ? 0.0 : d.back();
+        int64_t* row = keys_out ? keys_out + (size_t)(l - 1) * K : nullptr;
+        if (!std::isfinite(prev)) {  // no candidate was left for an earlier level
+            d.push_back(INFINITY);
+            if (row) for (int k = 0; k < K; ++k) row[k] = -1;
+            continue;
+        }
+        // Eq. 2 bands of the fixed levels 0 .. l-2 and the lower edge of level l-1
+        ThreshBands b;
+        for (int j = 0; j < kMaxLevels; ++j) { b.lo[j] = 0.f; b.hi[j] = INFINITY; }
+        for (int j = 0; j < l; ++j) {
+            const double a = j == 0 ? 0.0 : d[j - 1];
+            b.lo[j] = (float)(a * a);
+            if (j + 1 < l) b.hi[j] = (float)(d[j] * d[j]);
+        }
+        e = cudaMemsetAsync(d_acc.p, 0, sizeof(unsigned long long) * (2 * K + 2), s);
+        for (int v = 0; v < n_views && e == cudaSuccess; ++v) {
+            const DevCamera cam = make_cam(views[v]);
+            for (int c = 0; c < 3; ++c) b.c[c] = (float)views[v].center[c];
+            launch_threshold_cost(sc->dev, cam, sc->dev.level_off[l + 1], l, b, d_thr.as<float>(), K,
+                                  d_acc.as<unsigned long long>(), s);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(acc.data(), d_acc.p, sizeof(unsigned long long) * (2 * K + 2),
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { r = fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e)); break; }
+        // per-candidate totals: fixed part + level l-1 entering + level l leaving
+        unsigned long long lower = 0, upper = 0;
+        for (int m = 1; m <= K; ++m) upper += acc[K + 1 + m];
+        int best = -1;
+        unsigned long long best_keys = 0;
+        for (int k = 0; k < K; ++k) {
+            lower += acc[1 + k];
+            upper -= acc[K + 1 + k];   // bucket m = k no longer counts for candidate k
+            const unsigned long long keys = acc[0] + lower + upper;
+            const bool valid = candidates[k] > prev;
+            if (row) row[k] = valid ? (int64_t)keys : -1;
+            if (valid && (best < 0 || keys < best_keys)) { best = k; best_keys = keys; }
+        }
+        d.push_back(best < 0 ? INFINITY : candidates[best]);
+    }
+    release(ctx, d_thr, s);
+    release(ctx, d_acc, s);
+    if (r != LODGE_OK) return r;
+    for (int l = 1; l < L; ++l) d_out[l - 1] = d[l - 1];
+    return LODGE_OK;
+}
+
 lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
                               int32_t n_cams, lodge_selection* out, uint32_t* d_gids,
                               int64_t gids_capacity, void* stream) {
@@ -1081,7 +1197,15 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     for (int i = 0; i < n_cams; ++i) {
         std::unique_ptr<Saved> sv;
         if (save_for_backward) sv.reset(new Saved());
-        TRY(render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, s, sv.get(), stats ? stats + i : nullptr));
+        // consecutive frames of one call are not waited for one by one: the
+        // host prepares frame i + 1 while frame i's last kernels run
+        const bool last = i + 1 == n_cams;
+        lodge_status r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, s, sv.get(),
+                                    stats ? stats + i : nullptr, last);
+        if (r != LODGE_OK) {
+            if (sl.tail_pending) { cudaStreamSynchronize(s); sl.tail_pending = false; }
+            return r;
+        }
         off += (size_t)cams[i].width * cams[i].height * 3;
         if (sv) {
             std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -1156,7 +1280,7 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
     act.n = n;
     std::unique_ptr<Saved> sv;
     if (save_for_backward) sv.reset(new Saved());
-    TRY(render_frame(ctx, sl, d, act, *cam, d_rgb, s, sv.get(), stats));
+    TRY(render_frame(ctx, sl, d, act, *cam, d_rgb, s, sv.get(), stats, true));
     if (sv) {
         sv->params = true;
         sv->n = n;
@@ -1190,7 +1314,8 @@ lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* 
     TRY(ensure(ctx, ws.grec, sizeof(float) * n9, s));
     CUDA_TRY(cudaMemsetAsync(ws.grec.p, 0, sizeof(float) * n9, s));
     CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
-    launch_blend_bwd(v.cam, v.ranges.as<uint2>(), v.tval.as<uint32_t>(), v.n_keys, v.rec_a.as<float4>(),
+    launch_blend_bwd(v.cam, v.ranges.as<uint2>(), v.rbits ? v.tkey.as<uint32_t>() : v.tval.as<uint32_t>(),
+                     v.rbits ? (1u << v.rbits) - 1u : 0xffffffffu, v.n_keys, v.rec_a.as<float4>(),
                      v.rec_b.as<float4>(), v.rec_c.as<float>(), v.n_vis, v.T.as<float>(),
                      v.last.as<uint32_t>(), d_dL_drgb, ws.grec.as<float>(), s);
     launch_project_bwd(v.cam, v.n_vis, v.rec_gid.as<uint32_t>(), ws.grec.as<float>(), v.means,
@@ -1228,7 +1353,7 @@ lodge_status lodge_debug_keys(lodge_ctx* ctx, int64_t handle, uint64_t* d_keys, 
     DBuf zrec;
     TRY(ensure(ctx, zrec, sizeof(uint32_t) * (size_t)std::max<int64_t>(v.n_vis, 1), s));
     if (v.n_vis) zrec_kernel<<<(unsigned)((v.n_vis + 255) / 256), 256, 0, s>>>(v.zsorted.as<uint32_t>(), v.rsorted.as<uint32_t>(), v.n_vis, zrec.as<uint32_t>());
-    if (v.n_keys) debug_keys_kernel<<<(unsigned)((v.n_keys + 255) / 256), 256, 0, s>>>(v.tkey.as<uint32_t>(), v.tval.as<uint32_t>(), v.n_keys, std::max<int64_t>(v.n_vis, 1), zrec.as<uint32_t>(), v.rec_gid.as<uint32_t>(), d_keys, d_gids);
+    if (v.n_keys) debug_keys_kernel<<<(unsigned)((v.n_keys + 255) / 256), 256, 0, s>>>(v.tkey.as<uint32_t>(), v.tval.as<uint32_t>(), v.rbits, v.n_keys, std::max<int64_t>(v.n_vis, 1), zrec.as<uint32_t>(), v.rec_gid.as<uint32_t>(), d_keys, d_gids);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     release(ctx, zrec, s);

@@ -26,10 +26,14 @@ constexpr int64_t kStaticSortMaxPairs = 1ll << 20;
 constexpr size_t kAltBytes = sizeof(uint32_t) * (size_t)kStaticSortMaxPairs;
 constexpr size_t kErrOffset = 2 * kAltBytes;
 constexpr size_t kScratchOffset = kErrOffset + 256;
-constexpr size_t kScratchBytes =
-    sizeof(uint32_t) * (4 * 256 + 32 +
-                        4 * (size_t)((kStaticSortMaxPairs + kSortTile - 1) / kSortTile) * 256);
-constexpr size_t kStaticBytes = kScratchOffset + kScratchBytes;  // about 9.1 MB
+// The look-back words grow with the number of tiles, which is largest with
+// small tiles: size for the worst case over every n up to the limit.
+constexpr int64_t kWorstTiles = (kStaticSortMaxPairs + kSortTileSmall - 1) / kSortTileSmall;
+static_assert(kWorstTiles * kSortTileSmall >= kStaticSortMaxPairs, "tile count");
+static_assert(sort_scratch_words(kStaticSortMaxPairs, 4) <= 4 * 256 + 32 + 4 * kWorstTiles * 256,
+              "scratch bound");
+constexpr size_t kScratchBytes = sizeof(uint32_t) * (size_t)(4 * 256 + 32 + 4 * kWorstTiles * 256);
+constexpr size_t kStaticBytes = kScratchOffset + kScratchBytes;  // about 12.6 MB
 
 // One copy per device that loads the library, held until process exit.
 __device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];

@@ -17,6 +17,8 @@ so these synthetic scenes stand in for them):
                          N0 / 4^l Gaussians, scales doubling per level), a
                          regular chunk grid and a camera trajectory.
 * ``finetune_scene``   - one chunk cell of the outdoor generator.
+* ``ray_scene``        - tiny Gaussians at given distances on tile-centre rays
+                         (one tile key each), for counting checks.
 * ``large_scene``      - 80M Gaussians over 6 levels: the outdoor heightfield
                          with room-like indoor blocks (walls, floors) on a
                          quarter of the chunk cells, 32x32 chunks, viewed by
@@ -144,6 +146,41 @@ def plain_camera(width: int = 256, height: int = 256, fov_y_deg: float = 60.0) -
     (world up is -y), so R = I and t = (0, 0, 3)."""
     return look_at((0.0, 0.0, -3.0), (0.0, 0.0, 1.0), (0.0, -1.0, 0.0),
                    width, height, fov_y_deg)
+
+
+def ray_scene(level_distances: Sequence[Sequence[float]], width: int = 256, height: int = 256,
+              fov_y_deg: float = 60.0):
+    """Scene whose every Gaussian yields exactly one tile key: level l holds
+    one tiny, nearly opaque Gaussian per entry of ``level_distances[l]``,
+    placed at that distance (metres) from the camera centre on the ray
+    through the centre of a 16x16 tile (tiles taken in turn).  The camera
+    sits at the origin looking along +z (R = I, t = 0).  Returns (scene,
+    camera); the tile-key count of any active set is then the number of its
+    Gaussians."""
+    cam = look_at((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), (0.0, -1.0, 0.0), width, height, fov_y_deg)
+    tx, ty = width // 16, height // 16
+    levels = []
+    slot = 0
+    for dl in level_distances:
+        dl = np.asarray(dl, np.float64)
+        means = np.zeros((dl.size, 3))
+        for i, dist in enumerate(dl):
+            t = slot % (tx * ty)
+            slot += 1
+            u = 16.0 * (t % tx) + 8.0
+            v = 16.0 * (t // tx) + 8.0
+            ray = np.array([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, 1.0])
+            means[i] = dist * ray / np.linalg.norm(ray)
+        n = dl.size
+        levels.append(Level(means=means.astype(np.float32),
+                            log_scales=np.full((n, 3), -12.0, np.float32),
+                            quats=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                            opacity_logits=np.full(n, 5.0, np.float32),
+                            sh=np.zeros((n, SH_COEFFS, 3), np.float32)))
+    L = len(levels)
+    scene = Scene(levels=levels, d_thresholds=np.array([10.0 * 2 ** l for l in range(L - 1)]),
+                  chunk_centers=np.zeros((1, 3)))
+    return scene, cam
 
 
 # --------------------------------------------------------------------------
