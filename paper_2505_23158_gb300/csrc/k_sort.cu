@@ -89,20 +89,31 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     for (int j = 0; j < kIPT; ++j) k[j] = (j * 32 + lane < nvalid) ? __ldcs(kin + base + j * 32) : 0u;
 
     // warp-private stable ranking in (j, lane) order = input order; ranks
-    // (< 2^16) packed two per register
+    // (< 2^16) packed two per register.  The lanes holding the same digit
+    // are found with one ballot per digit bit (cheaper than match.any); the
+    // first lane of each group adds the group's size to the warp's count
+    // with a shared atomic and hands the previous count to the group by a
+    // shuffle (no warp barriers in the loop).
     const uint32_t lt = lanemask_lt();
     uint32_t rk[(kIPT + 1) / 2];
 #pragma unroll
     for (int j = 0; j < kIPT; ++j) {
         const bool valid = j * 32 + lane < nvalid;
-        const uint32_t d = valid ? (k[j] >> shift) & dmask : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = valid ? s_whist[warp][d] : 0u;
+        const uint32_t d = valid ? (k[j] >> shift) & dmask : 0u;
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {   // bits above a short last digit are 0: no-ops
+            const bool on = (d >> bit) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, on);
+            peers &= on ? m : ~m;
+        }
+        if (!valid) peers = 1u << lane;
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (valid && lane == leader) before = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+        before = __shfl_sync(0xffffffffu, before, leader);
         const uint32_t r = before + __popc(peers & lt);
         if (j & 1) rk[j >> 1] |= r << 16; else rk[j >> 1] = r;
-        __syncwarp();
-        if (valid && (peers & lt) == 0u) s_whist[warp][d] = before + __popc(peers);
-        __syncwarp();
     }
     __syncthreads();
 
