@@ -212,6 +212,32 @@ lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode
                                const lodge_camera* cams, int32_t n_cams, float* h_rgb,
                                void* stream, lodge_frame_stats* stats);
 
+/* Importance score (Sec. 3 "Importance pruning" and "Visibility filtering",
+ * which follow RadSplat): render each of the n_cams cameras (host array) and
+ * raise d_score[gid] (DEVICE, n_total floats, caller-initialised, normally
+ * to 0) to the largest blending weight T * alpha that the Gaussian receives
+ * at any pixel where it is composited (Eq. 1, same decisions as
+ * lodge_render).  Calls accumulate: the score over several calls is the
+ * maximum over all their views.  chunk < 0: the mode's active set per camera;
+ * chunk >= 0: chunk `chunk`'s own active set for every camera, with no
+ * blending (resident scenes only; the views of a chunk's visibility
+ * filtering).  Synchronous on stream.  Errors: LODGE_E_INVALID,
+ * LODGE_E_NOT_RESIDENT. */
+lodge_status lodge_importance(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, int32_t chunk,
+                              const lodge_camera* cams, int32_t n_cams, float* d_score,
+                              void* stream);
+
+/* Visibility filtering of one chunk (Sec. 3): remove from chunk `chunk`'s
+ * active set every Gaussian whose score in d_score (DEVICE, n_total floats,
+ * from lodge_importance) is below threshold; the set keeps gid order.
+ * *n_kept (host, optional) receives the new size.  Later CHUNK and
+ * CHUNK_BLEND renders use the filtered set.  Resident scenes only; must not
+ * run while frames of the scene are being rendered.  Synchronous.  Errors:
+ * LODGE_E_INVALID, LODGE_E_NOT_RESIDENT, LODGE_E_BUDGET. */
+lodge_status lodge_filter_chunk(lodge_ctx* ctx, int32_t scene_id, int32_t chunk,
+                                const float* d_score, float threshold, int64_t* n_kept,
+                                void* stream);
+
 /* Render Gaussians given as raw DEVICE parameters (the fine-tuning path of
  * Sec. 3 "Building LOD", supplementary "LOD structure optimization steps":
  * only the trained level's parameters change between steps).  Activation is

@@ -16,6 +16,7 @@ Public functions mirror the paper's steps:
   active_set          the active list for a render mode and camera
   project / keys      per-Gaussian projection records, sorted tile keys
   n_keys              number of tile keys of an active list
+  importance          largest blending weight per Gaussian in a view (Sec. 3)
   render              Eq. 1 compositing (binned or brute force)
   select_thresholds   greedy depth-threshold search (Sec. 3)
 """
@@ -93,6 +94,7 @@ def _load():
             lib.orc_render.argtypes = [P, P, C.c_int64, P, P, C.c_int32, P, C.c_int32,
                                        C.c_double, C.c_double, P, P, P, P, P]
             lib.orc_project.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_importance.argtypes = [P, P, C.c_int64, P, P, C.c_double, C.c_double, P, P]
             lib.orc_keys.argtypes = [P, P, C.c_int64, P, P, P, P, C.c_int64]
             lib.orc_keys.restype = C.c_int64
             lib.orc_sh_basis.argtypes = [C.c_double, C.c_double, C.c_double, P]
@@ -299,6 +301,24 @@ def keys(osc: OracleScene, cam, gids, mults=None):
     lib.orc_keys(osc.ptr, C.byref(cc), g.size, _p(g), None if m is None else _p(m),
                  _p(k), _p(gg), n)
     return k, gg
+
+
+def importance(osc: OracleScene, cam, gids, mults=None, ke_alpha=1e-4, ke_t=1e-4):
+    """Importance score of each active entry for one view (Sec. 3, after
+    RadSplat): the largest blending weight T * alpha it receives at any
+    pixel where it is composited (0 if never).  Returns (score, clean):
+    ``clean`` takes the maximum only over pixels without a knife-edge
+    decision (alpha near 1/255 or T near 1e-4), where FP32 and FP64 can
+    composite different entries."""
+    lib = _load()
+    g = _c(gids, np.int64)
+    m = None if mults is None else _c(mults, np.float32)
+    sa = np.zeros(g.size, np.float64)
+    sc = np.zeros(g.size, np.float64)
+    cc = _cam(cam)
+    lib.orc_importance(osc.ptr, C.byref(cc), g.size, _p(g), None if m is None else _p(m),
+                       float(ke_alpha), float(ke_t), _p(sa), _p(sc))
+    return sa, sc
 
 
 def n_keys(osc: OracleScene, cam, gids, mults=None) -> int:

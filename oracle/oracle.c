@@ -656,6 +656,115 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, int64_t n_active,
 }
 
 /* ---------------------------------------------------------------------- */
+/* importance score (Sec. 3 "Importance pruning" and "Visibility filtering",  */
+/* after RadSplat): the largest blending weight T * alpha a Gaussian          */
+/* receives at any pixel of the view, where it is composited.  The pixels,    */
+/* order and decisions are those of orc_render's binned mode.                  */
+/* ---------------------------------------------------------------------- */
+/* One pixel: walk the list as composite_pixel does and raise score[rec] to
+ * T * alpha for every composited entry; the flags say whether the pixel has a
+ * knife-edge decision (composite_pixel's bands). */
+static void importance_pixel(const orc_splat* sp, const orc_item* list, int64_t n, double px,
+                             double py, const orc_knife* ke, double* score_all,
+                             double* score_clean)
+{
+    /* first pass: is this pixel a knife edge? */
+    double T = 1.0;
+    int kf = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const orc_splat* s = sp + list[i].rec;
+        double dx = px - s->mx, dy = py - s->my;
+        double q = s->conic[0] * dx * dx + 2.0 * s->conic[1] * dx * dy + s->conic[2] * dy * dy;
+        double a = s->opacity * exp(-0.5 * q);
+        if (a > ORC_ALPHA_MAX) a = ORC_ALPHA_MAX;
+        if (fabs(a - ORC_ALPHA_MIN) <= ke->ke_alpha * ORC_ALPHA_MIN) kf = 1;
+        if (a < ORC_ALPHA_MIN) continue;
+        double Tn = T * (1.0 - a);
+        if (fabs(Tn - ORC_T_MIN) <= ke->ke_t * ORC_T_MIN) kf = 1;
+        if (Tn < ORC_T_MIN) break;
+        T = Tn;
+    }
+    /* second pass: the weights */
+    T = 1.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const orc_splat* s = sp + list[i].rec;
+        double dx = px - s->mx, dy = py - s->my;
+        double q = s->conic[0] * dx * dx + 2.0 * s->conic[1] * dx * dy + s->conic[2] * dy * dy;
+        double a = s->opacity * exp(-0.5 * q);
+        if (a > ORC_ALPHA_MAX) a = ORC_ALPHA_MAX;
+        if (a < ORC_ALPHA_MIN) continue;
+        double Tn = T * (1.0 - a);
+        if (Tn < ORC_T_MIN) break;
+        double w = T * a;
+        int64_t r = list[i].rec;
+        if (w > score_all[r]) score_all[r] = w;
+        if (!kf && w > score_clean[r]) score_clean[r] = w;
+        T = Tn;
+    }
+}
+
+/* score_all[i]: largest weight of active entry i over all pixels (0 if it is
+ * never composited); score_clean[i]: the same over the pixels without a
+ * knife-edge decision.  Both are raised, not overwritten, so several views
+ * accumulate by calling again. */
+int orc_importance(const orc_scene* sc, const orc_camera* cam, int64_t n_active,
+                   const int64_t* gids, const float* mults, double ke_alpha, double ke_t,
+                   double* score_all, double* score_clean)
+{
+    const int W = cam->width, H = cam->height;
+    const int tx_n = (W + ORC_TILE - 1) / ORC_TILE, ty_n = (H + ORC_TILE - 1) / ORC_TILE;
+    const int32_t ntl = tx_n * ty_n;
+    orc_knife ke = { ke_alpha, ke_t };
+    size_t na = (size_t)(n_active ? n_active : 1);
+    orc_splat* sp = (orc_splat*)malloc(sizeof(orc_splat) * na);
+    orc_key_rec* kr = (orc_key_rec*)malloc(sizeof(orc_key_rec) * na);
+    uint8_t* vis = (uint8_t*)calloc(na, 1);
+    for (int64_t i = 0; i < n_active; ++i) {
+        float m = mults ? mults[i] : 1.0f;
+        vis[i] = (uint8_t)key_spec(sc, cam, gids[i], m, &kr[i]);
+        if (vis[i]) splat64(sc, cam, gids[i], (double)m, &sp[i]);
+    }
+    /* per tile, the entries whose tile rect contains it, by (depth, record) */
+    int64_t* cnt = (int64_t*)calloc((size_t)ntl + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < n_active; ++i) {
+        if (!vis[i]) continue;
+        for (int ty = kr[i].rect[1]; ty <= kr[i].rect[3]; ++ty)
+            for (int tx = kr[i].rect[0]; tx <= kr[i].rect[2]; ++tx) cnt[ty * tx_n + tx + 1]++;
+    }
+    for (int32_t t = 0; t < ntl; ++t) cnt[t + 1] += cnt[t];
+    orc_item* lists = (orc_item*)malloc(sizeof(orc_item) * (size_t)(cnt[ntl] ? cnt[ntl] : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)ntl);
+    for (int32_t t = 0; t < ntl; ++t) fill[t] = cnt[t];
+    for (int64_t i = 0; i < n_active; ++i) {
+        if (!vis[i]) continue;
+        for (int ty = kr[i].rect[1]; ty <= kr[i].rect[3]; ++ty)
+            for (int tx = kr[i].rect[0]; tx <= kr[i].rect[2]; ++tx) {
+                int64_t f = fill[ty * tx_n + tx]++;
+                lists[f].rec = i;
+                lists[f].z = kr[i].z;
+            }
+    }
+    /* scores per entry are local to this call, then raised into the outputs */
+    double* sa = (double*)calloc(na, sizeof(double));
+    double* scl = (double*)calloc(na, sizeof(double));
+    for (int32_t t = 0; t < ntl; ++t) {
+        int tx = t % tx_n, ty = t / tx_n;
+        orc_item* L = lists + cnt[t];
+        int64_t n = cnt[t + 1] - cnt[t];
+        qsort(L, (size_t)n, sizeof(orc_item), item_cmp);
+        for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < H; ++py)
+            for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < W; ++px)
+                importance_pixel(sp, L, n, px + 0.5, py + 0.5, &ke, sa, scl);
+    }
+    for (int64_t i = 0; i < n_active; ++i) {
+        if (sa[i] > score_all[i]) score_all[i] = sa[i];
+        if (scl[i] > score_clean[i]) score_clean[i] = scl[i];
+    }
+    free(sp); free(kr); free(vis); free(cnt); free(lists); free(fill); free(sa); free(scl);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* per-Gaussian projection records and the sorted tile key list             */
 /* ---------------------------------------------------------------------- */
 /* For each active entry: visible flag, FP32 depth, tile rect, FP32 final

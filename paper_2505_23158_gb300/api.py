@@ -61,6 +61,7 @@ class Lodge:
         self._h = h
         self._keep = {}
         self._num_levels = {}
+        self._n_total = {}
 
     # -- lifetime
     def close(self):
@@ -107,6 +108,7 @@ class Lodge:
         sid = C.c_int32()
         A.call("lodge_load_scene", self._h, C.byref(desc), C.byref(sid))
         self._num_levels[sid.value] = scene.num_levels
+        self._n_total[sid.value] = scene.n_total
         return sid.value
 
     def unload_scene(self, sid: int):
@@ -152,6 +154,27 @@ class Lodge:
                C.c_void_p(cand.ctypes.data), int(cand.size), C.c_void_p(d.ctypes.data),
                C.c_void_p(keys.ctypes.data), _stream(stream))
         return d[:L - 1], keys[:L - 1]
+
+    def importance(self, sid: int, mode: int, cams, score: Optional[torch.Tensor] = None,
+                   chunk: int = -1, stream=None) -> torch.Tensor:
+        """Largest blending weight per Gaussian over the cameras (float32
+        cuda tensor of n_total, raised in place if given)."""
+        cl = list(cams)
+        if score is None:
+            score = torch.zeros(self._n_total[sid], dtype=torch.float32,
+                                device=f"cuda:{self.device}")
+        A.call("lodge_importance", self._h, int(sid), int(mode), int(chunk), camera_array(cl),
+               len(cl), _ptr(score), _stream(stream))
+        return score
+
+    def filter_chunk(self, sid: int, chunk: int, score: torch.Tensor, threshold: float,
+                     stream=None) -> int:
+        """Visibility filtering: drop chunk's Gaussians scoring below threshold;
+        returns the new size of its set."""
+        n = C.c_int64(0)
+        A.call("lodge_filter_chunk", self._h, int(sid), int(chunk), _ptr(score),
+               float(threshold), C.byref(n), _stream(stream))
+        return n.value
 
     # -- render
     def render(self, sid: int, mode: int, cams, out: Optional[torch.Tensor] = None,

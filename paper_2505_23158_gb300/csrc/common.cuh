@@ -155,12 +155,18 @@ void launch_chunk_union(const uint32_t* a, int64_t na, const uint32_t* b, int64_
                         int64_t n_total, uint8_t* marks, uint32_t* out, uint32_t* d_count,
                         uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
 
+// Visibility filtering: entries of list (n, gid ascending) whose score[gid]
+// (n_total floats) is >= thr, compacted in order into out; *d_count = kept.
+void launch_score_filter(const uint32_t* list, int64_t n, const float* score, float thr,
+                         int64_t n_total, uint32_t* out, uint32_t* d_count, uint32_t* status,
+                         uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+
 // K3: projection + SH + visibility compaction.
 struct ProjectOut {
     float4* rec_a;      // (mean'x, mean'y, u00, u01)
     float4* rec_b;      // (u11, opacity', r, g)
     float* rec_c;       // b
-    uint2* rec_rect;    // (tx0 | ty0 << 16, tx1 | ty1 << 16)
+    uint2* rec_rect;    // pixel range (x0 | y0 << 16, x1 | y1 << 16), inclusive
     uint32_t* rec_gid;  // gid of the record
     uint32_t* depth_key;  // FP32 depth bits (sort key), index = record
     uint32_t* depth_val;  // record index
@@ -252,14 +258,23 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s);
 
+// K12: importance score: the blend's walk, and per record the largest
+// weight T * alpha it receives (rec_score, n_rec words, zeroed, FP32 bits),
+// then score[gid] (n_total floats, non-negative) raised to it.  rgb as in
+// launch_blend.
+void launch_importance(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+                       uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b,
+                       const float* rec_c, int64_t n_rec, const uint32_t* rec_gid, float* rgb,
+                       uint32_t* rec_score, int64_t n_total, float* score, cudaStream_t s);
+
 // K8 / K9: adjoint of compositing and projection (fine-tuning path).
-// grec: 9 x n_rec floats, zeroed: d(mean'x, mean'y, u00, u01, u11, o', r, g, b).
+// grec: 9 x n_rec doubles, zeroed: d(mean'x, mean'y, u00, u01, u11, o', r, g, b).
 void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
                       uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                       int64_t n_rec, const float* T_final, const uint32_t* last,
-                      const float* dL_drgb, float* grec, cudaStream_t s);
+                      const float* dL_drgb, double* grec, cudaStream_t s);
 void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec_gid,
-                        const float* grec, const float* means, const float4* act_so,
+                        const double* grec, const float* means, const float4* act_so,
                         const float4* act_q, const float* quats, const float* sh, int sh_degree,
                         float filter_var, float* g_means, float* g_log_scales, float* g_quats,
                         float* g_logits, float* g_sh, cudaStream_t s);

@@ -77,11 +77,11 @@ struct Saved {
 struct Workspace {
     DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
         tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp, koff, srec,
-        srect, doffs, grec, bonly;
+        srect, doffs, grec, bonly, iscore;
     std::vector<DBuf*> all() {
         return {&list, &marks, &status, &rec_a, &rec_b, &rec_c, &rec_rect, &rec_gid, &dkey, &dval,
                 &dkey2, &dval2, &tkey, &tval, &tkey2, &tval2, &ranges, &sort, &T, &last, &img,
-                &act_so, &act_q, &mtmp, &koff, &srec, &srect, &doffs, &grec, &bonly};
+                &act_so, &act_q, &mtmp, &koff, &srec, &srect, &doffs, &grec, &bonly, &iscore};
     }
 };
 

@@ -46,7 +46,7 @@ blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __
                  const float4* __restrict__ rec_a, const float4* __restrict__ rec_b,
                  const float* __restrict__ rec_c, const float* __restrict__ T_final,
                  const uint32_t* __restrict__ last, const float* __restrict__ dL_drgb,
-                 float* __restrict__ grec) {
+                 double* __restrict__ grec) {
     __shared__ float4 sa[kBatch];
     __shared__ float4 sb[kBatch];
     __shared__ float sc[kBatch];
@@ -137,18 +137,21 @@ blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __
                 d_u00 = warp_sum(d_u00); d_u01 = warp_sum(d_u01); d_u11 = warp_sum(d_u11);
                 d_o = warp_sum(d_o);
                 d_r = warp_sum(d_r); d_g = warp_sum(d_g); d_b = warp_sum(d_b);
+                // the per-record sums run over every pixel the record covers,
+                // often with terms of both signs: accumulate the warp partials
+                // in FP64 so their number does not grow the rounding error
                 if (lane == 0) {
                     const uint32_t r = sr[k];
-                    float* g = grec + r;
-                    atomicAdd(g + 0 * (size_t)n_rec, d_mx);
-                    atomicAdd(g + 1 * (size_t)n_rec, d_my);
-                    atomicAdd(g + 2 * (size_t)n_rec, d_u00);
-                    atomicAdd(g + 3 * (size_t)n_rec, d_u01);
-                    atomicAdd(g + 4 * (size_t)n_rec, d_u11);
-                    atomicAdd(g + 5 * (size_t)n_rec, d_o);
-                    atomicAdd(g + 6 * (size_t)n_rec, d_r);
-                    atomicAdd(g + 7 * (size_t)n_rec, d_g);
-                    atomicAdd(g + 8 * (size_t)n_rec, d_b);
+                    double* g = grec + r;
+                    atomicAdd(g + 0 * (size_t)n_rec, (double)d_mx);
+                    atomicAdd(g + 1 * (size_t)n_rec, (double)d_my);
+                    atomicAdd(g + 2 * (size_t)n_rec, (double)d_u00);
+                    atomicAdd(g + 3 * (size_t)n_rec, (double)d_u01);
+                    atomicAdd(g + 4 * (size_t)n_rec, (double)d_u11);
+                    atomicAdd(g + 5 * (size_t)n_rec, (double)d_o);
+                    atomicAdd(g + 6 * (size_t)n_rec, (double)d_r);
+                    atomicAdd(g + 7 * (size_t)n_rec, (double)d_g);
+                    atomicAdd(g + 8 * (size_t)n_rec, (double)d_b);
                 }
             }
         }
@@ -192,7 +195,7 @@ struct BwdParams {
     DevCamera cam;
     int64_t n_rec;
     const uint32_t* rec_gid;
-    const float* grec;           // 9 x n_rec
+    const double* grec;          // 9 x n_rec
     const float* means;          // N x 3 raw
     const float4* act_so;        // (s0, s1, s2, o) activated
     const float4* act_q;         // unit quaternion
@@ -212,10 +215,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
     if (r >= P.n_rec) return;
     const uint32_t g = P.rec_gid[r];
     const size_t nr = (size_t)P.n_rec;
-    const float gmx = P.grec[r], gmy = P.grec[nr + r];
-    const float gu00 = P.grec[2 * nr + r], gu01 = P.grec[3 * nr + r], gu11 = P.grec[4 * nr + r];
-    const float gop = P.grec[5 * nr + r];
-    const float grgb[3] = {P.grec[6 * nr + r], P.grec[7 * nr + r], P.grec[8 * nr + r]};
+    const float gmx = (float)P.grec[r], gmy = (float)P.grec[nr + r];
+    const float gu00 = (float)P.grec[2 * nr + r], gu01 = (float)P.grec[3 * nr + r],
+                gu11 = (float)P.grec[4 * nr + r];
+    const float gop = (float)P.grec[5 * nr + r];
+    const float grgb[3] = {(float)P.grec[6 * nr + r], (float)P.grec[7 * nr + r],
+                           (float)P.grec[8 * nr + r]};
     const DevCamera& cam = P.cam;
     const float* R = cam.R;
 
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
 void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
                       uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                       int64_t n_rec, const float* T_final, const uint32_t* last,
-                      const float* dL_drgb, float* grec, cudaStream_t s) {
+                      const float* dL_drgb, double* grec, cudaStream_t s) {
     int ntiles = cam.tiles_x * cam.tiles_y;
     if (ntiles == 0 || n_rec == 0) return;
     blend_bwd_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val,
@@ -383,7 +388,7 @@ void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t*
 }
 
 void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec_gid,
-                        const float* grec, const float* means, const float4* act_so,
+                        const double* grec, const float* means, const float4* act_so,
                         const float4* act_q, const float* quats, const float* sh, int sh_degree,
                         float filter_var, float* g_means, float* g_log_scales, float* g_quats,
                         float* g_logits, float* g_sh, cudaStream_t s) {

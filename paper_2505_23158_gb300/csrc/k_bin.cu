@@ -15,7 +15,7 @@ namespace {
 // Pass 1: per depth-sorted visible record, its tile count; block scan plus
 // decoupled look-back give the exclusive key offset koff[i] (koff[n_vis] =
 // total).  The record id and rect are gathered into depth order (srec,
-// srect) so that pass 2 reads them contiguously.
+// srect, in tiles) so that pass 2 reads them contiguously.
 __global__ void __launch_bounds__(kEmitThreads)
 emit_offsets_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
                     const uint2* __restrict__ rec_rect, uint32_t* __restrict__ koff,
@@ -33,7 +33,9 @@ emit_offsets_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     if (i < n_vis) {
         uint32_t rec = sorted_rec[i];
         if ((int64_t)rec >= n_vis) { atomicOr(err, kErrBadIndex); rec = 0; }
-        uint2 r = rec_rect[rec];
+        const uint2 p = rec_rect[rec];   // pixel range -> tile range
+        const uint2 r = make_uint2(((p.x & 0xffffu) / kTile) | (((p.x >> 16) / kTile) << 16),
+                                   ((p.y & 0xffffu) / kTile) | (((p.y >> 16) / kTile) << 16));
         uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu) + 1u;
         uint32_t h = (r.y >> 16) - (r.x >> 16) + 1u;
         cnt = w * h;

@@ -121,6 +121,97 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
     }
 }
 
+
+// K12: importance score (Sec. 3 "Importance pruning" / "Visibility
+// filtering", after RadSplat): the same per-pixel walk as blend_kernel (same
+// decisions, same arithmetic), and for every composited (pixel, record)
+// pair the blending weight T * alpha; each warp takes the maximum over its
+// 32 pixels and raises rec_score[record] (FP32 bits, non-negative, so the
+// unsigned maximum is the float maximum).  The image is written as well.
+// Lanes stay converged over the batch so the warp maximum can be taken per
+// record; a warp leaves the batch once all its pixels have stopped.
+__global__ void __launch_bounds__(256)
+importance_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __restrict__ ranges,
+                  const uint32_t* __restrict__ tile_val, uint32_t vmask, uint32_t n_keys,
+                  uint32_t n_rec, const float4* __restrict__ rec_a, const float4* __restrict__ rec_b,
+                  const float* __restrict__ rec_c, float* __restrict__ out_rgb,
+                  uint32_t* __restrict__ rec_score) {
+    __shared__ float4 sa[kBatch];
+    __shared__ float4 sb[kBatch];
+    __shared__ float sc[kBatch];
+    __shared__ uint32_t sr[kBatch];
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x = tx * kTile + (warp & 1) * 8 + (lane & 7);
+    const int y = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside = x < width && y < height;
+    const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
+    uint2 rg = ranges[tile];
+    if (rg.y > n_keys || rg.x > rg.y) rg = make_uint2(0, 0);
+    const int n = (int)(rg.y - rg.x);
+    const int nb = (n + kBatch - 1) / kBatch;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    bool done = !inside;
+    for (int b = 0; b < nb; ++b) {
+        __syncthreads();
+        const int k0 = b * kBatch + tid;
+        if (k0 < n) {
+            const uint32_t j = min(tile_val[rg.x + k0] & vmask, n_rec - 1u);
+            sr[tid] = j;
+            sa[tid] = rec_a[j];
+            sb[tid] = rec_b[j];
+            sc[tid] = rec_c[j];
+        }
+        __syncthreads();
+        const int cnt = min(kBatch, n - b * kBatch);
+        for (int k = 0; k < cnt; ++k) {
+            if (__all_sync(0xffffffffu, done)) break;
+            float w = 0.f;
+            if (!done) {
+                const float4 a = sa[k];
+                const float dx = pxf - a.x, dy = pyf - a.y;
+                const float t = fmaf(a.z, dx, a.w * dy);
+                const float4 bb = sb[k];
+                const float wq = bb.x * dy;
+                const float q = fmaf(t, t, wq * wq);
+                const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+                if (alpha >= (1.0f / 255.0f)) {
+                    const float Tn = T * (1.f - alpha);
+                    if (Tn < 1e-4f) {
+                        done = true;
+                    } else {
+                        w = T * alpha;
+                        C0 = fmaf(w, bb.z, C0);
+                        C1 = fmaf(w, bb.w, C1);
+                        C2 = fmaf(w, sc[k], C2);
+                        T = Tn;
+                    }
+                }
+            }
+            const uint32_t wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(w));
+            if (lane == 0 && wmax) atomicMax(rec_score + sr[k], wmax);
+        }
+        if (__syncthreads_count(done) == 256) break;
+    }
+    if (inside) {
+        const int64_t pix = (int64_t)y * width + x;
+        out_rgb[3 * pix + 0] = C0;
+        out_rgb[3 * pix + 1] = C1;
+        out_rgb[3 * pix + 2] = C2;
+    }
+}
+
+// raise score[gid] to each record's score
+__global__ void record_score_to_gid_kernel(const uint32_t* __restrict__ rec_score,
+                                           const uint32_t* __restrict__ rec_gid, int64_t n_rec,
+                                           int64_t n_total, uint32_t* __restrict__ score) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec) return;
+    const uint32_t v = rec_score[r];
+    const uint32_t g = rec_gid[r];
+    if (v && (int64_t)g < n_total) atomicMax(score + g, v);
+}
 }  // namespace
 
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
@@ -131,6 +222,20 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
     blend_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val, vmask,
                                         (uint32_t)n_keys, (uint32_t)std::max<int64_t>(n_rec, 1),
                                         rec_a, rec_b, rec_c, o.rgb, o.T_final, o.last);
+}
+
+void launch_importance(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,
+                       uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b,
+                       const float* rec_c, int64_t n_rec, const uint32_t* rec_gid, float* rgb,
+                       uint32_t* rec_score, int64_t n_total, float* score, cudaStream_t s) {
+    const int ntiles = cam.tiles_x * cam.tiles_y;
+    if (ntiles == 0) return;
+    importance_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val, vmask,
+                                             (uint32_t)n_keys, (uint32_t)std::max<int64_t>(n_rec, 1),
+                                             rec_a, rec_b, rec_c, rgb, rec_score);
+    if (n_rec > 0)
+        record_score_to_gid_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(
+            rec_score, rec_gid, n_rec, n_total, reinterpret_cast<uint32_t*>(score));
 }
 
 }  // namespace lodge

@@ -74,7 +74,8 @@ struct KeySplat {
     float d0, d1, d2;          // mean - chat
     float z, mx, my, op;       // depth, projected mean, opacity after Eq. 3 and Eq. 4
     float B0[3], B1[3];        // rows of J W R(q) diag(sigma)
-    uint32_t rx0, ry0, rx1, ry1;
+    uint32_t px0, py0, px1, py1;   // pixel range (inclusive), clipped to the image
+    uint32_t rx0, ry0, rx1, ry1;   // the same in tiles
 };
 
 __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& cam, float mxw,
@@ -145,8 +146,10 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
     if (y1 > ymax) y1 = ymax;
     if (!(x0 <= x1 && y0 <= y1)) return false;
     k.z = pz; k.mx = mx; k.my = my; k.op = op;
-    k.rx0 = (uint32_t)(int)x0 / kTile; k.ry0 = (uint32_t)(int)y0 / kTile;
-    k.rx1 = (uint32_t)(int)x1 / kTile; k.ry1 = (uint32_t)(int)y1 / kTile;
+    k.px0 = (uint32_t)(int)x0; k.py0 = (uint32_t)(int)y0;
+    k.px1 = (uint32_t)(int)x1; k.py1 = (uint32_t)(int)y1;
+    k.rx0 = k.px0 / kTile; k.ry0 = k.py0 / kTile;
+    k.rx1 = k.px1 / kTile; k.ry1 = k.py1 / kTile;
     return true;
 }
 
@@ -170,7 +173,7 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     float z = 0.f, mxp = 0.f, myp = 0.f, o = 0.f;
     float B0[3], B1[3];
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-    uint32_t rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
+    uint32_t rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0, pr0 = 0, pr1 = 0;
     // attribute source of this entry: the scene store (indexed by gid) or a
     // chunk block (indexed by position in the block)
     const float* smx = sc.mx;
@@ -210,6 +213,8 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
 #pragma unroll
             for (int k = 0; k < 3; ++k) { B0[k] = ks.B0[k]; B1[k] = ks.B1[k]; }
             rx0 = ks.rx0; ry0 = ks.ry0; rx1 = ks.rx1; ry1 = ks.ry1;
+            pr0 = ks.px0 | (ks.py0 << 16);
+            pr1 = ks.px1 | (ks.py1 << 16);
         }
     }
 
@@ -280,7 +285,7 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     P.o.rec_a[pos] = make_float4(mxp, myp, u00, u01);
     P.o.rec_b[pos] = make_float4(u11, o, fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
     P.o.rec_c[pos] = fmaxf(rgb[2], 0.f);
-    P.o.rec_rect[pos] = make_uint2(rx0 | (ry0 << 16), rx1 | (ry1 << 16));
+    P.o.rec_rect[pos] = make_uint2(pr0, pr1);   // pixel range
     P.o.rec_gid[pos] = g;
     P.o.depth_key[pos] = __float_as_uint(z);
     P.o.depth_val[pos] = pos;

@@ -63,6 +63,31 @@ struct LodSelectF {
     }
 };
 
+// Visibility filtering (Sec. 3): keep the entries of a chunk's gid list
+// whose importance score reaches the threshold, in list order.
+struct ScoreKeepF {
+    const uint32_t* list;
+    const float* score;
+    float thr;
+    int64_t n, n_total;
+    __device__ __forceinline__ uint32_t operator()(int64_t first, uint32_t* out_val) const {
+        uint32_t bits = 0;
+#pragma unroll
+        for (int j = 0; j < kSelectIPT; ++j) {
+            const int64_t i = first + j;
+            uint32_t g = 0;
+            bool keep = false;
+            if (i < n) {
+                g = __ldg(list + i);
+                keep = (int64_t)g < n_total && __ldg(score + g) >= thr;
+            }
+            bits |= (uint32_t)keep << j;
+            out_val[j] = g;
+        }
+        return bits;
+    }
+};
+
 struct UnionF {
     const uint8_t* marks;
     int64_t n;
@@ -158,6 +183,15 @@ void launch_chunk_union(const uint32_t* a, int64_t na, const uint32_t* b, int64_
     if (ntiles == 0) { cudaMemsetAsync(d_count, 0, 4, s); return; }
     compact_kernel<UnionF><<<(unsigned)ntiles, kSelectThreads, 0, s>>>(
         UnionF{marks, n_total}, n_total, out, d_count, status, tile_counter, err);
+}
+
+void launch_score_filter(const uint32_t* list, int64_t n, const float* score, float thr,
+                         int64_t n_total, uint32_t* out, uint32_t* d_count, uint32_t* status,
+                         uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
+    const int64_t ntiles = (n + kSelectTile - 1) / kSelectTile;
+    if (ntiles == 0) { cudaMemsetAsync(d_count, 0, 4, s); return; }
+    compact_kernel<ScoreKeepF><<<(unsigned)ntiles, kSelectThreads, 0, s>>>(
+        ScoreKeepF{list, score, thr, n, n_total}, n, out, d_count, status, tile_counter, err);
 }
 
 }  // namespace lodge

@@ -456,9 +456,11 @@ static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
 // end_sync = false leaves the frame's last kernels running when it returns
 // (the next frame on the same stream queues behind them); their status words
 // are checked at the slot's next sync.
+// importance != null: composite with K12 instead of K7 and raise
+// importance[gid] (n_total floats) to each Gaussian's largest weight.
 static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, const Active& act,
                                  const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
-                                 lodge_frame_stats* st, bool end_sync) {
+                                 lodge_frame_stats* st, bool end_sync, float* importance = nullptr) {
     Workspace& ws = sl.ws;
     TRY(check_cam(c));
     DevCamera cam = make_cam(c);
@@ -567,9 +569,17 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         bo.last = ws.last.as<uint32_t>();
     }
     prof_begin(sl, LODGE_STAGE_BLEND, s);
-    launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
-                 ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
-    prof_end(sl, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? 1 : 0);
+    if (importance) {
+        TRY(ensure(ctx, ws.iscore, sizeof(uint32_t) * nv1, s));
+        CUDA_TRY(cudaMemsetAsync(ws.iscore.p, 0, sizeof(uint32_t) * nv1, s));
+        launch_importance(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
+                          ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, ws.rec_gid.as<uint32_t>(),
+                          d_rgb, ws.iscore.as<uint32_t>(), dsc.n_total, importance, s);
+    } else {
+        launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
+                     ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
+    }
+    prof_end(sl, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
     CUDA_TRY(cudaGetLastError());
     if (end_sync || save) {
         TRY(sync_slot(ctx, sl, s));
@@ -619,12 +629,13 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
 // scenes are held for the frame and released after it.
 lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
                         const lodge_camera& cam, float* d_rgb, cudaStream_t s, Saved* save,
-                        lodge_frame_stats* st, bool end_sync) {
+                        lodge_frame_stats* st, bool end_sync, float* importance) {
     Active act;
     lodge_status r = select_active(ctx, sl, sc, mode, cam, s, &act);
     // blocks of a streamed scene are released after the frame: wait for it
     if (sc->residency == kStreamed) end_sync = true;
-    if (r == LODGE_OK) r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st, end_sync);
+    if (r == LODGE_OK)
+        r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st, end_sync, importance);
     if (sc->residency == kStreamed) {
         if (r != LODGE_OK) cudaStreamSynchronize(s);
         release_blocks(ctx, sl);
@@ -678,11 +689,11 @@ __global__ void debug_records_kernel(int64_t n, const float4* ra, const float4* 
     if (gid) gid[i] = gid_in[i];
     if (depth) depth[i] = __uint_as_float(zrec[i]);
     if (r4) {
-        uint2 r = rect[i];
-        r4[4 * i + 0] = (int32_t)(r.x & 0xffffu);
-        r4[4 * i + 1] = (int32_t)(r.x >> 16);
-        r4[4 * i + 2] = (int32_t)(r.y & 0xffffu);
-        r4[4 * i + 3] = (int32_t)(r.y >> 16);
+        uint2 r = rect[i];   // pixel range; reported in tiles
+        r4[4 * i + 0] = (int32_t)((r.x & 0xffffu) / kTile);
+        r4[4 * i + 1] = (int32_t)((r.x >> 16) / kTile);
+        r4[4 * i + 2] = (int32_t)((r.y & 0xffffu) / kTile);
+        r4[4 * i + 3] = (int32_t)((r.y >> 16) / kTile);
     }
     if (mean2) { mean2[2 * i] = a.x; mean2[2 * i + 1] = a.y; }
     if (conic) {
@@ -1201,7 +1212,7 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
         // host prepares frame i + 1 while frame i's last kernels run
         const bool last = i + 1 == n_cams;
         lodge_status r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, s, sv.get(),
-                                    stats ? stats + i : nullptr, last);
+                                    stats ? stats + i : nullptr, last, nullptr);
         if (r != LODGE_OK) {
             if (sl.tail_pending) { cudaStreamSynchronize(s); sl.tail_pending = false; }
             return r;
@@ -1232,6 +1243,82 @@ lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode
     TRY(lodge_render(ctx, scene_id, mode, cams, n_cams, sl.ws.img.as<float>(), stream, 0, nullptr, stats));
     if (total) CUDA_TRY(cudaMemcpyAsync(h_rgb, sl.ws.img.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    return LODGE_OK;
+}
+
+// Importance score (Sec. 3 "Importance pruning", "Visibility filtering"):
+// render each camera with K12 and raise d_score[gid] to the largest weight.
+lodge_status lodge_importance(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, int32_t chunk,
+                              const lodge_camera* cams, int32_t n_cams, float* d_score, void* stream) {
+    if (!ctx || !cams || !d_score || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    if (chunk >= 0) {
+        if (chunk >= (int32_t)sc->chunks.size()) return fail(LODGE_E_INVALID, "chunk %d out of range", chunk);
+        if (sc->residency != kResident)
+            return fail(LODGE_E_NOT_RESIDENT, "a chunk's own set is scored on resident scenes only");
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot& sl = *ctx->slots[0];
+    for (int i = 0; i < n_cams; ++i) {
+        TRY(check_cam(cams[i]));
+        TRY(ensure(ctx, sl.ws.img, sizeof(float) * 3 * (size_t)cams[i].width * cams[i].height, s));
+        if (chunk >= 0) {
+            Active act;
+            act.list = sc->chunks[chunk].list;
+            act.n = sc->chunks[chunk].n;
+            act.A = chunk;
+            TRY(render_frame(ctx, sl, sc->dev, act, cams[i], sl.ws.img.as<float>(), s, nullptr, nullptr,
+                             true, d_score));
+        } else {
+            TRY(render_one(ctx, sl, sc, mode, cams[i], sl.ws.img.as<float>(), s, nullptr, nullptr, true,
+                           d_score));
+        }
+    }
+    return LODGE_OK;
+}
+
+// Visibility filtering (Sec. 3): keep the Gaussians of chunk `chunk` whose
+// score reaches the threshold.
+lodge_status lodge_filter_chunk(lodge_ctx* ctx, int32_t scene_id, int32_t chunk, const float* d_score,
+                                float threshold, int64_t* n_kept, void* stream) {
+    if (!ctx || !d_score) return fail(LODGE_E_INVALID, "bad argument");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    if (chunk < 0 || chunk >= (int32_t)sc->chunks.size()) return fail(LODGE_E_INVALID, "chunk %d out of range", chunk);
+    if (sc->residency != kResident)
+        return fail(LODGE_E_NOT_RESIDENT, "visibility filtering edits resident chunk sets only");
+    if (!std::isfinite(threshold)) return fail(LODGE_E_INVALID, "threshold must be finite");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot& sl = *ctx->slots[0];
+    Chunk& ch = sc->chunks[chunk];
+    const int64_t n = ch.n;
+    const int64_t ntiles = std::max<int64_t>((n + kSelectTile - 1) / kSelectTile, 1);
+    TRY(ensure(ctx, sl.ws.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1), s));
+    TRY(ensure(ctx, sl.ws.status, sizeof(uint32_t) * (size_t)ntiles, s));
+    CUDA_TRY(cudaMemsetAsync(sl.ws.status.p, 0, sizeof(uint32_t) * (size_t)ntiles, s));
+    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    launch_score_filter(ch.list, n, d_score, threshold, sc->dev.n_total, sl.ws.list.as<uint32_t>(),
+                        sl.d_small + kSmListCount, sl.ws.status.as<uint32_t>(), sl.d_small + kSmCtrSelect,
+                        sl.d_small + kSmErr, s);
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_slot(ctx, sl, s));
+    const int64_t kept = sl.h_small[kSmListCount];
+    void* p = nullptr;
+    TRY(dmalloc(ctx, &p, sizeof(uint32_t) * (size_t)std::max<int64_t>(kept, 1)));
+    if (kept) CUDA_TRY(cudaMemcpyAsync(p, sl.ws.list.p, sizeof(uint32_t) * (size_t)kept,
+                                       cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    dfree(ctx, ch.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1));
+    sc->chunk_bytes -= sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1);
+    sc->chunk_bytes += sizeof(uint32_t) * (size_t)std::max<int64_t>(kept, 1);
+    ch.list = static_cast<uint32_t*>(p);
+    ch.n = kept;
+    // cached unions may hold the old set
+    for (auto& slp : ctx->slots) slp->u_scene = -1;
+    if (n_kept) *n_kept = kept;
     return LODGE_OK;
 }
 
@@ -1311,14 +1398,14 @@ lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* 
     Slot& sl = *ctx->slots[0];
     Workspace& ws = sl.ws;
     const size_t n9 = 9 * (size_t)std::max<int64_t>(v.n_vis, 1);
-    TRY(ensure(ctx, ws.grec, sizeof(float) * n9, s));
-    CUDA_TRY(cudaMemsetAsync(ws.grec.p, 0, sizeof(float) * n9, s));
+    TRY(ensure(ctx, ws.grec, sizeof(double) * n9, s));
+    CUDA_TRY(cudaMemsetAsync(ws.grec.p, 0, sizeof(double) * n9, s));
     CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
     launch_blend_bwd(v.cam, v.ranges.as<uint2>(), v.rbits ? v.tkey.as<uint32_t>() : v.tval.as<uint32_t>(),
                      v.rbits ? (1u << v.rbits) - 1u : 0xffffffffu, v.n_keys, v.rec_a.as<float4>(),
                      v.rec_b.as<float4>(), v.rec_c.as<float>(), v.n_vis, v.T.as<float>(),
-                     v.last.as<uint32_t>(), d_dL_drgb, ws.grec.as<float>(), s);
-    launch_project_bwd(v.cam, v.n_vis, v.rec_gid.as<uint32_t>(), ws.grec.as<float>(), v.means,
+                     v.last.as<uint32_t>(), d_dL_drgb, ws.grec.as<double>(), s);
+    launch_project_bwd(v.cam, v.n_vis, v.rec_gid.as<uint32_t>(), ws.grec.as<double>(), v.means,
                        v.act_so.as<float4>(), v.act_q.as<float4>(), v.quats, v.sh, v.sh_degree,
                        v.filter_var, d_g_means, d_g_log_scales, d_g_quats, d_g_opacity_logits, d_g_sh, s);
     CUDA_TRY(cudaGetLastError());

@@ -19,7 +19,7 @@ namespace lodge {
 
 lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
                         const lodge_camera& cam, float* d_rgb, cudaStream_t s, Saved* save,
-                        lodge_frame_stats* st, bool end_sync);
+                        lodge_frame_stats* st, bool end_sync, float* importance);
 
 }  // namespace lodge
 
@@ -79,7 +79,7 @@ extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, i
                 r = ensure(ctx, sl.ws.img, img_bytes, s);
                 if (r == LODGE_OK)
                     r = render_one(ctx, sl, sc, (lodge_mode)rq.mode, rq.cam, sl.ws.img.as<float>(), s,
-                                   nullptr, &res.stats, true);
+                                   nullptr, &res.stats, true, nullptr);
                 if (r != LODGE_E_BUDGET || now_s() - res.start_s > wait_limit) break;
                 // admission by footprint: wait for another request to release memory
                 std::unique_lock<std::recursive_mutex> lk(ctx->mu);

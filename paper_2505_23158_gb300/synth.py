@@ -355,6 +355,30 @@ def random_street_cameras(scene: Scene, seed: int, n: int, width: int, height_px
     return cams
 
 
+def chunk_views(scene: Scene, chunk: int, seed: int, n: int, width: int, height_px: int,
+                fov_y_deg: float = 70.0, cam_height: float = 2.0,
+                pitch_deg: float = 10.0) -> List[Camera]:
+    """Views of one chunk of a square chunk grid (index j * grid + i): uniform
+    positions inside the chunk's cell at street height, uniform yaw, fixed
+    downward pitch -- camera positions within the chunk with random
+    orientations, as the visibility filtering of Sec. 3 uses."""
+    r = _rng(seed, 310 + chunk)
+    K = scene.chunk_centers.shape[0]
+    grid = int(round(math.sqrt(K)))
+    cell = scene.extent / grid
+    i, j = chunk % grid, chunk // grid
+    pitch = math.radians(pitch_deg)
+    cams = []
+    for _ in range(n):
+        x = r.uniform(i * cell, (i + 1) * cell)
+        y = r.uniform(j * cell, (j + 1) * cell)
+        yaw = r.uniform(0, 2 * math.pi)
+        pz = float(height(scene.height_params, x, y)) + cam_height
+        fwd = (math.cos(yaw) * math.cos(pitch), math.sin(yaw) * math.cos(pitch), -math.sin(pitch))
+        cams.append(look_at((x, y, pz), fwd, (0.0, 0.0, 1.0), width, height_px, fov_y_deg))
+    return cams
+
+
 def finetune_scene(seed: int = 0, n: int = 2_000_000, cell: float = 62.5,
                    center_xy=(500.0, 500.0)) -> Scene:
     """One chunk cell of the outdoor generator (level-0 density scaled so

@@ -176,6 +176,7 @@ def test_finetune_gradients_on_crop(finetune):
         # pixel terms of both signs); the adjoint's sequential evaluation
         # with division-based T adds a few roundings per term
         tol = max(1e-3, 3.0 * e32)
+        print(f"{name}: relative L2 error {e:.3g}, FP32 evaluation {e32:.3g}")
         assert e < tol, f"{name}: relative L2 error {e:.3g} (FP32 evaluation {e32:.3g})"
         assert not gn[rest].any(), f"{name}: gradient outside the crop's Gaussians"
 
