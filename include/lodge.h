@@ -191,6 +191,26 @@ lodge_status lodge_select_thresholds(lodge_ctx* ctx, int32_t scene_id, const lod
                                      int32_t n_candidates, double* d_out, int64_t* keys_out,
                                      void* stream);
 
+/* Eq. 5 (supplementary "Selecting chunk centers"): the number of chunk
+ * clusters for n camera positions (host, 3n doubles, metres) and first depth
+ * threshold d1 > 0: ceil((4 / d1) max_i |c_i - c_mean|), clamped to [1, n].
+ * *k_out (host) receives it.  Host-only; needs no device. */
+lodge_status lodge_num_clusters(const double* positions, int32_t n, double d1, int32_t* k_out);
+
+/* Chunk centres by K-means on camera positions (supplementary "Selecting
+ * chunk centers"), Lloyd's iteration in FP64: start from the k positions
+ * positions[init[j]] (host, k distinct indices, 1 <= k <= n); then repeat
+ * (a) assign each position to its nearest centre (squared Euclidean
+ * distance, ties to the lower centre index) and stop if no assignment
+ * changed, (b) move each centre to the mean of its positions (summed in
+ * index order; a centre without positions stays), at most max_iter times.
+ * centers_out (host, 3k) receives the centres, assign_out (host, n,
+ * optional) each position's nearest returned centre, iters_out (optional)
+ * the number of update steps done.  Host-only; needs no device. */
+lodge_status lodge_kmeans_centers(const double* positions, int32_t n, int32_t k,
+                                  const int32_t* init, int32_t max_iter, double* centers_out,
+                                  int32_t* assign_out, int32_t* iters_out);
+
 /* ---------------------------------------------------------------- render */
 
 /* Render n_cams cameras of one scene in `mode`.  d_rgb (device,

@@ -19,6 +19,8 @@ Public functions mirror the paper's steps:
   importance          largest blending weight per Gaussian in a view (Sec. 3)
   render              Eq. 1 compositing (binned or brute force)
   select_thresholds   greedy depth-threshold search (Sec. 3)
+  num_clusters        number of chunk clusters (supplementary Eq. 5)
+  kmeans_centers      K-means chunk centres from camera positions
 """
 from __future__ import annotations
 
@@ -372,6 +374,65 @@ def select_thresholds(osc: OracleScene, views, candidates):
         best = ok[np.argmin(row[ok])]     # argmin returns the first minimum
         d.append(cand[best])
     return d, table
+
+
+def num_clusters(positions, d1: float) -> int:
+    """Eq. 5 (supplementary "Selecting chunk centers"):
+    N = (4 / d_1) max_i |c_i - c_mean|, read as the ceiling, clamped to
+    [1, number of cameras].  The mean sums the positions in index order."""
+    p = np.asarray(positions, np.float64).reshape(-1, 3)
+    mean = [0.0, 0.0, 0.0]
+    for row in p:
+        for c in range(3):
+            mean[c] += float(row[c])
+    mean = [v / p.shape[0] for v in mean]
+    rmax = 0.0
+    for row in p:
+        dx, dy, dz = row[0] - mean[0], row[1] - mean[1], row[2] - mean[2]
+        rmax = max(rmax, math.sqrt((dx * dx + dy * dy) + dz * dz))
+    k = math.ceil(4.0 / d1 * rmax)
+    return int(min(max(k, 1), p.shape[0]))
+
+
+def _nearest(p, m):
+    best, bd = 0, None
+    for j in range(m.shape[0]):
+        dx, dy, dz = p[0] - m[j, 0], p[1] - m[j, 1], p[2] - m[j, 2]
+        d = (dx * dx + dy * dy) + dz * dz
+        if bd is None or d < bd:
+            best, bd = j, d
+    return best
+
+
+def kmeans_centers(positions, init, max_iter: int = 100):
+    """K-means (Lloyd) on camera positions (supplementary "Selecting chunk
+    centers"; the paper names the method, these are its textbook steps):
+    centres start at the positions of ``init``; each step assigns every
+    position to its nearest centre (ties to the lower index) and stops if no
+    assignment changed, else moves each centre to the mean of its positions
+    (a centre without positions stays).  Returns (centres, assignment to the
+    returned centres, number of update steps)."""
+    p = np.asarray(positions, np.float64).reshape(-1, 3)
+    m = p[np.asarray(init, np.int64)].copy()
+    a = [-1] * p.shape[0]
+    it = 0
+    while it < max_iter:
+        new = [_nearest(p[i], m) for i in range(p.shape[0])]
+        if new == a:
+            break
+        a = new
+        for j in range(m.shape[0]):
+            members = [i for i in range(p.shape[0]) if a[i] == j]
+            if not members:
+                continue
+            acc = [0.0, 0.0, 0.0]
+            for i in members:           # index order
+                for c in range(3):
+                    acc[c] += float(p[i, c])
+            m[j] = [v / len(members) for v in acc]
+        it += 1
+    assign = np.array([_nearest(p[i], m) for i in range(p.shape[0])], np.int32)
+    return m, assign, it
 
 
 def depth32(means, cam):

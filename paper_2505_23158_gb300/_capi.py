@@ -99,6 +99,8 @@ _SIGS = {
     "lodge_upload_chunks": [P, C.c_int32, P, C.c_int32, C.c_int],
     "lodge_select_lod": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int64, P],
     "lodge_select_thresholds": [P, C.c_int32, P, C.c_int32, P, C.c_int32, P, P, P],
+    "lodge_num_clusters": [P, C.c_int32, C.c_double, P],
+    "lodge_kmeans_centers": [P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P],
     "lodge_importance": [P, C.c_int32, C.c_int, C.c_int32, P, C.c_int32, P, P],
     "lodge_filter_chunk": [P, C.c_int32, C.c_int32, P, C.c_float, C.POINTER(C.c_int64), P],
     "lodge_render": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int32,

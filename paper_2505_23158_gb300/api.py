@@ -331,6 +331,28 @@ class Lodge:
                _stream(stream))
 
 
+def num_clusters(positions, d1: float) -> int:
+    """Eq. 5: number of chunk clusters for camera positions (n x 3)."""
+    p = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+    k = C.c_int32(0)
+    A.call("lodge_num_clusters", C.c_void_p(p.ctypes.data), int(p.shape[0]), float(d1), C.byref(k))
+    return k.value
+
+
+def kmeans_centers(positions, init, max_iter: int = 100):
+    """K-means chunk centres of camera positions from the given initial
+    indices: (centres k x 3, assignment n, update steps)."""
+    p = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+    ini = np.ascontiguousarray(init, np.int32)
+    cen = np.zeros((ini.size, 3), np.float64)
+    asg = np.zeros(p.shape[0], np.int32)
+    it = C.c_int32(0)
+    A.call("lodge_kmeans_centers", C.c_void_p(p.ctypes.data), int(p.shape[0]), int(ini.size),
+           C.c_void_p(ini.ctypes.data), int(max_iter), C.c_void_p(cen.ctypes.data),
+           C.c_void_p(asg.ctypes.data), C.byref(it))
+    return cen, asg, it.value
+
+
 class _RenderParams(torch.autograd.Function):
     """Differentiable render of raw Gaussian parameters through the library's
     forward (lodge_render_params) and hand-written adjoint

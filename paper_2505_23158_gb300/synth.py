@@ -379,6 +379,15 @@ def chunk_views(scene: Scene, chunk: int, seed: int, n: int, width: int, height_
     return cams
 
 
+def kmeans_init(n: int, k: int, seed: int) -> np.ndarray:
+    """k distinct seeded indices into n positions (initial K-means centres)."""
+    return _rng(seed, 320).choice(n, size=k, replace=False).astype(np.int32)
+
+
+def camera_positions(cams: Sequence[Camera]) -> np.ndarray:
+    return np.array([np.asarray(c.center, np.float64) for c in cams])
+
+
 def finetune_scene(seed: int = 0, n: int = 2_000_000, cell: float = 62.5,
                    center_xy=(500.0, 500.0)) -> Scene:
     """One chunk cell of the outdoor generator (level-0 density scaled so
