@@ -99,6 +99,12 @@ typedef struct {
     int32_t num_chunks;              /* K >= 0 chunk centres (0: FULL/LOD only) */
     int32_t residency;               /* lodge_residency_mode */
     const double* chunk_centers;     /* K x 3 */
+    int32_t filter2d;                /* 0: Sigma' = Sigma2D + 0.3 I (3DGS dilation);
+                                        1: the same, and the opacity scaled by
+                                        sqrt(det Sigma2D / det Sigma') (Mip-Splatting's
+                                        2D filter, supplementary "Details on training
+                                        the full representation") */
+    int32_t pad_;
 } lodge_scene_desc;
 
 typedef struct {
@@ -231,6 +237,17 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
 lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
                                const lodge_camera* cams, int32_t n_cams, float* h_rgb,
                                void* stream, lodge_frame_stats* stats);
+
+/* LOD rendering (Eq. 2 at each camera centre) with thresholds given per
+ * camera instead of the scene's: d_inner (host) holds n_cams rows of
+ * num_levels - 1 non-negative, ascending distances (+inf allowed).  This is
+ * the rendering of the LOD build loop (supplementary "LOD structure
+ * optimization steps"), which draws d_l from U(0.7 d_l, 1.3 d_l) each step;
+ * the caller draws the values.  Images and stats as lodge_render.
+ * Resident scenes only.  Synchronous on stream. */
+lodge_status lodge_render_lod(lodge_ctx* ctx, int32_t scene_id, const lodge_camera* cams,
+                              int32_t n_cams, const double* d_inner, float* d_rgb, void* stream,
+                              lodge_frame_stats* stats);
 
 /* Importance score (Sec. 3 "Importance pruning" and "Visibility filtering",
  * which follow RadSplat): render each of the n_cams cameras (host array) and

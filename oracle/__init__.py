@@ -68,7 +68,7 @@ class _Scene(C.Structure):
     _fields_ = [("n_total", C.c_int64), ("num_levels", C.c_int32), ("sh_degree", C.c_int32),
                 ("level_off", C.c_void_p), ("filter_var", C.c_void_p), ("means", C.c_void_p),
                 ("scales", C.c_void_p), ("quats", C.c_void_p), ("opac", C.c_void_p),
-                ("sh", C.c_void_p)]
+                ("sh", C.c_void_p), ("filter2d", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -150,7 +150,8 @@ class OracleScene:
         self._s = _Scene(self.n_total, self.num_levels, self.sh_degree,
                          self.level_off.ctypes.data, self.filter_var.ctypes.data,
                          self.means.ctypes.data, self.scales.ctypes.data,
-                         self.quats.ctypes.data, self.opac.ctypes.data, self.sh.ctypes.data)
+                         self.quats.ctypes.data, self.opac.ctypes.data, self.sh.ctypes.data,
+                         int(bool(getattr(scene, "filter2d", False))))
         self._chunk_cache = {}
 
     @property

@@ -70,6 +70,7 @@ typedef struct {
     const float* quats;         /* n_total x 4, unit (w, x, y, z) */
     const float* opac;          /* n_total, activated opacity */
     const float* sh;            /* n_total x 16 x 3 */
+    int32_t filter2d;           /* 1: opacity-compensated 2D filter (Mip-Splatting) */
 } orc_scene;
 
 int orc_version(void) { return 1; }
@@ -323,8 +324,9 @@ static int key_spec(const orc_scene* sc, const orc_camera* cam, int64_t g,
         float comp = ((s[0] / sig[0]) * (s[1] / sig[1])) * (s[2] / sig[2]);
         o = o * comp;
     }
-    if (!(o >= (float)ORC_ALPHA_MIN)) return 0;
-    float Q = extent_q(o);
+    /* without the compensated 2D filter the opacity is final here; with it,
+     * the opacity cull waits for the compensation below */
+    if (!sc->filter2d && !(o >= (float)ORC_ALPHA_MIN)) return 0;
 
     float u = px / pz, w = py / pz;
     float mx = cam->fx * u + cam->cx;
@@ -352,8 +354,23 @@ static int key_spec(const orc_scene* sc, const orc_camera* cam, int64_t g,
         B0[k] = a0 * sig[k];
         B1[k] = a1 * sig[k];
     }
-    float sxx = ((B0[0] * B0[0] + B0[1] * B0[1]) + B0[2] * B0[2]) + 0.3f;
-    float syy = ((B1[0] * B1[0] + B1[1] * B1[1]) + B1[2] * B1[2]) + 0.3f;
+    float aB = (B0[0] * B0[0] + B0[1] * B0[1]) + B0[2] * B0[2];
+    float cB = (B1[0] * B1[0] + B1[1] * B1[1]) + B1[2] * B1[2];
+    if (sc->filter2d) {
+        /* Mip-Splatting's 2D filter: o *= sqrt(det(Sigma2D) / det(Sigma2D + 0.3 I)),
+         * det(Sigma2D) = det(B B^T) as the sum of squared 2x2 minors of B
+         * (Cauchy-Binet), det(Sigma2D + 0.3 I) = det + 0.3 (aB + cB) + 0.09 */
+        float m01 = B0[0] * B1[1] - B0[1] * B1[0];
+        float m02 = B0[0] * B1[2] - B0[2] * B1[0];
+        float m12 = B0[1] * B1[2] - B0[2] * B1[1];
+        float D0 = (m01 * m01 + m02 * m02) + m12 * m12;
+        float D1 = (D0 + 0.3f * (aB + cB)) + 0.09f;
+        o = o * sqrtf(D0 / D1);
+        if (!(o >= (float)ORC_ALPHA_MIN)) return 0;
+    }
+    float Q = extent_q(o);
+    float sxx = aB + 0.3f;
+    float syy = cB + 0.3f;
     float rx = sqrtf(Q * sxx), ry = sqrtf(Q * syy);
     float x0 = ceilf((mx - rx) - 0.5f), x1 = floorf((mx + rx) - 0.5f);
     float y0 = ceilf((my - ry) - 0.5f), y1 = floorf((my + ry) - 0.5f);
@@ -462,9 +479,13 @@ static void splat64(const orc_scene* sc, const orc_camera* cam, int64_t g, doubl
                 for (int b = 0; b < 3; ++b) acc += T[i][a] * S[a][b] * T[j][b];
             C[i][j] = acc;
         }
+    double det0 = C[0][0] * C[1][1] - C[0][1] * C[1][0];
     C[0][0] += ORC_DILATION;
     C[1][1] += ORC_DILATION;
     double det = C[0][0] * C[1][1] - C[0][1] * C[1][0];
+    /* Mip-Splatting's 2D filter keeps the splat's integral: opacity times
+     * sqrt(det(Sigma2D) / det(Sigma2D + 0.3 I)) */
+    if (sc->filter2d) comp *= sqrt((det0 > 0.0 ? det0 : 0.0) / det);
     o->cov[0] = C[0][0]; o->cov[1] = C[0][1]; o->cov[2] = C[1][1];
     o->conic[0] = C[1][1] / det;
     o->conic[1] = -C[0][1] / det;

@@ -38,7 +38,7 @@ RESIDENT, STREAMED = 0, 1
 class lodge_scene_desc(C.Structure):
     _fields_ = [("num_levels", C.c_int32), ("sh_degree", C.c_int32), ("levels", C.c_void_p),
                 ("d_thresholds", C.c_void_p), ("num_chunks", C.c_int32), ("residency", C.c_int32),
-                ("chunk_centers", C.c_void_p)]
+                ("chunk_centers", C.c_void_p), ("filter2d", C.c_int32), ("pad_", C.c_int32)]
 
 
 class lodge_camera(C.Structure):
@@ -102,6 +102,7 @@ _SIGS = {
     "lodge_num_clusters": [P, C.c_int32, C.c_double, P],
     "lodge_kmeans_centers": [P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P],
     "lodge_importance": [P, C.c_int32, C.c_int, C.c_int32, P, C.c_int32, P, P],
+    "lodge_render_lod": [P, C.c_int32, P, C.c_int32, P, P, P, P],
     "lodge_filter_chunk": [P, C.c_int32, C.c_int32, P, C.c_float, C.POINTER(C.c_int64), P],
     "lodge_render": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int32,
                      C.POINTER(C.c_int64), P],

@@ -105,6 +105,7 @@ class Lodge:
         desc.num_chunks = int(cc.shape[0])
         desc.chunk_centers = cc.ctypes.data if cc.size else None
         desc.residency = int(residency)
+        desc.filter2d = int(bool(getattr(scene, "filter2d", False)))
         sid = C.c_int32()
         A.call("lodge_load_scene", self._h, C.byref(desc), C.byref(sid))
         self._num_levels[sid.value] = scene.num_levels
@@ -154,6 +155,24 @@ class Lodge:
                C.c_void_p(cand.ctypes.data), int(cand.size), C.c_void_p(d.ctypes.data),
                C.c_void_p(keys.ctypes.data), _stream(stream))
         return d[:L - 1], keys[:L - 1]
+
+    def render_lod(self, sid: int, cams, d_inner, stream=None):
+        """LOD renders with per-camera thresholds (rows of num_levels - 1).
+        Returns (images, stats)."""
+        cl = list(cams)
+        L = self._num_levels[sid]
+        d = np.ascontiguousarray(d_inner, np.float64).reshape(len(cl), max(L - 1, 0))
+        total = sum(c.width * c.height * 3 for c in cl)
+        out = torch.empty(max(total, 1), dtype=torch.float32, device=f"cuda:{self.device}")
+        st = (A.lodge_frame_stats * len(cl))()
+        A.call("lodge_render_lod", self._h, int(sid), camera_array(cl), len(cl),
+               C.c_void_p(d.ctypes.data) if d.size else None, _ptr(out), _stream(stream), st)
+        imgs, off = [], 0
+        for c in cl:
+            n = c.width * c.height * 3
+            imgs.append(out[off:off + n].view(c.height, c.width, 3))
+            off += n
+        return imgs, [stats_dict(s) for s in st]
 
     def importance(self, sid: int, mode: int, cams, score: Optional[torch.Tensor] = None,
                    chunk: int = -1, stream=None) -> torch.Tensor:

@@ -108,6 +108,7 @@ struct DevScene {
     int64_t n_total = 0;
     int32_t num_levels = 0;
     int32_t sh_degree = 3;
+    int32_t filter2d = 0;   // 1: opacity-compensated 2D filter
     int64_t level_off[kMaxLevels + 1] = {0};
     float filter_var[kMaxLevels] = {0};
     const float* mx = nullptr;   // means, one plane per axis
@@ -149,17 +150,18 @@ void launch_lod_select(const DevScene& sc, const float c32[3], const float* thr_
                        const float* thr_hi, uint32_t* out, uint32_t* d_count, uint32_t* status,
                        uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
 
-// K2: union of two gid-ascending lists with membership flags (bit 31 = A,
-// bit 30 = B).  marks: n_total bytes of scratch.
-void launch_chunk_union(const uint32_t* a, int64_t na, const uint32_t* b, int64_t nb,
-                        int64_t n_total, uint8_t* marks, uint32_t* out, uint32_t* d_count,
-                        uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
 
 // Visibility filtering: entries of list (n, gid ascending) whose score[gid]
 // (n_total floats) is >= thr, compacted in order into out; *d_count = kept.
 void launch_score_filter(const uint32_t* list, int64_t n, const float* score, float thr,
                          int64_t n_total, uint32_t* out, uint32_t* d_count, uint32_t* status,
                          uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
+
+// K2: union of two gid-ascending lists with membership flags (bit 31 = A,
+// bit 30 = B).  marks: n_total bytes of scratch.
+void launch_chunk_union(const uint32_t* a, int64_t na, const uint32_t* b, int64_t nb,
+                        int64_t n_total, uint8_t* marks, uint32_t* out, uint32_t* d_count,
+                        uint32_t* status, uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
 
 // K3: projection + SH + visibility compaction.
 struct ProjectOut {
@@ -234,7 +236,8 @@ int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 // rbits > 0: one packed word per pair, tile << rbits | record (tile_val
 // unused); rbits = 0: tile in tile_key, record in tile_val.
 constexpr int kEmitThreads = 256;
-constexpr int kEmitKeysPerCta = 2048;
+constexpr int kEmitKeysPerCta = 2048;   // slice of the key list (small records)
+constexpr int64_t kEmitWarpMinKeys = 32;  // mean keys per record for one warp per record
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
                  int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
                  int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,

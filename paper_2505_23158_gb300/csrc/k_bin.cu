@@ -62,7 +62,7 @@ emit_offsets_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     if (i < n_vis) koff[i] = s_prefix + excl;
 }
 
-// Pass 2: the key list is cut into slices of kEmitKeysPerCta keys; a CTA
+// Pass 2, many small records: the key list is cut into slices of kEmitKeysPerCta keys; a CTA
 // writes whole slices (grid-stride).  The (at most kEmitKeysPerCta) records
 // that own a slice are located by one warp-parallel search in koff, staged in
 // shared memory, and each key finds its record by binary search there, so
@@ -90,7 +90,7 @@ __device__ __forceinline__ int64_t warp_upper_bound(const uint32_t* __restrict__
 }
 
 __global__ void __launch_bounds__(kEmitThreads)
-emit_keys_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__ srec,
+emit_keys_sliced_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__ srec,
                  const uint2* __restrict__ srect, int64_t n_vis, int64_t n_keys, int32_t tiles_x,
                  uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits,
                  int passes, uint32_t last_mask, uint32_t* __restrict__ digit_hist,
@@ -155,6 +155,68 @@ emit_keys_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__
     }
 }
 
+// Pass 2, large records: one warp per depth-sorted record writes the record's keys,
+// koff[i] .. koff[i+1]-1, its rect row-major, the lanes striding over them
+// (warps of a CTA take consecutive records, CTAs stride over the list).  The
+// CTA also counts the tile sort's digits in shared-memory histograms flushed
+// once: the lowest digit per key (consecutive tiles fall in different bins),
+// the higher digits per rect row, whose tile ids are one contiguous range
+// that crosses a digit boundary at most once per 256 tiles.
+__global__ void __launch_bounds__(kEmitThreads)
+emit_keys_rect_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restrict__ srec,
+                 const uint2* __restrict__ srect, int64_t n_vis, int32_t tiles_x,
+                 uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits,
+                 int passes, uint32_t last_mask, uint32_t* __restrict__ digit_hist) {
+    __shared__ uint32_t s_hist[3][256];
+    for (int i = threadIdx.x; i < 3 * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * (kEmitThreads / 32);
+    for (int64_t i = (int64_t)blockIdx.x * (kEmitThreads / 32) + (threadIdx.x >> 5); i < n_vis;
+         i += wstride) {
+        const uint32_t k0 = koff[i];
+        const uint32_t cnt = koff[i + 1] - k0;
+        const uint2 rr = srect[i];
+        const uint32_t rec = srec[i];
+        const uint32_t tx0 = rr.x & 0xffffu, ty0 = rr.x >> 16;
+        const uint32_t w = (rr.y & 0xffffu) - tx0 + 1u, h = (rr.y >> 16) - ty0 + 1u;
+        // key k = lane + 32 j sits at row k / w, column k % w (stepped)
+        uint32_t row = lane / w, col = lane - row * w;
+        const uint32_t drow = 32u / w, dcol = 32u - drow * w;
+        for (uint32_t k = lane; k < cnt; k += 32) {
+            const uint32_t tile = (ty0 + row) * (uint32_t)tiles_x + tx0 + col;
+            if (rbits) {
+                tile_key[k0 + k] = (tile << rbits) | rec;
+            } else {
+                tile_key[k0 + k] = tile;
+                tile_val[k0 + k] = rec;
+            }
+            atomicAdd(&s_hist[0][tile & (passes == 1 ? last_mask : 0xffu)], 1u);
+            row += drow;
+            col += dcol;
+            if (col >= w) { col -= w; ++row; }
+        }
+        for (int p = 1; p < passes; ++p) {
+            const uint32_t mask = p == passes - 1 ? last_mask : 0xffu;
+            const int sh = 8 * p;
+            for (uint32_t r = lane; r < h; r += 32) {
+                uint32_t a = (ty0 + r) * (uint32_t)tiles_x + tx0;
+                const uint32_t b = a + w - 1u;
+                while (a <= b) {   // split [a, b] where digit p changes
+                    const uint32_t end = min(b, ((a >> sh) + 1u << sh) - 1u);
+                    atomicAdd(&s_hist[p][(a >> sh) & mask], end - a + 1u);
+                    a = end + 1u;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += kEmitThreads) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(digit_hist + i, c);
+    }
+}
+
 // exclusive scan of each pass's 256-bin digit histogram, in place
 __global__ void digit_scan_kernel(uint32_t* hist) {
     __shared__ uint32_t s_scan[33];
@@ -196,14 +258,23 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
     if (nb == 0) return;
     emit_offsets_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, koff, srec,
                                                               srect, status, tile_counter, err);
-    const int64_t nslices = (n_keys + kEmitKeysPerCta - 1) / kEmitKeysPerCta;
-    if (nslices == 0) return;
+    if (n_keys == 0) return;
     const int P = (key_bits + 7) / 8;
     const int last_bits = key_bits - 8 * (P - 1);
     const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
-    const unsigned grid = (unsigned)std::min<int64_t>(nslices, 152 * 4);
-    emit_keys_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, n_keys, tiles_x, tile_key,
-                                                   tile_val, rbits, P, last_mask, digit_hist, err);
+    if (n_keys >= kEmitWarpMinKeys * n_vis) {
+        // records average a warp's worth of keys or more: one warp per record
+        const unsigned grid = (unsigned)std::min<int64_t>((n_vis + kEmitThreads / 32 - 1) / (kEmitThreads / 32),
+                                                          152 * 8);
+        emit_keys_rect_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, tiles_x, tile_key,
+                                                            tile_val, rbits, P, last_mask, digit_hist);
+    } else {
+        const int64_t nslices = (n_keys + kEmitKeysPerCta - 1) / kEmitKeysPerCta;
+        const unsigned grid = (unsigned)std::min<int64_t>(nslices, 152 * 4);
+        emit_keys_sliced_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, n_keys, tiles_x,
+                                                              tile_key, tile_val, rbits, P, last_mask,
+                                                              digit_hist, err);
+    }
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
 }
 

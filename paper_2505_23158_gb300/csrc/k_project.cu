@@ -104,8 +104,9 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
         float comp = fm(fm(__fdiv_rn(so.x, sig0), __fdiv_rn(so.y, sig1)), __fdiv_rn(so.z, sig2));
         op = fm(op, comp);
     }
-    if (!(op >= (float)(1.0 / 255.0))) return false;
-    const float Q = extent_q(op);
+    // without the compensated 2D filter the opacity is final here; with it,
+    // the opacity cull waits for the compensation below
+    if (!sc.filter2d && !(op >= (float)(1.0 / 255.0))) return false;
     const float4 q = sq[idx];
     float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
     float mx = fa(fm(cam.fx, u), cam.cx);
@@ -134,8 +135,22 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
         k.B0[c] = fm(a0, sig[c]);
         k.B1[c] = fm(a1, sig[c]);
     }
-    float sxx = fa(fa(fa(fm(k.B0[0], k.B0[0]), fm(k.B0[1], k.B0[1])), fm(k.B0[2], k.B0[2])), 0.3f);
-    float syy = fa(fa(fa(fm(k.B1[0], k.B1[0]), fm(k.B1[1], k.B1[1])), fm(k.B1[2], k.B1[2])), 0.3f);
+    const float aB = fa(fa(fm(k.B0[0], k.B0[0]), fm(k.B0[1], k.B0[1])), fm(k.B0[2], k.B0[2]));
+    const float cB = fa(fa(fm(k.B1[0], k.B1[0]), fm(k.B1[1], k.B1[1])), fm(k.B1[2], k.B1[2]));
+    if (sc.filter2d) {
+        // Mip-Splatting's 2D filter: o' *= sqrt(det Sigma2D / det(Sigma2D + 0.3 I)),
+        // det Sigma2D = sum of squared 2x2 minors of B (Cauchy-Binet)
+        const float m01 = fs(fm(k.B0[0], k.B1[1]), fm(k.B0[1], k.B1[0]));
+        const float m02 = fs(fm(k.B0[0], k.B1[2]), fm(k.B0[2], k.B1[0]));
+        const float m12 = fs(fm(k.B0[1], k.B1[2]), fm(k.B0[2], k.B1[1]));
+        const float D0 = fa(fa(fm(m01, m01), fm(m02, m02)), fm(m12, m12));
+        const float D1 = fa(fa(D0, fm(0.3f, fa(aB, cB))), 0.09f);
+        op = fm(op, __fsqrt_rn(__fdiv_rn(D0, D1)));
+        if (!(op >= (float)(1.0 / 255.0))) return false;
+    }
+    const float Q = extent_q(op);
+    float sxx = fa(aB, 0.3f);
+    float syy = fa(cB, 0.3f);
     float rx = __fsqrt_rn(fm(Q, sxx)), ry = __fsqrt_rn(fm(Q, syy));
     float x0 = ceilf(fs(fs(mx, rx), 0.5f)), x1 = floorf(fs(fa(mx, rx), 0.5f));
     float y0 = ceilf(fs(fs(my, ry), 0.5f)), y1 = floorf(fs(fa(my, ry), 0.5f));

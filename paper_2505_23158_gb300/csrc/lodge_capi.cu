@@ -899,6 +899,8 @@ lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int3
         return fail(LODGE_E_INVALID, "bad chunk centres");
     if (desc->residency != kResident && desc->residency != kStreamed)
         return fail(LODGE_E_INVALID, "unknown residency %d", desc->residency);
+    if (desc->filter2d != 0 && desc->filter2d != 1)
+        return fail(LODGE_E_INVALID, "filter2d must be 0 or 1");
     if (desc->residency == kStreamed && desc->num_chunks < 1)
         return fail(LODGE_E_INVALID, "a streamed scene needs chunk centres");
     CUDA_TRY(cudaSetDevice(ctx->device));
@@ -907,6 +909,7 @@ lodge_status lodge_load_scene(lodge_ctx* ctx, const lodge_scene_desc* desc, int3
     DevScene& d = sc->dev;
     d.num_levels = L;
     d.sh_degree = desc->sh_degree;
+    d.filter2d = desc->filter2d;
     d.level_off[0] = 0;
     for (int l = 0; l < L; ++l) {
         const lodge_level_desc& lv = desc->levels[l];
@@ -1243,6 +1246,45 @@ lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode
     TRY(lodge_render(ctx, scene_id, mode, cams, n_cams, sl.ws.img.as<float>(), stream, 0, nullptr, stats));
     if (total) CUDA_TRY(cudaMemcpyAsync(h_rgb, sl.ws.img.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    return LODGE_OK;
+}
+
+// LOD rendering with per-camera thresholds (supplementary "LOD structure
+// optimization steps": the build loop renders with d_l drawn from
+// U(0.7 d_l, 1.3 d_l) per step; the caller draws them).
+lodge_status lodge_render_lod(lodge_ctx* ctx, int32_t scene_id, const lodge_camera* cams,
+                              int32_t n_cams, const double* d_inner, float* d_rgb, void* stream,
+                              lodge_frame_stats* stats) {
+    if (!ctx || !cams || !d_rgb || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
+    Scene* sc = get_scene(ctx, scene_id);
+    if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
+    if (sc->residency != kResident)
+        return fail(LODGE_E_NOT_RESIDENT, "scene %d is streamed by chunk: LOD rendering needs it resident",
+                    scene_id);
+    const int L = sc->dev.num_levels;
+    if (L > 1 && !d_inner) return fail(LODGE_E_INVALID, "d_inner is NULL");
+    for (int i = 0; i < n_cams; ++i)
+        for (int l = 0; l + 1 < L; ++l) {
+            const double v = d_inner[(size_t)i * (L - 1) + l];
+            if (!(v >= 0.0) || (l && !(v >= d_inner[(size_t)i * (L - 1) + l - 1])))
+                return fail(LODGE_E_INVALID, "camera %d: thresholds must be non-negative and ascending", i);
+        }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot& sl = *ctx->slots[0];
+    size_t off = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        TRY(check_cam(cams[i]));
+        Active act;
+        int64_t n = 0;
+        TRY(run_lod_select(ctx, sl, sc->dev, cams[i].center, L > 1 ? d_inner + (size_t)i * (L - 1) : nullptr,
+                           s, &n));
+        act.list = sl.ws.list.as<uint32_t>();
+        act.n = n;
+        TRY(render_frame(ctx, sl, sc->dev, act, cams[i], d_rgb + off, s, nullptr,
+                         stats ? stats + i : nullptr, true));
+        off += (size_t)cams[i].width * cams[i].height * 3;
+    }
     return LODGE_OK;
 }
 

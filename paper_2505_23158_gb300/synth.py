@@ -68,6 +68,7 @@ class Scene:
     sh_degree: int = 3
     extent: float = 0.0                 # side of the square world (outdoor)
     height_params: Optional[dict] = None
+    filter2d: bool = False              # opacity-compensated 2D filter (Mip-Splatting)
 
     @property
     def num_levels(self) -> int:

@@ -283,3 +283,49 @@ def test_hbm_budget_enforced(torch_cuda):
         with pytest.raises(LodgeError) as e:
             c.load_scene(scene)
         assert e.value.status == 6
+
+
+def test_lod_with_randomised_thresholds(ctx, torch_cuda):
+    """LOD renders whose thresholds are drawn per frame from U(0.7 d_l,
+    1.3 d_l) (supplementary "LOD structure optimization steps"): selected
+    counts, keys and pixels equal the oracle's for the same thresholds."""
+    scene, cams = synth.workload_outdoor(seed=6, n_poses=20, scale=0.02, width=320, height_px=180)
+    osc = O.OracleScene(scene)
+    rng = np.random.default_rng(11)
+    d0 = np.asarray(scene.d_thresholds, np.float64)
+    views = cams[::5]
+    d = np.stack([np.sort(d0 * rng.uniform(0.7, 1.3, size=d0.size)) for _ in views])
+    sid = ctx.load_scene(scene)
+    imgs, stats = ctx.render_lod(sid, views, d)
+    for cam, dd, img, st in zip(views, d, imgs, stats):
+        g, _ = O.lod_select(osc, cam.center, dd)
+        ref = O.render(osc, cam, g)
+        assert st["n_active"] == g.size and st["n_keys"] == ref["n_keys"]
+        compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], "randomised LOD")
+
+
+@pytest.mark.parametrize("which", ["plain", "outdoor"])
+def test_compensated_2d_filter(ctx, torch_cuda, which):
+    """Scenes rendered with Mip-Splatting's opacity-compensated 2D filter:
+    keys bit-exact (the compensation enters the opacity cull and extent) and
+    pixels within the bars."""
+    from paper_2505_23158_gb300.api import CHUNK_BLEND, FULL
+    if which == "plain":
+        scene, cams = synth.workload_plain(0)
+        mode, omode = FULL, O.MODE_FULL
+    else:
+        scene, cams = synth.workload_outdoor(seed=7, n_poses=10, scale=0.02, width=320, height_px=180)
+        cams = cams[::3]
+        mode, omode = CHUNK_BLEND, O.MODE_CHUNK_BLEND
+    scene.filter2d = True
+    osc = O.OracleScene(scene)
+    sid = ctx.load_scene(scene)
+    for cam in cams:
+        g, m, _ = O.active_set(osc, omode, cam)
+        img, st, h = ctx.render(sid, mode, cam, save=True)
+        keys, _ = ctx.debug_keys(h)
+        ctx.release(h)
+        k_ref, _ = O.keys(osc, cam, g, m)
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref)
+        ref = O.render(osc, cam, g, m)
+        compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"filter2d {which}")

@@ -60,6 +60,35 @@ def test_single_isotropic_gaussian_closed_form():
     assert (r["ncontrib"] == (a > 0)).all()
 
 
+def test_single_gaussian_with_compensated_2d_filter():
+    """Mip-Splatting's 2D filter (supplementary "Details on training the full
+    representation"): with Sigma2D = s^2 I (s = fx sigma / z), Sigma' = (s^2 +
+    0.3) I and the opacity is scaled by sqrt(det Sigma2D / det Sigma') =
+    s^2 / (s^2 + 0.3), so each pixel is o s^2/(s^2+0.3) exp(-d^2 / (2 (s^2 +
+    0.3))) rgb, and the splat's integral no longer depends on the 0.3."""
+    sigma, z, o = 0.01, 3.0, 0.8
+    rgb = (0.9, 0.4, 0.2)
+    sc = _single_level_scene([[0, 0, 0]], [[math.log(sigma)] * 3], [[1, 0, 0, 0]],
+                             [_logit(o)], [_sh_for_rgb(rgb)])
+    sc.filter2d = True
+    cam = synth.plain_camera(64, 64)
+    r = O.render(O.OracleScene(sc), cam, np.arange(1))
+    s_eff = float(np.float32(math.exp(np.float32(math.log(sigma)))))
+    s2 = cam.fx ** 2 * s_eff ** 2 / z ** 2
+    o_eff = float(np.float32(1 / (1 + math.exp(-np.float32(_logit(o))))))
+    ys, xs = np.mgrid[0:64, 0:64]
+    d2 = (xs + 0.5 - cam.cx) ** 2 + (ys + 0.5 - cam.cy) ** 2
+    a = np.minimum(0.99, o_eff * s2 / (s2 + 0.3) * np.exp(-0.5 * d2 / (s2 + 0.3)))
+    a = np.where(a >= 1 / 255, a, 0.0)
+    assert np.abs(r["rgb"] - a[..., None] * np.asarray(rgb)).max() < 1e-6
+    # integral: o * 2 pi s^2 with the filter, o * 2 pi (s^2 + 0.3) without
+    plain = O.render(O.OracleScene(_single_level_scene([[0, 0, 0]], [[math.log(sigma)] * 3],
+                                                       [[1, 0, 0, 0]], [_logit(o)],
+                                                       [_sh_for_rgb(rgb)])), cam, np.arange(1))
+    ratio = r["rgb"][..., 0].sum() / plain["rgb"][..., 0].sum()
+    assert abs(ratio - s2 / (s2 + 0.3)) < 0.02
+
+
 def test_two_gaussians_closed_form():
     """Two Gaussians on the axis: front alpha1 c1 + (1 - alpha1) alpha2 c2,
     the nearer one in front regardless of input order."""
