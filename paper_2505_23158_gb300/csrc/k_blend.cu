@@ -1,12 +1,13 @@
 // K7: per-tile front-to-back alpha compositing (Eq. 1; Sec. 3
-// "Preliminaries: 3DGS").  One CTA per 16x16 tile, one thread per pixel;
-// each warp covers an 8x4 block so that its pixels terminate together.
-// The tile's Gaussians arrive in batches of 256 records, gathered from the
-// projection records into shared memory with cp.async and double-buffered
-// (batch b+1 is in flight while batch b is composited).  A pixel stops at
-// the first Gaussian that would take its transmittance below 1e-4; a warp
-// whose 32 pixels have all stopped skips the batch, and the CTA leaves as
-// soon as all 256 have stopped.
+// "Preliminaries: 3DGS").  One CTA of 128 threads per 16x16 tile, two pixels
+// per thread (one column, 4 rows apart), so each record read from shared
+// memory serves two pixels; each warp covers an 8x8 block so that its
+// pixels terminate together.  The tile's Gaussians arrive in batches of 128
+// records, gathered from the projection records into shared memory with
+// cp.async and double-buffered (batch b+1 is in flight while batch b is
+// composited).  A pixel stops at the first Gaussian that would take its
+// transmittance below 1e-4; a warp whose 64 pixels have all stopped skips
+// the batch, and the CTA leaves as soon as all 256 have stopped.
 //
 // Per pixel and Gaussian (record = mean', upper-triangular U with
 // U^T U = (1/2) log2(e) Sigma'^-1, opacity o', colour):
@@ -19,7 +20,9 @@ namespace lodge {
 
 namespace {
 
-constexpr int kBatch = 256;
+constexpr int kBatch = 256;        // importance kernel: records per batch
+constexpr int kBlendThreads = 128; // blend: two pixels per thread
+constexpr int kBlendBatch = 128;   // blend: records per batch (one per thread)
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -39,30 +42,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBlendThreads)
 blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __restrict__ ranges,
              const uint32_t* __restrict__ tile_val, uint32_t vmask, uint32_t n_keys, uint32_t n_rec,
              const float4* __restrict__ rec_a,
              const float4* __restrict__ rec_b, const float* __restrict__ rec_c,
              float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_last) {
-    __shared__ float4 sa[2][kBatch];
-    __shared__ float4 sb[2][kBatch];
-    __shared__ float sc[2][kBatch];
+    __shared__ float4 sa[2][kBlendBatch];
+    __shared__ float4 sb[2][kBlendBatch];
+    __shared__ float sc[2][kBlendBatch];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // warp w covers the 8x8 block (w & 1, w >> 1) of the tile; a lane owns
+    // two pixels of one column, 4 rows apart
     const int x = tx * kTile + (warp & 1) * 8 + (lane & 7);
-    const int y = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside = x < width && y < height;
-    const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
+    const int y0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3), y1 = y0 + 4;
+    const bool in0 = x < width && y0 < height, in1 = x < width && y1 < height;
+    const float pxf = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
     uint2 rg = ranges[tile];
     if (rg.y > n_keys || rg.x > rg.y) rg = make_uint2(0, 0);  // never for a consistent sort
     const int n = (int)(rg.y - rg.x);
-    const int nb = (n + kBatch - 1) / kBatch;
+    const int nb = (n + kBlendBatch - 1) / kBlendBatch;
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    bool done = !inside;
-    uint32_t last = 0;
+    float T0 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f;
+    float T1 = 1.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+    bool done0 = !in0, done1 = !in1;
+    uint32_t last0 = 0, last1 = 0;
 
     if (nb > 0) {
         if (tid < n) {
@@ -76,7 +82,7 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
     for (int b = 0; b < nb; ++b) {
         const int buf = b & 1;
         if (b + 1 < nb) {
-            int k = (b + 1) * kBatch + tid;
+            int k = (b + 1) * kBlendBatch + tid;
             if (k < n) {
                 uint32_t j = min(tile_val[rg.x + k] & vmask, n_rec - 1u);
                 cp_async16(&sa[buf ^ 1][tid], rec_a + j);
@@ -87,37 +93,72 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
-        const int cnt = min(kBatch, n - b * kBatch);
-        if (!__all_sync(0xffffffffu, done)) {
-            for (int k = 0; k < cnt && !done; ++k) {
+        const int cnt = min(kBlendBatch, n - b * kBlendBatch);
+        if (!__all_sync(0xffffffffu, done0 && done1)) {
+            for (int k = 0; k < cnt && !(done0 && done1); ++k) {
                 const float4 a = sa[buf][k];
-                const float dx = pxf - a.x, dy = pyf - a.y;
-                const float t = fmaf(a.z, dx, a.w * dy);
                 const float4 bb = sb[buf][k];
-                const float wq = bb.x * dy;
-                const float q = fmaf(t, t, wq * wq);
-                const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
-                if (alpha < (1.0f / 255.0f)) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < 1e-4f) { done = true; break; }
-                const float wgt = T * alpha;
-                C0 = fmaf(wgt, bb.z, C0);
-                C1 = fmaf(wgt, bb.w, C1);
-                C2 = fmaf(wgt, sc[buf][k], C2);
-                T = Tn;
-                last = (uint32_t)(b * kBatch + k + 1);
+                const float dx = pxf - a.x;
+                if (!done0) {
+                    const float dy = py0 - a.y;
+                    const float t = fmaf(a.z, dx, a.w * dy);
+                    const float wq = bb.x * dy;
+                    const float q = fmaf(t, t, wq * wq);
+                    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+                    if (alpha >= (1.0f / 255.0f)) {
+                        const float Tn = T0 * (1.f - alpha);
+                        if (Tn < 1e-4f) {
+                            done0 = true;
+                        } else {
+                            const float wgt = T0 * alpha;
+                            C00 = fmaf(wgt, bb.z, C00);
+                            C01 = fmaf(wgt, bb.w, C01);
+                            C02 = fmaf(wgt, sc[buf][k], C02);
+                            T0 = Tn;
+                            last0 = (uint32_t)(b * kBlendBatch + k + 1);
+                        }
+                    }
+                }
+                if (!done1) {
+                    const float dy = py1 - a.y;
+                    const float t = fmaf(a.z, dx, a.w * dy);
+                    const float wq = bb.x * dy;
+                    const float q = fmaf(t, t, wq * wq);
+                    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+                    if (alpha >= (1.0f / 255.0f)) {
+                        const float Tn = T1 * (1.f - alpha);
+                        if (Tn < 1e-4f) {
+                            done1 = true;
+                        } else {
+                            const float wgt = T1 * alpha;
+                            C10 = fmaf(wgt, bb.z, C10);
+                            C11 = fmaf(wgt, bb.w, C11);
+                            C12 = fmaf(wgt, sc[buf][k], C12);
+                            T1 = Tn;
+                            last1 = (uint32_t)(b * kBlendBatch + k + 1);
+                        }
+                    }
+                }
             }
         }
-        if (__syncthreads_count(done) == 256) break;
+        if (__syncthreads_count(done0 && done1) == kBlendThreads) break;
     }
     cp_async_wait0();
-    if (inside) {
-        const int64_t pix = (int64_t)y * width + x;
-        out_rgb[3 * pix + 0] = C0;
-        out_rgb[3 * pix + 1] = C1;
-        out_rgb[3 * pix + 2] = C2;
-        if (out_T) out_T[pix] = T;
-        if (out_last) out_last[pix] = last;
+    if (in0) {
+        const int64_t pix = (int64_t)y0 * width + x;
+        out_rgb[3 * pix + 0] = C00;
+        out_rgb[3 * pix + 1] = C01;
+        out_rgb[3 * pix + 2] = C02;
+        if (out_T) out_T[pix] = T0;
+        if (out_last) out_last[pix] = last0;
+    }
+    if (in1) {
+        const int64_t pix = (int64_t)y1 * width + x;
+        out_rgb[3 * pix + 0] = C10;
+        out_rgb[3 * pix + 1] = C11;
+        out_rgb[3 * pix + 2] = C12;
+        if (out_T) out_T[pix] = T1;
+        if (out_last) out_last[pix] = last1;
     }
 }
 
@@ -219,7 +260,7 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
                   int64_t n_rec, const BlendOut& o, cudaStream_t s) {
     int ntiles = cam.tiles_x * cam.tiles_y;
     if (ntiles == 0) return;
-    blend_kernel<<<ntiles, 256, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val, vmask,
+    blend_kernel<<<ntiles, kBlendThreads, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val, vmask,
                                         (uint32_t)n_keys, (uint32_t)std::max<int64_t>(n_rec, 1),
                                         rec_a, rec_b, rec_c, o.rgb, o.T_final, o.last);
 }
