@@ -222,11 +222,16 @@ constexpr int64_t sort_scratch_words(int64_t n, int passes) {
 }
 // digit_offsets: optional exclusive per-pass digit offsets (passes x 256)
 // that replace the upfront histogram; final_keys = false skips writing the
-// keys in the last pass (only the values are wanted).
+// keys in the last pass (only the values are wanted).  ranges: for a sort by
+// tile (tile = key >> shift0), the last pass also records each tile's
+// [begin, end) in the output for tiles < range_tiles; .x must start at
+// 0xffffffff and .y at 0 (a tile without keys keeps begin > end).  Not
+// written if n <= 1.
 size_t sort_scratch_bytes(int64_t n, int key_bits);
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
-                    const uint32_t* digit_offsets = nullptr, bool final_keys = true, int shift0 = 0);
+                    const uint32_t* digit_offsets = nullptr, bool final_keys = true, int shift0 = 0,
+                    uint2* ranges = nullptr, uint32_t range_tiles = 0);
 int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
 // K4: emit (tile, record) pairs in depth order.  koff: n_vis + 1 words;

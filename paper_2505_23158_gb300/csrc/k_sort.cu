@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(kSortThreads, 4)
 onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
               uint32_t dmask, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ status,
-              uint32_t* __restrict__ counter, uint32_t* __restrict__ err) {
+              uint32_t* __restrict__ counter, uint32_t* __restrict__ err, uint2* __restrict__ ranges,
+              int range_shift, uint32_t range_tiles) {
     constexpr int kTileN = kSortThreads * kIPT;
     __shared__ uint32_t s_whist[kWarps][kRadix];
     __shared__ uint32_t s_keys[kTileN];
@@ -183,6 +184,19 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
         if ((int64_t)out < n) {
             if (kWriteKeys) kout[out] = key;
             if (kValues) vout[out] = s_vals[i];
+            if (ranges) {
+                // last pass of a sort by tile: the keys of one tile are one
+                // run here and one run in the output; the first and last
+                // key of each run of this tile bound the tile's range
+                const uint32_t t = key >> range_shift;
+                if (t < range_tiles) {
+                    if (i == 0 || (s_keys[i - 1] >> range_shift) != t) atomicMin(&ranges[t].x, out);
+                    if (i + 1 == total || (s_keys[i + 1] >> range_shift) != t)
+                        atomicMax(&ranges[t].y, out + 1u);
+                } else {
+                    atomicOr(err, kErrBadIndex);
+                }
+            }
         } else {
             atomicOr(err, kErrOverflow);  // only after a look-back gave up
         }
@@ -203,13 +217,14 @@ static_assert(kSmallIPT * kSortThreads == kSortTileSmall, "small tile must be wh
 template <bool kWK, bool kV>
 void launch_pass(bool small, int64_t ntiles, const uint32_t* ki, const uint32_t* vi, uint32_t* ko,
                  uint32_t* vo, int64_t n, int shift, uint32_t dm, const uint32_t* off, uint32_t* st,
-                 uint32_t* ctr, uint32_t* err, cudaStream_t s) {
+                 uint32_t* ctr, uint32_t* err, uint2* ranges, int range_shift, uint32_t range_tiles,
+                 cudaStream_t s) {
     if (small)
         onesweep_pass<kSmallIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err);
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles);
     else
         onesweep_pass<kSortIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err);
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles);
 }
 
 }  // namespace
@@ -220,7 +235,8 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
-                    const uint32_t* digit_offsets, bool final_keys, int shift0) {
+                    const uint32_t* digit_offsets, bool final_keys, int shift0, uint2* ranges,
+                    uint32_t range_tiles) {
     const int P = passes_for(key_bits);
     if (n <= 1 || P == 0) return 0;
     const bool small = sort_tile_for(n) == kSortTileSmall;
@@ -248,11 +264,12 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
         uint32_t* stp = status + (size_t)p * ntiles * kRadix;
         const bool wk = !(p == P - 1 && !final_keys);
         const int sh = shift0 + 8 * p;
+        uint2* rg = p == P - 1 ? ranges : nullptr;
         if (values) {
-            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, s);
-            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, s);
+            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, s);
+            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, s);
         } else {
-            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, s);
+            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, s);
         }
         std::swap(ki, ko);
         std::swap(vi, vo);

@@ -543,23 +543,33 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
                 ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
     prof_end(sl, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_keys > 0 ? 2 : 0));
 
+    // ---- K6 tile ranges: recorded by the tile sort's last pass (begin by
+    // atomic minimum from 0xffffffff, end by atomic maximum from 0); with at
+    // most one key the sort does not run and K6 scans the key list instead
+    const bool fused_ranges = n_keys > 1;
+    TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
+    CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
+    if (fused_ranges && ntiles_img)
+        CUDA_TRY(cudaMemset2DAsync(ws.ranges.p, sizeof(uint2), 0xff, sizeof(uint32_t), (size_t)ntiles_img, s));
+
     // ---- K5 tile sort (stable: keeps depth order within a tile)
     prof_begin(sl, LODGE_STAGE_TILE_SORT, s);
     int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), rbits ? nullptr : ws.tval.as<uint32_t>(),
                              ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_keys,
-                             tbits, ws.sort.p, sl.d_small + kSmErr, s, ws.doffs.as<uint32_t>(), true, rbits);
+                             tbits, ws.sort.p, sl.d_small + kSmErr, s, ws.doffs.as<uint32_t>(), true, rbits,
+                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)ntiles_img);
     prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_keys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
     const uint32_t* rec_of_pair = rbits ? ks.as<uint32_t>() : vs.as<uint32_t>();
     const uint32_t vmask = rbits ? (1u << rbits) - 1u : 0xffffffffu;
+    if (!fused_ranges) {
+        prof_begin(sl, LODGE_STAGE_RANGES, s);
+        launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, rbits, s);
+        prof_end(sl, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
+    }
 
-    // ---- K6 ranges, K7 blend
-    TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
-    CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
-    prof_begin(sl, LODGE_STAGE_RANGES, s);
-    launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, rbits, s);
-    prof_end(sl, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
+    // ---- K7 blend
     BlendOut bo{d_rgb, nullptr, nullptr};
     if (save) {
         const size_t npix = (size_t)c.width * c.height;
