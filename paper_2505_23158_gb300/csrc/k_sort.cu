@@ -91,7 +91,7 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
 
     // warp-private stable ranking in (j, lane) order = input order; ranks
     // (< 2^16) packed two per register.  The lanes holding the same digit
-    // are found with one ballot per digit bit (cheaper than match.any); the
+    // are found either with match.any or with one ballot per digit bit; the
     // first lane of each group adds the group's size to the warp's count
     // with a shared atomic and hands the previous count to the group by a
     // shuffle (no warp barriers in the loop).
@@ -101,12 +101,19 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     for (int j = 0; j < kIPT; ++j) {
         const bool valid = j * 32 + lane < nvalid;
         const uint32_t d = valid ? (k[j] >> shift) & dmask : 0u;
-        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers;
+        if (j % 3 == 0) {
+            // every third key through match.any (the ADU pipe), the others
+            // through ballots (the ALU pipe), so that both pipes share the work
+            peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        } else {
+            peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-        for (int bit = 0; bit < 8; ++bit) {   // bits above a short last digit are 0: no-ops
-            const bool on = (d >> bit) & 1u;
-            const uint32_t m = __ballot_sync(0xffffffffu, on);
-            peers &= on ? m : ~m;
+            for (int bit = 0; bit < 8; ++bit) {   // bits above a short last digit are 0: no-ops
+                const bool on = (d >> bit) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, on);
+                peers &= on ? m : ~m;
+            }
         }
         if (!valid) peers = 1u << lane;
         const int leader = __ffs(peers) - 1;
