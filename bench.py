@@ -5,10 +5,11 @@ Workload: the outdoor LOD scene (16M / 4M / 1M / 250k Gaussians over a 1 km x
 1 km heightfield, 16 x 16 chunk grid, SH degree 3, fp32 attributes) and a
 300-pose street-level trajectory at 1920 x 1080.  A step renders
 --poses-per-step consecutive poses of the trajectory in LOD+chunk mode with
-opacity blending (the paper's method) through one render call (frames one
-after another on one stream; the host prepares a frame while the previous
-one finishes); value = frames/s over all ranks.  The latency of a single
-frame rendered alone is reported beside it.  The
+opacity blending (the paper's method) through one render call (the call's
+frames alternate between two streams, so one frame's stages overlap the
+next one's); value = frames/s over all ranks.  The latency of a single
+frame rendered alone, and the per-stage device times of such frames, are
+reported beside it.  The
 same poses are also rendered at full detail (every level-0 Gaussian) on the
 same GPU for the speedup.  Inputs are resident in HBM before timing (5.0 GB
 scene, larger than L2, no flush between steps).
@@ -63,6 +64,11 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--large", action="store_true",
+                    help="also time the large scene (60M level-0 Gaussians, 64 cameras at 4K)")
+    ap.add_argument("--large-scale", type=float, default=1.0)
+    ap.add_argument("--serve-batch", type=int, default=16,
+                    help="frames per step of the batched serving run")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="scene size factor of the serving scenes (1.0 = 2M/8M/16M/30M)")
@@ -305,17 +311,21 @@ def run_lodge(args, rank, world, local_rank):
             lat.append(a.elapsed_time(b))
         return lat
 
-    # warm-up (also grows every scratch buffer to its steady size)
+    # warm-up, the same calls as the timed steps (grows every scratch buffer,
+    # of both slots a step's frames alternate between, to its steady size)
     for s in range(args.warmup):
-        for cam in frames(s):
-            ctx.render(sid, CHUNK_BLEND, cam, out=out)
-    for cam in frames(0)[:2]:
-        ctx.render(sid, FULL, cam, out=out)
+        if args.per_frame_calls:
+            for cam in frames(s):
+                ctx.render(sid, CHUNK_BLEND, cam, out=out)
+        else:
+            ctx.render(sid, CHUNK_BLEND, frames(s), out=out_step)
+    ctx.render(sid, FULL, frames(0)[:2], out=out_step)
     torch.cuda.synchronize()
 
-    # ---- timed: LOD + chunk + opacity blending
+    # ---- timed: LOD + chunk + opacity blending.  No event timing inside the
+    # timed region (the counters of frames, keys and launches still run).
     clk = ClockSampler(local_rank)
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)
     clk.start()
     # NVTX range "timed_chunk_blend" marks the timed launches for profilers
     # (ncu --nvtx --nvtx-include timed_chunk_blend/)
@@ -323,20 +333,27 @@ def run_lodge(args, rank, world, local_rank):
     t_blend = timed(CHUNK_BLEND, args.steps)
     torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
+    prof_timed = ctx.profile_read()
     n_frames = args.steps * P
     value = job_throughput(n_frames, world, t_blend)
 
     # ---- full detail on the same poses
     fsteps = args.full_steps if args.full_steps is not None else max(1, args.steps // 2)
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)
     t_full = timed(FULL, fsteps)
+    prof_full_timed = ctx.profile_read()
+    full_fps = job_throughput(fsteps * P, world, t_full)
+
+    # ---- single frames, one call each: the latency of a frame and, with
+    # event timing per stage, the stage breakdown and the roofline (frames of
+    # one call overlap on two streams, which would blur per-stage events)
+    ctx.profile_enable(True)
+    lat = frame_latency(CHUNK_BLEND, min(len(cams), 100))
+    prof = ctx.profile_read()
+    ctx.profile_enable(True)
+    lat_full = frame_latency(FULL, 10)
     prof_full = ctx.profile_read()
     ctx.profile_enable(False)
-    full_fps = job_throughput(fsteps * P, world, t_full)
-    lat = frame_latency(CHUNK_BLEND, min(len(cams), 100))
-    lat_full = frame_latency(FULL, 10)
 
     # ---- end to end through the host-buffer entry point (camera H2D, image D2H)
     host = torch.empty(npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)
@@ -353,7 +370,7 @@ def run_lodge(args, rank, world, local_rank):
     pk, pk_kind = peaks()
     ms = prof["ms"]
     dom = max(ms, key=lambda k: ms[k])
-    launches = sum(prof["launches"].values())
+    launches = sum(prof_timed["launches"].values())
     roof = None
     if dom == "blend":
         # ALU-bound: bound by the FP32 pipes; report against the SM count x
@@ -403,12 +420,12 @@ def run_lodge(args, rank, world, local_rank):
                              "p99": round(float(np.percentile(lat, 99)), 4),
                              "full_p50": round(float(np.percentile(lat_full, 50)), 4)},
         "serve_latency": None,
-        "per_frame": {"active": prof["active"] // max(prof["frames"], 1),
-                      "visible": prof["visible"] // max(prof["frames"], 1),
-                      "keys": prof["keys"] // max(prof["frames"], 1),
-                      "full_active": prof_full["active"] // max(prof_full["frames"], 1),
-                      "full_visible": prof_full["visible"] // max(prof_full["frames"], 1),
-                      "full_keys": prof_full["keys"] // max(prof_full["frames"], 1)},
+        "per_frame": {"active": prof_timed["active"] // max(prof_timed["frames"], 1),
+                      "visible": prof_timed["visible"] // max(prof_timed["frames"], 1),
+                      "keys": prof_timed["keys"] // max(prof_timed["frames"], 1),
+                      "full_active": prof_full_timed["active"] // max(prof_full_timed["frames"], 1),
+                      "full_visible": prof_full_timed["visible"] // max(prof_full_timed["frames"], 1),
+                      "full_keys": prof_full_timed["keys"] // max(prof_full_timed["frames"], 1)},
         "stage_ms_per_frame": stages, "stage_ms_per_frame_full": stages_full,
         "stage_gbs": stage_gbs,
         "e2e": {"value": round(e2e_fps, 2), "unit": UNIT, "h2d_bytes_per_step": 104 * P,
@@ -426,6 +443,50 @@ def run_lodge(args, rank, world, local_rank):
     if not args.no_serve:
         torch.cuda.empty_cache()
         res["serve_latency"] = run_serve(args, local_rank)
+    if args.large:
+        torch.cuda.empty_cache()
+        res["large_scene"] = run_large(args, local_rank)
+    return res
+
+
+def run_large(args, local_rank):
+    """The large indoor+outdoor scene: 60M level-0 Gaussians over 6 levels,
+    32x32 chunks, a batch of 64 cameras at 3840x2160 rendered by one call,
+    LOD + chunks + opacity blending against full detail (all 60M level-0
+    Gaussians) on the same GPU."""
+    import torch
+    from paper_2505_23158_gb300 import synth
+    from paper_2505_23158_gb300.api import CHUNK_BLEND, FULL, Lodge
+    t0 = time.time()
+    scene, cams = synth.workload_large(seed=args.seed, n_cams=64, scale=args.large_scale)
+    t_gen = time.time() - t0
+    dev = torch.device("cuda", local_rank)
+    npix = cams[0].width * cams[0].height
+    out = torch.empty(len(cams) * npix * 3, dtype=torch.float32, device=dev)
+    res = {}
+    with Lodge(local_rank) as ctx:
+        sid = ctx.load_scene(scene)
+        for name, mode in (("chunk_blend", CHUNK_BLEND), ("full", FULL)):
+            ctx.render(sid, mode, cams, out=out)          # warm-up, grows scratch
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                _, st = ctx.render(sid, mode, cams, out=out)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            res[name] = {"batch_ms": round(float(np.median(ts)), 2),
+                         "frames_per_s": round(len(cams) / (float(np.median(ts)) / 1e3), 1),
+                         "keys_per_frame": int(np.mean([s["n_keys"] for s in st])),
+                         "visible_per_frame": int(np.mean([s["n_visible"] for s in st]))}
+    res["speedup_vs_full"] = round(res["full"]["batch_ms"] / res["chunk_blend"]["batch_ms"], 3)
+    res["workload"] = (f"large indoor+outdoor scene {scene.n_total} Gaussians over 6 levels, "
+                       f"32x32 chunks, 64 cameras at {cams[0].width}x{cams[0].height} per call, "
+                       "median of 3 calls")
+    res["setup_s"] = round(t_gen, 1)
     return res
 
 
@@ -506,6 +567,19 @@ def run_serve(args, local_rank):
         results, _ = ctx.serve(reqs, slots=args.serve_slots, realtime=True)
         clocks = clk.stop()
         r1 = ctx.residency_stats()
+        # the same stream served in steps, each step's frames composited by
+        # one launch (a fresh draw of the same arrival process)
+        breqs = serve_requests(rng, scenes, sids, int(args.serve_seconds * args.serve_rate),
+                               args.serve_rate)
+        bres, _ = ctx.serve(breqs, realtime=True, batch=args.serve_batch)
+    bok = [r for r in bres if r["status"] == 0]
+    blat = np.array([r["latency_s"] for r in bok]) * 1e3
+    bt_end = max(r["finish_s"] for r in bres)
+    batched = {"batch": args.serve_batch, "requests": len(breqs), "completed": len(bok),
+               "throughput_rps": round(len(bok) / bt_end, 2),
+               "p50_ms": round(float(np.percentile(blat, 50)), 3) if blat.size else None,
+               "p99_ms": round(float(np.percentile(blat, 99)), 3) if blat.size else None,
+               "mean_frames_per_step": round(len(bok) / max(sum(1 for r in bok if r["slot"] == 0), 1), 2)}
     ok = [r for r in results if r["status"] == 0]
     lat = np.array([r["latency_s"] for r in ok]) * 1e3
     t_end = max(r["finish_s"] for r in results)
@@ -528,6 +602,7 @@ def run_serve(args, local_rank):
                       "evictions": r1["block_evictions"] - r0["block_evictions"],
                       "upload_gb": round((r1["upload_bytes"] - r0["upload_bytes"]) / 1e9, 2),
                       "hbm_used_gb": round(r1["hbm_used"] / (1 << 30), 2)},
+        "batched_steps": batched,
         "clocks": clocks, "setup_s": {"generate": round(t_gen, 1), "load": round(t_load, 1)},
         "workload": "4 streamed outdoor LOD scenes (4 levels, constant density, 16x16 chunks), "
                     "Poisson arrivals, uniform scene, random street-height pose, resolution "

@@ -230,6 +230,18 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
                           int32_t save_for_backward, int64_t* handle_out,
                           lodge_frame_stats* stats);
 
+/* Render n frames (1..64) of any scenes, modes and sizes as one batch:
+ * each frame runs its stages up to the tile ranges on its own scratch, then
+ * a single launch composites the tiles of all frames (the step of the
+ * serving loop).  scene_ids, modes, cams: host arrays of n; d_rgb: host
+ * array of n DEVICE image pointers (H x W x 3 each, caller-owned).  stats
+ * and statuses (host, optional) receive per-frame counters and outcomes.
+ * Images equal lodge_render's.  Synchronous on stream.  Returns
+ * LODGE_E_INVALID if any frame failed (its status says why). */
+lodge_status lodge_render_batch(lodge_ctx* ctx, int32_t n, const int32_t* scene_ids,
+                                const int32_t* modes, const lodge_camera* cams, float* const* d_rgb,
+                                void* stream, lodge_frame_stats* stats, int32_t* statuses);
+
 /* Same as lodge_render but cameras and the image live in HOST memory: the
  * call copies the image back (device -> host) before returning.  h_rgb:
  * n_cams images, H x W x 3 float32 each.  Intended for callers that do not
@@ -369,16 +381,26 @@ typedef struct {
     float* h_images;       /* optional host buffer: the images back to back in
                               request order (H x W x 3 each) */
     double wait_limit_s;   /* how long a request may wait for HBM (0: 10 s) */
+    int32_t batch;         /* 0: slot workers as above; B > 0: steps - each step
+                              takes the requests that have arrived (at most B, in
+                              arrival order), runs their stages up to the tile
+                              ranges and composites all of them with one launch */
+    int32_t pad_;
 } lodge_serve_opts;
 
 /* Serve n requests with continuous batching (the serving loop built around
  * the paper's renderer: chunk residency, sort buffers and images stay on the
- * device).  Each slot is a worker with its own stream and scratch; requests
- * are admitted in arrival order as slots free up and as their memory fits the
- * HBM budget, and their work overlaps on the device.  results[i] (host)
- * receives request i's times, status and frame counters; latency =
- * finish_s - arrival_s.  Returns LODGE_E_INVALID if any request failed (its
- * own status says why); the other requests still complete. */
+ * device).  With opts->batch = 0, each slot is a worker with its own stream
+ * and scratch; requests are admitted in arrival order as slots free up and
+ * as their memory fits the HBM budget, and their work overlaps on the
+ * device.  With opts->batch > 0, the loop runs in steps: every request that
+ * has arrived when a step starts joins it (up to batch), and one launch
+ * composites all of the step's frames; requests arriving meanwhile join the
+ * next step, and a request whose memory does not fit waits for a later step
+ * (up to wait_limit_s).  results[i] (host) receives request i's times, status
+ * and frame counters (slot = its place in the step in batch mode); latency
+ * = finish_s - arrival_s.  Returns LODGE_E_INVALID if any request failed
+ * (its own status says why); the other requests still complete. */
 lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, int32_t n,
                          const lodge_serve_opts* opts, lodge_request_result* results);
 

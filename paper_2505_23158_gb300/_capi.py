@@ -80,7 +80,7 @@ class lodge_request_result(C.Structure):
 
 class lodge_serve_opts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("realtime", C.c_int32), ("h_images", C.c_void_p),
-                ("wait_limit_s", C.c_double)]
+                ("wait_limit_s", C.c_double), ("batch", C.c_int32), ("pad_", C.c_int32)]
 
 
 class lodge_residency(C.Structure):
@@ -103,6 +103,7 @@ _SIGS = {
     "lodge_kmeans_centers": [P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P],
     "lodge_importance": [P, C.c_int32, C.c_int, C.c_int32, P, C.c_int32, P, P],
     "lodge_render_lod": [P, C.c_int32, P, C.c_int32, P, P, P, P],
+    "lodge_render_batch": [P, C.c_int32, P, P, P, P, P, P, P],
     "lodge_filter_chunk": [P, C.c_int32, C.c_int32, P, C.c_float, C.POINTER(C.c_int64), P],
     "lodge_render": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int32,
                      C.POINTER(C.c_int64), P],

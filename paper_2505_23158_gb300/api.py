@@ -218,6 +218,21 @@ class Lodge:
         res = (imgs[0] if single else imgs, stats[0] if single else stats)
         return res + (h.value,) if save else res
 
+    def render_batch(self, frames, stream=None):
+        """frames: list of (scene_id, mode, camera), composited by one launch.
+        Returns (images, stats)."""
+        n = len(frames)
+        sids = (C.c_int32 * n)(*[int(f[0]) for f in frames])
+        modes = (C.c_int32 * n)(*[int(f[1]) for f in frames])
+        cams = camera_array([f[2] for f in frames])
+        outs = [torch.empty(f[2].height, f[2].width, 3, dtype=torch.float32,
+                            device=f"cuda:{self.device}") for f in frames]
+        ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        st = (A.lodge_frame_stats * n)()
+        status = (C.c_int32 * n)()
+        A.call("lodge_render_batch", self._h, n, sids, modes, cams, ptrs, _stream(stream), st, status)
+        return outs, [stats_dict(s) for s in st]
+
     def render_host(self, sid: int, mode: int, cams, out: np.ndarray, stream=None):
         cl = list(cams)
         st = (A.lodge_frame_stats * len(cl))()
@@ -286,10 +301,12 @@ class Lodge:
 
     # -- serving and residency
     def serve(self, requests, slots: int = 4, realtime: bool = True, images: bool = False,
-              wait_limit_s: float = 10.0):
-        """requests: list of (scene_id, mode, camera, arrival_s).  Returns
-        (results list of dicts, images list or None).  Raises LodgeError only
-        for invalid arguments; per-request failures are in each result."""
+              wait_limit_s: float = 10.0, batch: int = 0):
+        """requests: list of (scene_id, mode, camera, arrival_s).  batch > 0
+        serves in steps composited by one launch each (at most batch frames).
+        Returns (results list of dicts, images list or None).  Raises
+        LodgeError only for invalid arguments; per-request failures are in
+        each result."""
         n = len(requests)
         arr = (A.lodge_request * max(n, 1))()
         for i, (sid, mode, cam, t) in enumerate(requests):
@@ -302,6 +319,7 @@ class Lodge:
         opts.slots = int(slots)
         opts.realtime = int(realtime)
         opts.wait_limit_s = float(wait_limit_s)
+        opts.batch = int(batch)
         host = None
         if images:
             total = sum(c.width * c.height * 3 for _, _, c, _ in requests)

@@ -265,6 +265,30 @@ struct BlendOut {
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s);
+// Everything one frame's compositing reads and writes; a batch of frames is
+// composited by one launch over all their tiles (at most kMaxBlendBatch).
+struct BlendFrame {
+    int32_t width, height, tiles_x, ntiles;
+    uint32_t tile_base;        // first tile of this frame in a batch launch
+    uint32_t vmask, n_keys, n_rec;
+    const uint2* ranges;
+    const uint32_t* tile_val;
+    const float4* rec_a;
+    const float4* rec_b;
+    const float* rec_c;
+    float* rgb;
+    float* T_final;
+    uint32_t* last;
+};
+constexpr int kMaxBlendBatch = 64;
+struct BlendBatch {
+    int32_t n;
+    BlendFrame f[kMaxBlendBatch];
+};
+BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
+                       int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                       int64_t n_rec, const BlendOut& o);
+void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s);
 
 // K12: importance score: the blend's walk, and per record the largest
 // weight T * alpha it receives (rec_score, n_rec words, zeroed, FP32 bits),

@@ -103,6 +103,7 @@ enum : int {
 struct Slot {
     int index = 0;
     cudaStream_t own = nullptr;   // stream created for this slot (request loop)
+    cudaEvent_t fence = nullptr;  // orders slot 1's stream against the caller's
     Workspace ws;
     uint32_t* d_small = nullptr;
     uint32_t* h_small = nullptr;  // pinned
@@ -119,6 +120,18 @@ struct Slot {
     int64_t un = 0;
     DBuf ulist;
     Block* held[2] = {nullptr, nullptr};
+    // unions of recent chunk pairs of resident scenes, least recently used
+    // replaced first (a camera moving inside a cell alternates between a few
+    // pairs)
+    struct UnionEntry {
+        int scene = -1, a = -1, b = -1;
+        int64_t n = 0;
+        uint64_t used = 0;
+        DBuf list;
+    };
+    static constexpr int kUnionCache = 16;
+    UnionEntry ucache[kUnionCache];
+    uint64_t utick = 0;
 };
 
 struct ResidencyStats {
@@ -162,6 +175,18 @@ bool make_room(lodge_ctx* ctx, size_t bytes);
 lodge_status sync_slot(lodge_ctx* ctx, Slot& sl, cudaStream_t s);
 const char* last_error();
 lodge_status create_slot(lodge_ctx* ctx, Slot** out);
+lodge_status second_slot(lodge_ctx* ctx, Slot** out);
+
+// a batch of frames composited by one launch (lodge_capi.cu)
+struct BatchItem {
+    Scene* sc = nullptr;
+    lodge_mode mode = LODGE_FULL;
+    lodge_camera cam{};
+    float* d_rgb = nullptr;
+    lodge_frame_stats* st = nullptr;
+    lodge_status status = LODGE_OK;
+};
+lodge_status render_batch(lodge_ctx* ctx, BatchItem* items, int n, int first, cudaStream_t s);
 
 // residency (residency.cu)
 lodge_status acquire_block(lodge_ctx* ctx, Slot& sl, Scene* sc, int chunk, cudaStream_t s,

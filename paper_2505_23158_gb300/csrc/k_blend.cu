@@ -42,16 +42,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-__global__ void __launch_bounds__(kBlendThreads)
-blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __restrict__ ranges,
-             const uint32_t* __restrict__ tile_val, uint32_t vmask, uint32_t n_keys, uint32_t n_rec,
-             const float4* __restrict__ rec_a,
-             const float4* __restrict__ rec_b, const float* __restrict__ rec_c,
-             float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_last) {
+__device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     __shared__ float4 sa[2][kBlendBatch];
     __shared__ float4 sb[2][kBlendBatch];
     __shared__ float sc[2][kBlendBatch];
-    const int tile = blockIdx.x;
+    const int32_t width = f.width, height = f.height, tiles_x = f.tiles_x;
+    const uint2* __restrict__ ranges = f.ranges;
+    const uint32_t* __restrict__ tile_val = f.tile_val;
+    const uint32_t vmask = f.vmask, n_keys = f.n_keys, n_rec = f.n_rec;
+    const float4* __restrict__ rec_a = f.rec_a;
+    const float4* __restrict__ rec_b = f.rec_b;
+    const float* __restrict__ rec_c = f.rec_c;
+    float* __restrict__ out_rgb = f.rgb;
+    float* __restrict__ out_T = f.T_final;
+    uint32_t* __restrict__ out_last = f.last;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // warp w covers the 8x8 block (w & 1, w >> 1) of the tile; a lane owns
@@ -162,6 +166,20 @@ blend_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __rest
     }
 }
 
+__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) { blend_tile(f, blockIdx.x); }
+
+// One launch for the tiles of several frames (a serving step): CTA b
+// composites tile b - tile_base of the last frame whose tile_base <= b.
+__global__ void __launch_bounds__(kBlendThreads) blend_batch_kernel(BlendBatch bb) {
+    const uint32_t b = blockIdx.x;
+    int lo = 0, hi = bb.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bb.f[mid].tile_base <= b) lo = mid; else hi = mid - 1;
+    }
+    blend_tile(bb.f[lo], (int)(b - bb.f[lo].tile_base));
+}
+
 
 // K12: importance score (Sec. 3 "Importance pruning" / "Visibility
 // filtering", after RadSplat): the same per-pixel walk as blend_kernel (same
@@ -255,14 +273,50 @@ __global__ void record_score_to_gid_kernel(const uint32_t* __restrict__ rec_scor
 }
 }  // namespace
 
+BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
+                       int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
+                       int64_t n_rec, const BlendOut& o) {
+    BlendFrame f;
+    f.width = cam.width;
+    f.height = cam.height;
+    f.tiles_x = cam.tiles_x;
+    f.ntiles = cam.tiles_x * cam.tiles_y;
+    f.tile_base = 0;
+    f.vmask = vmask;
+    f.n_keys = (uint32_t)n_keys;
+    f.n_rec = (uint32_t)std::max<int64_t>(n_rec, 1);
+    f.ranges = ranges;
+    f.tile_val = tile_val;
+    f.rec_a = rec_a;
+    f.rec_b = rec_b;
+    f.rec_c = rec_c;
+    f.rgb = o.rgb;
+    f.T_final = o.T_final;
+    f.last = o.last;
+    return f;
+}
+
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s) {
-    int ntiles = cam.tiles_x * cam.tiles_y;
-    if (ntiles == 0) return;
-    blend_kernel<<<ntiles, kBlendThreads, 0, s>>>(cam.width, cam.height, cam.tiles_x, ranges, tile_val, vmask,
-                                        (uint32_t)n_keys, (uint32_t)std::max<int64_t>(n_rec, 1),
-                                        rec_a, rec_b, rec_c, o.rgb, o.T_final, o.last);
+    const BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o);
+    if (f.ntiles == 0) return;
+    blend_kernel<<<f.ntiles, kBlendThreads, 0, s>>>(f);
+}
+
+void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s) {
+    BlendBatch bb;
+    uint32_t base = 0;
+    bb.n = 0;
+    for (int i = 0; i < n && i < kMaxBlendBatch; ++i) {
+        if (frames[i].ntiles == 0) continue;
+        bb.f[bb.n] = frames[i];
+        bb.f[bb.n].tile_base = base;
+        base += (uint32_t)frames[i].ntiles;
+        ++bb.n;
+    }
+    if (bb.n == 0) return;
+    blend_batch_kernel<<<base, kBlendThreads, 0, s>>>(bb);
 }
 
 void launch_importance(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,

@@ -159,6 +159,21 @@ static void prof_collect(Slot& sl) {
     }
 }
 
+// Slot 1 with its own stream and fence event (created on first use; the
+// request loop and batches reuse it as their first slot).
+lodge_status second_slot(lodge_ctx* ctx, Slot** out) {
+    while (ctx->slots.size() < 2) {
+        Slot* sl = nullptr;
+        TRY(create_slot(ctx, &sl));
+    }
+    Slot* sl = ctx->slots[1].get();
+    if (!sl->own) CUDA_TRY(cudaStreamCreateWithFlags(&sl->own, cudaStreamNonBlocking));
+    if (!sl->fence) CUDA_TRY(cudaEventCreateWithFlags(&sl->fence, cudaEventDisableTiming));
+    sl->prof_on = ctx->slots[0]->prof_on;
+    *out = sl;
+    return LODGE_OK;
+}
+
 lodge_status create_slot(lodge_ctx* ctx, Slot** out) {
     std::unique_ptr<Slot> sl(new Slot());
     {
@@ -183,6 +198,8 @@ static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
     for (DBuf* b : sl.ws.all())
         if (b->p) cudaFree(b->p);
     if (sl.ulist.p) cudaFree(sl.ulist.p);
+    for (auto& u : sl.ucache)
+        if (u.list.p) cudaFree(u.list.p);
     if (sl.d_small) cudaFree(sl.d_small);
     if (sl.h_small) cudaFreeHost(sl.h_small);
     if (sl.h_tail) cudaFreeHost(sl.h_tail);
@@ -191,6 +208,7 @@ static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
         if (sl.ev_end[k]) cudaEventDestroy(sl.ev_end[k]);
     }
     if (sl.own) cudaStreamDestroy(sl.own);
+    if (sl.fence) cudaEventDestroy(sl.fence);
     (void)ctx;
 }
 
@@ -419,32 +437,39 @@ static lodge_status select_active(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mod
         if (mode == LODGE_CHUNK) { act->B = -1; act->tA = act->tB = 1.0; }
         return LODGE_OK;
     }
-    if (sl.u_scene != sc->id || sl.ua != act->A || sl.ub != act->B) {
+    Slot::UnionEntry* ue = nullptr;
+    for (auto& u : sl.ucache)
+        if (u.scene == sc->id && u.a == act->A && u.b == act->B) ue = &u;
+    if (!ue) {
+        ue = &sl.ucache[0];
+        for (auto& u : sl.ucache)
+            if (u.used < ue->used) ue = &u;
+        ue->scene = -1;
         const Chunk& a = sc->chunks[act->A];
         const Chunk& b = sc->chunks[act->B];
         Workspace& ws = sl.ws;
         int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
-        TRY(ensure(ctx, sl.ulist, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
+        TRY(ensure(ctx, ue->list, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
         TRY(ensure(ctx, ws.marks, (size_t)((sc->dev.n_total + 63) / 64 * 64), s));
         TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
         CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
         CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
         prof_begin(sl, LODGE_STAGE_UNION, s);
         launch_chunk_union(a.list, a.n, b.list, b.n, sc->dev.n_total, ws.marks.as<uint8_t>(),
-                           sl.ulist.as<uint32_t>(), sl.d_small + kSmListCount,
+                           ue->list.as<uint32_t>(), sl.d_small + kSmListCount,
                            ws.status.as<uint32_t>(), sl.d_small + kSmCtrUnion,
                            sl.d_small + kSmErr, s);
         prof_end(sl, LODGE_STAGE_UNION, s, (a.n > 0) + (b.n > 0) + (ntiles > 0));
         CUDA_TRY(cudaGetLastError());
-        sl.u_scene = -1;
         TRY(sync_slot(ctx, sl, s));
-        sl.un = sl.h_small[kSmListCount];
-        sl.u_scene = sc->id;
-        sl.ua = act->A;
-        sl.ub = act->B;
+        ue->n = sl.h_small[kSmListCount];
+        ue->scene = sc->id;
+        ue->a = act->A;
+        ue->b = act->B;
     }
-    act->list = sl.ulist.as<uint32_t>();
-    act->n = sl.un;
+    ue->used = ++sl.utick;
+    act->list = ue->list.as<uint32_t>();
+    act->n = ue->n;
     return LODGE_OK;
 }
 
@@ -458,9 +483,12 @@ static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
 // are checked at the slot's next sync.
 // importance != null: composite with K12 instead of K7 and raise
 // importance[gid] (n_total floats) to each Gaussian's largest weight.
+// job != null: stop before compositing and describe it in *job (the caller
+// composites a batch of frames with one launch and then syncs their slots).
 static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, const Active& act,
                                  const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
-                                 lodge_frame_stats* st, bool end_sync, float* importance = nullptr) {
+                                 lodge_frame_stats* st, bool end_sync, float* importance = nullptr,
+                                 BlendFrame* job = nullptr) {
     Workspace& ws = sl.ws;
     TRY(check_cam(c));
     DevCamera cam = make_cam(c);
@@ -578,8 +606,15 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         bo.T_final = ws.T.as<float>();
         bo.last = ws.last.as<uint32_t>();
     }
+    if (job) {
+        *job = blend_frame(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
+                           ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo);
+        end_sync = false;
+    }
     prof_begin(sl, LODGE_STAGE_BLEND, s);
-    if (importance) {
+    if (job) {
+        // composited later by the batch launch
+    } else if (importance) {
         TRY(ensure(ctx, ws.iscore, sizeof(uint32_t) * nv1, s));
         CUDA_TRY(cudaMemsetAsync(ws.iscore.p, 0, sizeof(uint32_t) * nv1, s));
         launch_importance(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
@@ -589,9 +624,11 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
                      ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
     }
-    prof_end(sl, LODGE_STAGE_BLEND, s, ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
+    prof_end(sl, LODGE_STAGE_BLEND, s, job ? 0 : ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
     CUDA_TRY(cudaGetLastError());
-    if (end_sync || save) {
+    if (job) {
+        // the caller syncs after the batch launch
+    } else if (end_sync || save) {
         TRY(sync_slot(ctx, sl, s));
     } else {
         CUDA_TRY(cudaMemcpyAsync(sl.h_tail, sl.d_small, sizeof(uint32_t) * kSmWords,
@@ -651,6 +688,47 @@ lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
         release_blocks(ctx, sl);
     }
     return r;
+}
+
+// A batch of frames (any scenes, modes and sizes) on slots first .. first+n-1
+// of one stream: each frame runs its own stages up to the tile ranges on its
+// slot's scratch, then one launch composites the tiles of all of them.
+// items[k].status receives each frame's outcome.
+lodge_status render_batch(lodge_ctx* ctx, BatchItem* items, int n, int first, cudaStream_t s) {
+    if (n < 1 || n > kMaxBlendBatch) return fail(LODGE_E_INVALID, "batch of %d frames (1..%d)", n, kMaxBlendBatch);
+    while ((int)ctx->slots.size() < first + n) {
+        Slot* sl = nullptr;
+        TRY(create_slot(ctx, &sl));
+    }
+    std::vector<BlendFrame> jobs;
+    std::vector<int> ok;
+    for (int k = 0; k < n; ++k) {
+        BatchItem& it = items[k];
+        Slot& sl = *ctx->slots[first + k];
+        Active act;
+        BlendFrame job;
+        lodge_status r = select_active(ctx, sl, it.sc, it.mode, it.cam, s, &act);
+        if (r == LODGE_OK)
+            r = render_frame(ctx, sl, it.sc->dev, act, it.cam, it.d_rgb, s, nullptr, it.st, false, nullptr,
+                             &job);
+        it.status = r;
+        if (r == LODGE_OK) {
+            jobs.push_back(job);
+            ok.push_back(k);
+        } else if (it.sc->residency == kStreamed) {
+            cudaStreamSynchronize(s);
+            release_blocks(ctx, sl);
+        }
+    }
+    if (!jobs.empty()) launch_blend_batch(jobs.data(), (int)jobs.size(), s);
+    const cudaError_t e = cudaGetLastError();
+    for (int k : ok) {
+        Slot& sl = *ctx->slots[first + k];
+        lodge_status r = e == cudaSuccess ? sync_slot(ctx, sl, s) : fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e));
+        items[k].status = r;
+        if (items[k].sc->residency == kStreamed) release_blocks(ctx, sl);
+    }
+    return LODGE_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1042,8 +1120,11 @@ lodge_status lodge_unload_scene(lodge_ctx* ctx, int32_t scene_id) {
     CUDA_TRY(cudaSetDevice(ctx->device));
     CUDA_TRY(cudaDeviceSynchronize());
     free_scene(ctx, *sc);
-    for (auto& sl : ctx->slots)
+    for (auto& sl : ctx->slots) {
         if (sl->u_scene == scene_id) sl->u_scene = -1;
+        for (auto& u : sl->ucache)
+            if (u.scene == scene_id) u.scene = -1;
+    }
     CUDA_TRY(cudaDeviceSynchronize());
     ctx->scenes[scene_id].reset();
     return LODGE_OK;
@@ -1216,18 +1297,38 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Slot& sl = *ctx->slots[0];
+    Slot& sl0 = *ctx->slots[0];
+    // Several frames of a resident scene alternate between two slots, the
+    // second on its own stream: while the host waits for one frame's counts,
+    // the device runs the other frame's stages.  The second stream starts
+    // after the work already queued on the caller's stream and the caller's
+    // stream ends after all of it.
+    Slot* sl1 = nullptr;
+    cudaStream_t s1 = nullptr;
+    if (n_cams > 1 && !save_for_backward && sc->residency == kResident) {
+        TRY(second_slot(ctx, &sl1));
+        s1 = sl1->own;
+        CUDA_TRY(cudaEventRecord(sl1->fence, s));
+        CUDA_TRY(cudaStreamWaitEvent(s1, sl1->fence, 0));
+    }
     size_t off = 0;
     for (int i = 0; i < n_cams; ++i) {
         std::unique_ptr<Saved> sv;
         if (save_for_backward) sv.reset(new Saved());
+        Slot& sl = (sl1 && (i & 1)) ? *sl1 : sl0;
+        cudaStream_t si = (sl1 && (i & 1)) ? s1 : s;
         // consecutive frames of one call are not waited for one by one: the
         // host prepares frame i + 1 while frame i's last kernels run
-        const bool last = i + 1 == n_cams;
-        lodge_status r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, s, sv.get(),
+        const bool last = sl1 ? i + 2 >= n_cams : i + 1 == n_cams;
+        lodge_status r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, si, sv.get(),
                                     stats ? stats + i : nullptr, last, nullptr);
         if (r != LODGE_OK) {
-            if (sl.tail_pending) { cudaStreamSynchronize(s); sl.tail_pending = false; }
+            for (Slot* q : {&sl0, sl1}) {
+                if (q && q->tail_pending) {
+                    cudaStreamSynchronize(q == &sl0 ? s : s1);
+                    q->tail_pending = false;
+                }
+            }
             return r;
         }
         off += (size_t)cams[i].width * cams[i].height * 3;
@@ -1238,6 +1339,38 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
             *handle_out = h;
         }
     }
+    if (sl1) {   // the caller's stream ends after the second stream's frames
+        CUDA_TRY(cudaEventRecord(sl1->fence, s1));
+        CUDA_TRY(cudaStreamWaitEvent(s, sl1->fence, 0));
+    }
+    return LODGE_OK;
+}
+
+lodge_status lodge_render_batch(lodge_ctx* ctx, int32_t n, const int32_t* scene_ids, const int32_t* modes,
+                                const lodge_camera* cams, float* const* d_rgb, void* stream,
+                                lodge_frame_stats* stats, int32_t* statuses) {
+    if (!ctx || n < 1 || !scene_ids || !modes || !cams || !d_rgb) return fail(LODGE_E_INVALID, "bad argument");
+    if (n > kMaxBlendBatch) return fail(LODGE_E_INVALID, "at most %d frames per batch", kMaxBlendBatch);
+    std::vector<BatchItem> items((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        Scene* sc = get_scene(ctx, scene_ids[k]);
+        if (!sc) return fail(LODGE_E_INVALID, "frame %d names no scene", k);
+        if (!d_rgb[k]) return fail(LODGE_E_INVALID, "frame %d has no image buffer", k);
+        items[k].sc = sc;
+        items[k].mode = (lodge_mode)modes[k];
+        items[k].cam = cams[k];
+        items[k].d_rgb = d_rgb[k];
+        items[k].st = stats ? stats + k : nullptr;
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    // batch frames use slots 1..n (slot 0 serves the single-frame calls)
+    TRY(render_batch(ctx, items.data(), n, 1, static_cast<cudaStream_t>(stream)));
+    int failed = 0;
+    for (int k = 0; k < n; ++k) {
+        if (statuses) statuses[k] = items[k].status;
+        failed += items[k].status != LODGE_OK;
+    }
+    if (failed) return fail(LODGE_E_INVALID, "%d of %d frames failed (see their status)", failed, n);
     return LODGE_OK;
 }
 
@@ -1369,7 +1502,11 @@ lodge_status lodge_filter_chunk(lodge_ctx* ctx, int32_t scene_id, int32_t chunk,
     ch.list = static_cast<uint32_t*>(p);
     ch.n = kept;
     // cached unions may hold the old set
-    for (auto& slp : ctx->slots) slp->u_scene = -1;
+    for (auto& slp : ctx->slots) {
+        slp->u_scene = -1;
+        for (auto& u : slp->ucache)
+            if (u.scene == scene_id) u.scene = -1;
+    }
     if (n_kept) *n_kept = kept;
     return LODGE_OK;
 }
@@ -1551,16 +1688,33 @@ lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals
 
 lodge_status lodge_profile_enable(lodge_ctx* ctx, int enable) {
     if (!ctx) return fail(LODGE_E_INVALID, "NULL context");
-    Slot& sl = *ctx->slots[0];
-    sl.prof = lodge_profile{};
-    for (int k = 0; k < LODGE_NUM_STAGES; ++k) sl.ev_pending[k] = false;
-    sl.prof_on = enable != 0;
+    for (auto& slp : ctx->slots) {
+        Slot& sl = *slp;
+        sl.prof = lodge_profile{};
+        for (int k = 0; k < LODGE_NUM_STAGES; ++k) sl.ev_pending[k] = false;
+        sl.prof_on = enable != 0;
+    }
     return LODGE_OK;
 }
 
+// the sum over the context's slots (frames of one call may alternate
+// between two)
 lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
     if (!ctx || !out) return fail(LODGE_E_INVALID, "bad argument");
-    *out = ctx->slots[0]->prof;
+    lodge_profile p{};
+    for (auto& slp : ctx->slots) {
+        const lodge_profile& q = slp->prof;
+        for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
+            p.ms[k] += q.ms[k];
+            p.launches[k] += q.launches[k];
+        }
+        p.frames += q.frames;
+        p.keys += q.keys;
+        p.visible += q.visible;
+        p.active += q.active;
+        p.packed_keys += q.packed_keys;
+    }
+    *out = p;
     return LODGE_OK;
 }
 

@@ -157,3 +157,50 @@ def test_budget_too_small_fails_cleanly(env, scene_cams):
         assert results[0]["status"] == 6
         # the context is still usable
         assert ctx.residency_stats()["hbm_used"] <= budget
+
+
+def test_batch_render_equals_single(env, scene_cams):
+    """One compositing launch for frames of different scenes, modes and sizes
+    gives the images of rendering each frame alone, bit for bit."""
+    torch, api = env
+    scene, cams = scene_cams
+    plain, pcams = synth.workload_plain(0)
+    with api.Lodge(0) as ctx:
+        r = ctx.load_scene(scene, api.RESIDENT)
+        s = ctx.load_scene(scene, api.STREAMED)
+        p = ctx.load_scene(plain, api.RESIDENT)
+        frames = []
+        for i in range(12):
+            c = cams[(5 * i) % len(cams)]
+            w, h = [(320, 180), (160, 90), (256, 144)][i % 3]
+            cam = synth.look_at(c.center, c.R[2].astype(np.float64), (0, 0, 1), w, h, 70.0)
+            sid, mode = [(r, api.CHUNK_BLEND), (s, api.CHUNK), (r, api.LOD), (s, api.CHUNK_BLEND)][i % 4]
+            frames.append((sid, mode, cam))
+        frames.append((p, api.FULL, pcams[0]))
+        imgs, stats = ctx.render_batch(frames)
+        for (sid, mode, cam), img, st in zip(frames, imgs, stats):
+            alone, st1 = ctx.render(sid, mode, cam)
+            assert torch.equal(alone, img)
+            assert st1["n_keys"] == st["n_keys"] and st1["n_visible"] == st["n_visible"]
+
+
+def test_serve_batched_steps_equal_alone(env, scene_cams):
+    """The serving loop in step mode (each step's frames composited by one
+    launch): every image equals the same request rendered alone."""
+    torch, api = env
+    scene, cams = scene_cams
+    with api.Lodge(0) as ctx:
+        s = ctx.load_scene(scene, api.STREAMED)
+        reqs = []
+        for i in range(24):
+            w, h = [(320, 180), (160, 90), (96, 64)][i % 3]
+            c = cams[(7 * i) % len(cams)]
+            cam = synth.look_at(c.center, c.R[2].astype(np.float64), (0, 0, 1), w, h, 70.0)
+            reqs.append((s, api.CHUNK_BLEND if i % 2 else api.CHUNK, cam, 0.001 * i))
+        # all requests are there at once (not realtime): steps of 8 frames
+        results, imgs = ctx.serve(reqs, realtime=False, images=True, batch=8)
+        assert all(r["status"] == 0 for r in results), [r["status"] for r in results]
+        assert max(r["slot"] for r in results) == 7          # full steps of 8 frames
+        for (sid, mode, cam, _), img in zip(reqs, imgs):
+            alone, _ = _render(ctx, sid, mode, cam)
+            assert np.array_equal(alone, img)
