@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -58,7 +59,15 @@ struct Scene {
     std::vector<double> radius;
     std::vector<Chunk> chunks;
     size_t chunk_bytes = 0;
+    // resident scenes: unions of chunk pairs met so far, shared by every slot
+    // (computed once and kept while the chunk sets stay as they are)
+    struct PairUnion {
+        DBuf list;
+        int64_t n = 0;
+    };
+    std::unordered_map<uint64_t, PairUnion> unions;
 };
+constexpr size_t kMaxPairUnions = 1024;   // per scene; beyond, slots cache their own
 
 struct Saved {
     DevCamera cam{};

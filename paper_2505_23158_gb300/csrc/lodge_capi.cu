@@ -409,6 +409,31 @@ static lodge_status select_streamed(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_m
     return LODGE_OK;
 }
 
+// Union of chunk sets A and B of a resident scene into `out` (gid
+// ascending, bit 31 / 30 = member of A / B); waits for the count.  The union
+// is complete on the device when this returns.
+static lodge_status compute_union(lodge_ctx* ctx, Slot& sl, Scene* sc, int A, int B, cudaStream_t s,
+                                  DBuf& out, int64_t* n) {
+    const Chunk& a = sc->chunks[A];
+    const Chunk& b = sc->chunks[B];
+    Workspace& ws = sl.ws;
+    int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
+    TRY(ensure(ctx, out, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
+    TRY(ensure(ctx, ws.marks, (size_t)((sc->dev.n_total + 63) / 64 * 64), s));
+    TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
+    CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
+    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    prof_begin(sl, LODGE_STAGE_UNION, s);
+    launch_chunk_union(a.list, a.n, b.list, b.n, sc->dev.n_total, ws.marks.as<uint8_t>(),
+                       out.as<uint32_t>(), sl.d_small + kSmListCount, ws.status.as<uint32_t>(),
+                       sl.d_small + kSmCtrUnion, sl.d_small + kSmErr, s);
+    prof_end(sl, LODGE_STAGE_UNION, s, (a.n > 0) + (b.n > 0) + (ntiles > 0));
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_slot(ctx, sl, s));
+    *n = sl.h_small[kSmListCount];
+    return LODGE_OK;
+}
+
 static lodge_status select_active(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
                                   const lodge_camera& cam, cudaStream_t s, Active* act) {
     *act = Active{};
@@ -437,6 +462,27 @@ static lodge_status select_active(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mod
         if (mode == LODGE_CHUNK) { act->B = -1; act->tA = act->tB = 1.0; }
         return LODGE_OK;
     }
+    // the pair's union: shared by all slots once computed, else this slot's cache
+    const uint64_t key = ((uint64_t)(uint32_t)act->A << 32) | (uint32_t)act->B;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        auto it = sc->unions.find(key);
+        if (it == sc->unions.end() && sc->unions.size() < kMaxPairUnions) {
+            Scene::PairUnion pu;
+            lodge_status r = compute_union(ctx, sl, sc, act->A, act->B, s, pu.list, &pu.n);
+            if (r == LODGE_OK) {
+                it = sc->unions.emplace(key, pu).first;
+            } else {
+                release(ctx, pu.list, s);
+                if (r != LODGE_E_BUDGET) return r;   // out of budget: a slot's cache below
+            }
+        }
+        if (it != sc->unions.end()) {
+            act->list = it->second.list.as<uint32_t>();
+            act->n = it->second.n;
+            return LODGE_OK;
+        }
+    }
     Slot::UnionEntry* ue = nullptr;
     for (auto& u : sl.ucache)
         if (u.scene == sc->id && u.a == act->A && u.b == act->B) ue = &u;
@@ -445,24 +491,7 @@ static lodge_status select_active(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mod
         for (auto& u : sl.ucache)
             if (u.used < ue->used) ue = &u;
         ue->scene = -1;
-        const Chunk& a = sc->chunks[act->A];
-        const Chunk& b = sc->chunks[act->B];
-        Workspace& ws = sl.ws;
-        int64_t ntiles = (sc->dev.n_total + kSelectTile - 1) / kSelectTile;
-        TRY(ensure(ctx, ue->list, sizeof(uint32_t) * (size_t)std::max<int64_t>(a.n + b.n, 1), s));
-        TRY(ensure(ctx, ws.marks, (size_t)((sc->dev.n_total + 63) / 64 * 64), s));
-        TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
-        CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1), s));
-        CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
-        prof_begin(sl, LODGE_STAGE_UNION, s);
-        launch_chunk_union(a.list, a.n, b.list, b.n, sc->dev.n_total, ws.marks.as<uint8_t>(),
-                           ue->list.as<uint32_t>(), sl.d_small + kSmListCount,
-                           ws.status.as<uint32_t>(), sl.d_small + kSmCtrUnion,
-                           sl.d_small + kSmErr, s);
-        prof_end(sl, LODGE_STAGE_UNION, s, (a.n > 0) + (b.n > 0) + (ntiles > 0));
-        CUDA_TRY(cudaGetLastError());
-        TRY(sync_slot(ctx, sl, s));
-        ue->n = sl.h_small[kSmListCount];
+        TRY(compute_union(ctx, sl, sc, act->A, act->B, s, ue->list, &ue->n));
         ue->scene = sc->id;
         ue->a = act->A;
         ue->b = act->B;
@@ -913,6 +942,12 @@ static void point_store(DevScene& d, float* base, int64_t NP) {
     d.sh = f4 + 2 * NP;
 }
 
+// (callers have synchronised the device: no frame still reads the lists)
+static void free_pair_unions(lodge_ctx* ctx, Scene& sc) {
+    for (auto& kv : sc.unions) release(ctx, kv.second.list, 0);
+    sc.unions.clear();
+}
+
 static void free_scene(lodge_ctx* ctx, Scene& sc) {
     free_scene_blocks(ctx, sc.id);
     if (sc.block) dfree(ctx, sc.block, sc.block_bytes);
@@ -925,6 +960,7 @@ static void free_scene(lodge_ctx* ctx, Scene& sc) {
         for (auto& ch : sc.chunks)
             if (ch.list) dfree(ctx, ch.list, sizeof(uint32_t) * (size_t)std::max<int64_t>(ch.n, 1));
     sc.chunks.clear();
+    free_pair_unions(ctx, sc);
 }
 
 }  // namespace lodge
@@ -1502,6 +1538,8 @@ lodge_status lodge_filter_chunk(lodge_ctx* ctx, int32_t scene_id, int32_t chunk,
     ch.list = static_cast<uint32_t*>(p);
     ch.n = kept;
     // cached unions may hold the old set
+    CUDA_TRY(cudaDeviceSynchronize());
+    free_pair_unions(ctx, *sc);
     for (auto& slp : ctx->slots) {
         slp->u_scene = -1;
         for (auto& u : slp->ucache)
