@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--bin-log2", type=int, default=None,
+                    help="key lists per bin of 2^k x 2^k tiles (default: the library's)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -196,20 +198,23 @@ def stage_bytes(stage: str, prof: dict) -> float:
         # list entry + means per active Gaussian; scale/opacity, quaternion and
         # 48 SH coefficients per visible Gaussian; 56 B of records written
         return a * (4 + 12) + v * (16 + 16 + 192 + 56)
-    # keys of frames whose (tile, record) pair fits one word are written and
-    # sorted as single 4 B words; the others as a 4 B key plus a 4 B value
+    # one key per (record, bin): bins are tiles or squares of 2^k tiles.  Keys
+    # of frames whose (bin, record) pair fits one word are written and sorted
+    # as single 4 B words; the others as a 4 B key plus a 4 B value
+    bk = prof.get("bin_keys", k)
     kp = prof.get("packed_keys", 0)
     if stage == "depth_sort":
         return v * (4 + 4 * 16)          # histogram read + 4 passes of read/write key+value
     if stage == "emit":
         # offsets pass: read record id + rect, write offset, id, rect (28 B per
         # visible); key pass: stage offset/id/rect (16 B), write 4 or 8 B per key
-        return v * (28 + 16) + kp * 4 + (k - kp) * 8
+        return v * (28 + 16) + kp * 4 + (bk - kp) * 8
     if stage == "tile_sort":
-        # 13-bit tile ids: 2 passes, each reading and writing every key (and value)
-        return kp * (2 * 8) + (k - kp) * (2 * 16)
+        # every pass (8 bits of the bin id each) reads and writes every key (and value)
+        passes = prof.get("bin_sort_passes", 2 * prof["frames"]) / max(prof["frames"], 1)
+        return (kp * 8 + (bk - kp) * 16) * passes
     if stage == "ranges":
-        return k * 4
+        return bk * 4
     return 0.0
 
 
@@ -259,6 +264,8 @@ def run_lodge(args, rank, world, local_rank):
                                         height_px=args.height)
     t_gen = time.time() - t0
     ctx = Lodge(local_rank)
+    if args.bin_log2 is not None:
+        ctx.set_bin_size(args.bin_log2)
     t0 = time.time()
     sid = ctx.load_scene(scene)
     t_load = time.time() - t0
@@ -387,8 +394,8 @@ def run_lodge(args, rank, world, local_rank):
         ach = by / (ms[dom] / 1e3) / 1e9
         peak = pk["hbm_gbs"]
         nl = max(prof["launches"][dom], 1)
-        # every tile-sort pass processes all of a frame's keys
-        per_launch_units = prof["keys"] / max(prof["frames"], 1) if dom == "tile_sort" else 0
+        # every bin-sort pass processes all of a frame's bin keys
+        per_launch_units = prof["bin_keys"] / max(prof["frames"], 1) if dom == "tile_sort" else 0
         tr = measured_traffic(dom, per_launch_units)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": None if tr is None else round(tr),
@@ -423,6 +430,7 @@ def run_lodge(args, rank, world, local_rank):
         "per_frame": {"active": prof_timed["active"] // max(prof_timed["frames"], 1),
                       "visible": prof_timed["visible"] // max(prof_timed["frames"], 1),
                       "keys": prof_timed["keys"] // max(prof_timed["frames"], 1),
+                      "bin_keys": prof_timed["bin_keys"] // max(prof_timed["frames"], 1),
                       "full_active": prof_full_timed["active"] // max(prof_full_timed["frames"], 1),
                       "full_visible": prof_full_timed["visible"] // max(prof_full_timed["frames"], 1),
                       "full_keys": prof_full_timed["keys"] // max(prof_full_timed["frames"], 1)},
@@ -465,6 +473,8 @@ def run_large(args, local_rank):
     out = torch.empty(len(cams) * npix * 3, dtype=torch.float32, device=dev)
     res = {}
     with Lodge(local_rank) as ctx:
+        if args.bin_log2 is not None:
+            ctx.set_bin_size(args.bin_log2)
         sid = ctx.load_scene(scene)
         for name, mode in (("chunk_blend", CHUNK_BLEND), ("full", FULL)):
             ctx.render(sid, mode, cams, out=out)          # warm-up, grows scratch
@@ -553,6 +563,8 @@ def run_serve(args, local_rank):
     t_gen = time.time() - t0
     budget = int(args.serve_budget_gb * (1 << 30))
     with Lodge(local_rank, hbm_budget_bytes=budget) as ctx:
+        if args.bin_log2 is not None:
+            ctx.set_bin_size(args.bin_log2)
         t0 = time.time()
         sids = [ctx.load_scene(sc, STREAMED) for sc in scenes]
         t_load = time.time() - t0

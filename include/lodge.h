@@ -219,6 +219,18 @@ lodge_status lodge_kmeans_centers(const double* positions, int32_t n, int32_t k,
 
 /* ---------------------------------------------------------------- render */
 
+/* Size of the bins whose key lists the renders of this context sort and
+ * composite from: squares of 2^log2_tiles x 2^log2_tiles 16x16 tiles
+ * (0..3; the context starts at 2, 64x64 pixels).  A Gaussian is keyed once
+ * per bin its tile rect touches (Sec. 3, "Preliminaries: 3DGS", assigns it
+ * to every tile it overlaps); compositing walks the bin's list for each of
+ * the bin's tiles and skips the Gaussians whose tile rect misses the tile,
+ * so images do not depend on the setting, only the number of keys sorted
+ * does.  Frames saved for the adjoint (save_for_backward) and the
+ * importance walk always use per-tile lists (log2_tiles = 0).  Errors:
+ * LODGE_E_INVALID for a NULL ctx or log2_tiles outside 0..3. */
+lodge_status lodge_set_bin_size(lodge_ctx* ctx, int32_t log2_tiles);
+
 /* Render n_cams cameras of one scene in `mode`.  d_rgb (device,
  * caller-owned) receives n_cams images back to back, each H x W x 3 of its
  * camera.  stats (host, optional) receives n_cams frame counters.  With
@@ -430,9 +442,9 @@ typedef enum {
     LODGE_STAGE_UNION = 1,      /* K2 chunk-pair union (when the pair changes) */
     LODGE_STAGE_PROJECT = 2,    /* K3 projection + SH + compaction */
     LODGE_STAGE_DEPTH_SORT = 3, /* K5 onesweep sort by depth */
-    LODGE_STAGE_EMIT = 4,       /* K4 tile emission */
-    LODGE_STAGE_TILE_SORT = 5,  /* K5 onesweep sort by tile */
-    LODGE_STAGE_RANGES = 6,     /* K6 tile ranges */
+    LODGE_STAGE_EMIT = 4,       /* K4 bin emission */
+    LODGE_STAGE_TILE_SORT = 5,  /* K5 onesweep sort by bin */
+    LODGE_STAGE_RANGES = 6,     /* K6 bin ranges */
     LODGE_STAGE_BLEND = 7,      /* K7 compositing */
     LODGE_NUM_STAGES = 8
 } lodge_stage;
@@ -447,8 +459,11 @@ typedef struct {
     int64_t keys;      /* sum of per-frame tile keys */
     int64_t visible;   /* sum of per-frame visible Gaussians */
     int64_t active;    /* sum of per-frame active Gaussians */
-    int64_t packed_keys; /* keys of frames whose tile and record index fit one
-                          * 32-bit word: sorted as single words, no values */
+    int64_t packed_keys; /* bin keys of frames whose bin and record index fit
+                          * one 32-bit word: sorted as single words, no values */
+    int64_t bin_keys;    /* sum of per-frame keys emitted and sorted (one per
+                          * record and bin; equals keys for per-tile bins) */
+    int64_t bin_sort_passes; /* sum of per-frame passes of the bin sort */
 } lodge_profile;
 
 /* Start (enable != 0, counters reset) or stop collecting the profile.

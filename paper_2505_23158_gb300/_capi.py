@@ -59,7 +59,8 @@ STAGE_NAMES = ["select", "union", "project", "depth_sort", "emit", "tile_sort", 
 class lodge_profile(C.Structure):
     _fields_ = [("ms", C.c_double * NUM_STAGES), ("launches", C.c_int64 * NUM_STAGES),
                 ("frames", C.c_int64), ("keys", C.c_int64), ("visible", C.c_int64),
-                ("active", C.c_int64), ("packed_keys", C.c_int64)]
+                ("active", C.c_int64), ("packed_keys", C.c_int64), ("bin_keys", C.c_int64),
+                ("bin_sort_passes", C.c_int64)]
 
 
 class lodge_frame_stats(C.Structure):
@@ -120,6 +121,7 @@ _SIGS = {
     "lodge_serve": [P, P, C.c_int32, C.POINTER(lodge_serve_opts), P],
     "lodge_residency_stats": [P, C.POINTER(lodge_residency)],
     "lodge_inject_upload_failures": [P, C.c_int32],
+    "lodge_set_bin_size": [P, C.c_int32],
     "lodge_profile_enable": [P, C.c_int],
     "lodge_profile_read": [P, C.POINTER(lodge_profile)],
 }

@@ -347,6 +347,11 @@ class Lodge:
         A.call("lodge_residency_stats", self._h, C.byref(r))
         return {f: getattr(r, f) for f, _ in r._fields_}
 
+    def set_bin_size(self, log2_tiles: int):
+        """Key lists per bin of 2**log2_tiles x 2**log2_tiles tiles (0..3);
+        images do not depend on it (lodge_set_bin_size)."""
+        A.call("lodge_set_bin_size", self._h, int(log2_tiles))
+
     def inject_upload_failures(self, n: int):
         A.call("lodge_inject_upload_failures", self._h, int(n))
 
@@ -359,7 +364,8 @@ class Lodge:
         return dict(ms={n: p.ms[i] for i, n in enumerate(A.STAGE_NAMES)},
                     launches={n: p.launches[i] for i, n in enumerate(A.STAGE_NAMES)},
                     frames=p.frames, keys=p.keys, visible=p.visible, active=p.active,
-                    packed_keys=p.packed_keys)
+                    packed_keys=p.packed_keys, bin_keys=p.bin_keys,
+                    bin_sort_passes=p.bin_sort_passes)
 
     def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
         """Stable in-place sort of int32 (bit pattern = uint32) keys and values."""

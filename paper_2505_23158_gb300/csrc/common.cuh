@@ -172,7 +172,9 @@ struct ProjectOut {
     uint32_t* rec_gid;  // gid of the record
     uint32_t* depth_key;  // FP32 depth bits (sort key), index = record
     uint32_t* depth_val;  // record index
-    uint32_t* counts;     // 8-byte aligned: [0] = visible (u32), [2..3] = keys (u64)
+    uint32_t* counts;     // 8-byte aligned: [0] = visible (u32), [2..3] = tile keys (u64),
+                          // [4..5] = bin keys (u64, only when bin_log2 > 0)
+    int32_t bin_log2 = 0; // bins of 2^bin_log2 x 2^bin_log2 tiles (see launch_emit)
 };
 constexpr int kProjThreads = 256;
 // Attribute sources for streamed scenes: list entries index into chunk block
@@ -234,17 +236,20 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
                     uint2* ranges = nullptr, uint32_t range_tiles = 0);
 int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
-// K4: emit (tile, record) pairs in depth order.  koff: n_vis + 1 words;
-// srec / srect: n_vis gathered record ids and rects; n_keys from the
-// projection's count.  digit_hist (zeroed, 4 x 256 words) receives the
-// exclusive digit offsets of the tile sort on key_bits tile bits.
-// rbits > 0: one packed word per pair, tile << rbits | record (tile_val
-// unused); rbits = 0: tile in tile_key, record in tile_val.
+// K4: emit (bin, record) pairs in depth order.  A bin is a square of
+// 2^bin_log2 x 2^bin_log2 tiles (bin_log2 = 0: the 16x16 tile itself), bins_x
+// per image row; a record goes to every bin its tile rect touches.  koff:
+// n_vis + 1 words; srec / srect: n_vis gathered record ids and bin rects;
+// n_keys (bin keys) from the projection's count.  digit_hist (zeroed,
+// 4 x 256 words) receives the exclusive digit offsets of the bin sort on
+// key_bits bin bits.  rbits > 0: one packed word per pair,
+// bin << rbits | record (tile_val unused); rbits = 0: bin in tile_key,
+// record in tile_val.
 constexpr int kEmitThreads = 256;
 constexpr int kEmitKeysPerCta = 2048;   // slice of the key list (small records)
 constexpr int64_t kEmitWarpMinKeys = 32;  // mean keys per record for one warp per record
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
-                 int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
+                 int32_t bins_x, int bin_log2, uint32_t* koff, uint32_t* srec, uint2* srect,
                  int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s);
@@ -262,17 +267,24 @@ struct BlendOut {
 };
 // tile_val[i] & vmask is the record of sorted pair i (vmask = all ones for
 // separate values, the low rbits for packed keys).
+// bin_log2 > 0: ranges and keys are per bin of 2^bin_log2 x 2^bin_log2
+// tiles (launch_emit); a tile walks its bin's list and skips the records
+// whose tile rect (from rec_rect) misses it, which leaves exactly the
+// tile's own list, in the same order.
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
-                  int64_t n_rec, const BlendOut& o, cudaStream_t s);
+                  int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2 = 0,
+                  const uint2* rec_rect = nullptr);
 // Everything one frame's compositing reads and writes; a batch of frames is
 // composited by one launch over all their tiles (at most kMaxBlendBatch).
 struct BlendFrame {
     int32_t width, height, tiles_x, ntiles;
     uint32_t tile_base;        // first tile of this frame in a batch launch
     uint32_t vmask, n_keys, n_rec;
-    const uint2* ranges;
+    int32_t bin_log2, bins_x;  // key lists per bin of 2^bin_log2 tiles square
+    const uint2* ranges;       // per bin
     const uint32_t* tile_val;
+    const uint2* rec_rect;     // pixel ranges (read when bin_log2 > 0)
     const float4* rec_a;
     const float4* rec_b;
     const float* rec_c;
@@ -287,7 +299,7 @@ struct BlendBatch {
 };
 BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                        int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
-                       int64_t n_rec, const BlendOut& o);
+                       int64_t n_rec, const BlendOut& o, int bin_log2 = 0, const uint2* rec_rect = nullptr);
 void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s);
 
 // K12: importance score: the blend's walk, and per record the largest

@@ -165,6 +165,7 @@ struct lodge_ctx {
     cudaStream_t upload_stream = nullptr;
     lodge::ResidencyStats res;
     int fail_next_uploads = 0;       // host-side fault injection
+    int bin_log2 = 2;                // key lists per bin of 2^bin_log2 x 2^bin_log2 tiles
 };
 
 namespace lodge {

@@ -1,26 +1,28 @@
 // K4: tile binning.  Walks the visible records in depth order and emits one
-// (tile id, record) pair per tile that the record's rect covers (Sec. 3
+// (bin id, record) pair per bin that the record's tile rect touches (Sec. 3
 // "Preliminaries: 3DGS": each 2D Gaussian is assigned to every 16x16 tile it
-// overlaps).  Two passes: key offsets by block scan plus decoupled look-back,
-// then key-balanced emission (every CTA writes the same number of keys, so a
-// few huge near-camera rects cannot serialise the pass).
+// overlaps).  A bin is the tile itself or a square of 2^bin_log2 tiles; the
+// compositing then drops, per tile, the records of its bin that miss the
+// tile.  Two passes: key offsets by block scan plus decoupled look-back, then
+// emission, key-balanced for small records, one warp per record for large
+// ones.
 //
-// K6: per-tile [begin, end) ranges of the tile-sorted keys.
+// K6: per-bin [begin, end) ranges of the bin-sorted keys.
 #include "common.cuh"
 
 namespace lodge {
 
 namespace {
 
-// Pass 1: per depth-sorted visible record, its tile count; block scan plus
+// Pass 1: per depth-sorted visible record, its bin count; block scan plus
 // decoupled look-back give the exclusive key offset koff[i] (koff[n_vis] =
 // total).  The record id and rect are gathered into depth order (srec,
-// srect, in tiles) so that pass 2 reads them contiguously.
+// srect, in bins) so that pass 2 reads them contiguously.
 __global__ void __launch_bounds__(kEmitThreads)
 emit_offsets_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
                     const uint2* __restrict__ rec_rect, uint32_t* __restrict__ koff,
                     uint32_t* __restrict__ srec, uint2* __restrict__ srect,
-                    uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
+                    int bin_log2, uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
                     uint32_t* __restrict__ err) {
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_tile, s_prefix;
@@ -33,9 +35,11 @@ emit_offsets_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     if (i < n_vis) {
         uint32_t rec = sorted_rec[i];
         if ((int64_t)rec >= n_vis) { atomicOr(err, kErrBadIndex); rec = 0; }
-        const uint2 p = rec_rect[rec];   // pixel range -> tile range
-        const uint2 r = make_uint2(((p.x & 0xffffu) / kTile) | (((p.x >> 16) / kTile) << 16),
-                                   ((p.y & 0xffffu) / kTile) | (((p.y >> 16) / kTile) << 16));
+        const uint2 p = rec_rect[rec];   // pixel range -> tile range -> bin range
+        const uint2 r = make_uint2((((p.x & 0xffffu) / kTile) >> bin_log2) |
+                                       ((((p.x >> 16) / kTile) >> bin_log2) << 16),
+                                   (((p.y & 0xffffu) / kTile) >> bin_log2) |
+                                       ((((p.y >> 16) / kTile) >> bin_log2) << 16));
         uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu) + 1u;
         uint32_t h = (r.y >> 16) - (r.x >> 16) + 1u;
         cnt = w * h;
@@ -249,15 +253,15 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ key, int64_t n, uint2
 }  // namespace
 
 void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rect,
-                 int32_t tiles_x, int32_t tiles_y, uint32_t* koff, uint32_t* srec, uint2* srect,
+                 int32_t bins_x, int bin_log2, uint32_t* koff, uint32_t* srec, uint2* srect,
                  int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s) {
-    (void)tiles_y;
+    const int32_t tiles_x = bins_x;   // the emit kernels index bins as tiles
     int64_t nb = (n_vis + kEmitThreads - 1) / kEmitThreads;
     if (nb == 0) return;
     emit_offsets_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, koff, srec,
-                                                              srect, status, tile_counter, err);
+                                                              srect, bin_log2, status, tile_counter, err);
     if (n_keys == 0) return;
     const int P = (key_bits + 7) / 8;
     const int last_bits = key_bits - 8 * (P - 1);

@@ -9,6 +9,12 @@
 // transmittance below 1e-4; a warp whose 64 pixels have all stopped skips
 // the batch, and the CTA leaves as soon as all 256 have stopped.
 //
+// With coarse bins (squares of 2^bin_log2 tiles) the tile walks its bin's
+// key list: each batch also stages the records' pixel rects, every warp
+// ballots which of the 128 records touch the tile (the same test as tile
+// binning: the record's tile rect contains the tile) and the walk visits
+// only those, so a tile composites exactly its own list, in the same order.
+//
 // Per pixel and Gaussian (record = mean', upper-triangular U with
 // U^T U = (1/2) log2(e) Sigma'^-1, opacity o', colour):
 //   q = (u00 dx + u01 dy)^2 + (u11 dy)^2,  alpha = min(0.99, o' 2^-q)
@@ -34,6 +40,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
@@ -42,10 +52,36 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// one record of the batch against one pixel (Eq. 1)
+__device__ __forceinline__ void blend_px(const float4 a, const float4 bb, const float cz, float dx,
+                                         float py, float& T, float& C0, float& C1, float& C2,
+                                         bool& done, uint32_t& last, uint32_t pos) {
+    const float dy = py - a.y;
+    const float t = fmaf(a.z, dx, a.w * dy);
+    const float wq = bb.x * dy;
+    const float q = fmaf(t, t, wq * wq);
+    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+    if (alpha >= (1.0f / 255.0f)) {
+        const float Tn = T * (1.f - alpha);
+        if (Tn < 1e-4f) {
+            done = true;
+        } else {
+            const float wgt = T * alpha;
+            C0 = fmaf(wgt, bb.z, C0);
+            C1 = fmaf(wgt, bb.w, C1);
+            C2 = fmaf(wgt, cz, C2);
+            T = Tn;
+            last = pos;
+        }
+    }
+}
+
+template <bool kBins>
 __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     __shared__ float4 sa[2][kBlendBatch];
     __shared__ float4 sb[2][kBlendBatch];
     __shared__ float sc[2][kBlendBatch];
+    __shared__ uint2 sr[2][kBins ? kBlendBatch : 1];
     const int32_t width = f.width, height = f.height, tiles_x = f.tiles_x;
     const uint2* __restrict__ ranges = f.ranges;
     const uint32_t* __restrict__ tile_val = f.tile_val;
@@ -64,7 +100,11 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     const int y0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3), y1 = y0 + 4;
     const bool in0 = x < width && y0 < height, in1 = x < width && y1 < height;
     const float pxf = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
-    uint2 rg = ranges[tile];
+    const uint2* __restrict__ rec_rect = f.rec_rect;
+    // a frame of a binned batch launch may still have per-tile lists
+    const bool binned = kBins && f.bin_log2 > 0 && rec_rect != nullptr;
+    const int bin = binned ? (ty >> f.bin_log2) * f.bins_x + (tx >> f.bin_log2) : tile;
+    uint2 rg = ranges[bin];
     if (rg.y > n_keys || rg.x > rg.y) rg = make_uint2(0, 0);  // never for a consistent sort
     const int n = (int)(rg.y - rg.x);
     const int nb = (n + kBlendBatch - 1) / kBlendBatch;
@@ -80,6 +120,7 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
             cp_async16(&sa[0][tid], rec_a + j);
             cp_async16(&sb[0][tid], rec_b + j);
             cp_async4(&sc[0][tid], rec_c + j);
+            if (binned) cp_async8(&sr[0][tid], rec_rect + j);
         }
         cp_async_commit();
     }
@@ -92,57 +133,53 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                 cp_async16(&sa[buf ^ 1][tid], rec_a + j);
                 cp_async16(&sb[buf ^ 1][tid], rec_b + j);
                 cp_async4(&sc[buf ^ 1][tid], rec_c + j);
+                if (binned) cp_async8(&sr[buf ^ 1][tid], rec_rect + j);
             }
         }
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
         const int cnt = min(kBlendBatch, n - b * kBlendBatch);
-        if (!__all_sync(0xffffffffu, done0 && done1)) {
+        if (kBins) {
+            // which records of the batch touch this tile: 4 ballots per warp
+            uint32_t m[kBlendBatch / 32];
+#pragma unroll
+            for (int w = 0; w < kBlendBatch / 32; ++w) {
+                const int k = w * 32 + lane;
+                bool hit = k < cnt;
+                if (hit && binned) {
+                    const uint2 r = sr[buf][k];
+                    hit = ((r.x & 0xffffu) / kTile) <= (uint32_t)tx && ((r.y & 0xffffu) / kTile) >= (uint32_t)tx &&
+                          ((r.x >> 16) / kTile) <= (uint32_t)ty && ((r.y >> 16) / kTile) >= (uint32_t)ty;
+                }
+                m[w] = __ballot_sync(0xffffffffu, hit);
+            }
+            if (!__all_sync(0xffffffffu, done0 && done1)) {
+#pragma unroll
+                for (int w = 0; w < kBlendBatch / 32; ++w) {
+                    uint32_t mm = m[w];
+                    while (mm && !(done0 && done1)) {
+                        const int k = w * 32 + __ffs(mm) - 1;
+                        mm &= mm - 1u;
+                        const float4 a = sa[buf][k];
+                        const float4 bb = sb[buf][k];
+                        const float cz = sc[buf][k];
+                        const float dx = pxf - a.x;
+                        const uint32_t pos = (uint32_t)(b * kBlendBatch + k + 1);
+                        if (!done0) blend_px(a, bb, cz, dx, py0, T0, C00, C01, C02, done0, last0, pos);
+                        if (!done1) blend_px(a, bb, cz, dx, py1, T1, C10, C11, C12, done1, last1, pos);
+                    }
+                }
+            }
+        } else if (!__all_sync(0xffffffffu, done0 && done1)) {
             for (int k = 0; k < cnt && !(done0 && done1); ++k) {
                 const float4 a = sa[buf][k];
                 const float4 bb = sb[buf][k];
+                const float cz = sc[buf][k];
                 const float dx = pxf - a.x;
-                if (!done0) {
-                    const float dy = py0 - a.y;
-                    const float t = fmaf(a.z, dx, a.w * dy);
-                    const float wq = bb.x * dy;
-                    const float q = fmaf(t, t, wq * wq);
-                    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
-                    if (alpha >= (1.0f / 255.0f)) {
-                        const float Tn = T0 * (1.f - alpha);
-                        if (Tn < 1e-4f) {
-                            done0 = true;
-                        } else {
-                            const float wgt = T0 * alpha;
-                            C00 = fmaf(wgt, bb.z, C00);
-                            C01 = fmaf(wgt, bb.w, C01);
-                            C02 = fmaf(wgt, sc[buf][k], C02);
-                            T0 = Tn;
-                            last0 = (uint32_t)(b * kBlendBatch + k + 1);
-                        }
-                    }
-                }
-                if (!done1) {
-                    const float dy = py1 - a.y;
-                    const float t = fmaf(a.z, dx, a.w * dy);
-                    const float wq = bb.x * dy;
-                    const float q = fmaf(t, t, wq * wq);
-                    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
-                    if (alpha >= (1.0f / 255.0f)) {
-                        const float Tn = T1 * (1.f - alpha);
-                        if (Tn < 1e-4f) {
-                            done1 = true;
-                        } else {
-                            const float wgt = T1 * alpha;
-                            C10 = fmaf(wgt, bb.z, C10);
-                            C11 = fmaf(wgt, bb.w, C11);
-                            C12 = fmaf(wgt, sc[buf][k], C12);
-                            T1 = Tn;
-                            last1 = (uint32_t)(b * kBlendBatch + k + 1);
-                        }
-                    }
-                }
+                const uint32_t pos = (uint32_t)(b * kBlendBatch + k + 1);
+                if (!done0) blend_px(a, bb, cz, dx, py0, T0, C00, C01, C02, done0, last0, pos);
+                if (!done1) blend_px(a, bb, cz, dx, py1, T1, C10, C11, C12, done1, last1, pos);
             }
         }
         if (__syncthreads_count(done0 && done1) == kBlendThreads) break;
@@ -166,10 +203,14 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     }
 }
 
-__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) { blend_tile(f, blockIdx.x); }
+template <bool kBins>
+__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) {
+    blend_tile<kBins>(f, blockIdx.x);
+}
 
 // One launch for the tiles of several frames (a serving step): CTA b
 // composites tile b - tile_base of the last frame whose tile_base <= b.
+template <bool kBins>
 __global__ void __launch_bounds__(kBlendThreads) blend_batch_kernel(BlendBatch bb) {
     const uint32_t b = blockIdx.x;
     int lo = 0, hi = bb.n - 1;
@@ -177,7 +218,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_batch_kernel(BlendBatch b
         const int mid = (lo + hi + 1) >> 1;
         if (bb.f[mid].tile_base <= b) lo = mid; else hi = mid - 1;
     }
-    blend_tile(bb.f[lo], (int)(b - bb.f[lo].tile_base));
+    blend_tile<kBins>(bb.f[lo], (int)(b - bb.f[lo].tile_base));
 }
 
 
@@ -275,7 +316,7 @@ __global__ void record_score_to_gid_kernel(const uint32_t* __restrict__ rec_scor
 
 BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                        int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
-                       int64_t n_rec, const BlendOut& o) {
+                       int64_t n_rec, const BlendOut& o, int bin_log2, const uint2* rec_rect) {
     BlendFrame f;
     f.width = cam.width;
     f.height = cam.height;
@@ -285,8 +326,11 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
     f.vmask = vmask;
     f.n_keys = (uint32_t)n_keys;
     f.n_rec = (uint32_t)std::max<int64_t>(n_rec, 1);
+    f.bin_log2 = rec_rect ? bin_log2 : 0;
+    f.bins_x = (cam.tiles_x + (1 << f.bin_log2) - 1) >> f.bin_log2;
     f.ranges = ranges;
     f.tile_val = tile_val;
+    f.rec_rect = rec_rect;
     f.rec_a = rec_a;
     f.rec_b = rec_b;
     f.rec_c = rec_c;
@@ -298,25 +342,34 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
 
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
-                  int64_t n_rec, const BlendOut& o, cudaStream_t s) {
-    const BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o);
+                  int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2, const uint2* rec_rect) {
+    const BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o,
+                                     bin_log2, rec_rect);
     if (f.ntiles == 0) return;
-    blend_kernel<<<f.ntiles, kBlendThreads, 0, s>>>(f);
+    if (f.bin_log2 > 0)
+        blend_kernel<true><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+    else
+        blend_kernel<false><<<f.ntiles, kBlendThreads, 0, s>>>(f);
 }
 
 void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s) {
     BlendBatch bb;
     uint32_t base = 0;
     bb.n = 0;
+    bool bins = false;   // the binned walk also serves frames with per-tile lists
     for (int i = 0; i < n && i < kMaxBlendBatch; ++i) {
         if (frames[i].ntiles == 0) continue;
         bb.f[bb.n] = frames[i];
         bb.f[bb.n].tile_base = base;
         base += (uint32_t)frames[i].ntiles;
+        bins = bins || frames[i].bin_log2 > 0;
         ++bb.n;
     }
     if (bb.n == 0) return;
-    blend_batch_kernel<<<base, kBlendThreads, 0, s>>>(bb);
+    if (bins)
+        blend_batch_kernel<true><<<base, kBlendThreads, 0, s>>>(bb);
+    else
+        blend_batch_kernel<false><<<base, kBlendThreads, 0, s>>>(bb);
 }
 
 void launch_importance(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val,

@@ -174,8 +174,8 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
                uint32_t* __restrict__ err) {
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_scan[33];
-    __shared__ unsigned long long s_keys;
-    if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_keys = 0ull; }
+    __shared__ unsigned long long s_keys, s_bkeys;
+    if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_keys = 0ull; s_bkeys = 0ull; }
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t ntiles = (uint32_t)((P.n_active + kProjThreads - 1) / kProjThreads);
@@ -242,6 +242,12 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
     }
+    const int bl = P.o.bin_log2;
+    if (bl > 0) {   // keys of the coarse bins (squares of 2^bl tiles)
+        uint32_t wsum = vis ? ((rx1 >> bl) - (rx0 >> bl) + 1) * ((ry1 >> bl) - (ry0 >> bl) + 1) : 0u;
+        for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_bkeys, (unsigned long long)wsum);
+    }
     if (threadIdx.x < 32) {
         uint32_t prefix = 0;
         if (tile == 0) {
@@ -259,6 +265,8 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     __syncthreads();
     if (threadIdx.x == 0 && s_keys)
         atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 2), s_keys);
+    if (threadIdx.x == 0 && s_bkeys)
+        atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 4), s_bkeys);
     if (!vis) return;
 
     // ---- inverse 2D covariance in Cholesky form, with (1/2) log2(e) folded

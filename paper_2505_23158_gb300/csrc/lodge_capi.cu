@@ -547,6 +547,10 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     po.depth_key = ws.dkey.as<uint32_t>();
     po.depth_val = ws.dval.as<uint32_t>();
     po.counts = sl.d_small + kSmProj;
+    // frames kept for the adjoint and the importance walk use per-tile lists
+    // (their per-pixel positions index the tile's own list)
+    const int bl = (save || importance) ? 0 : ctx->bin_log2;
+    po.bin_log2 = bl;
     prof_begin(sl, LODGE_STAGE_PROJECT, s);
     launch_project(dsc, cam, act.list, na, (float)act.tA, (float)act.tB, po,
                    ws.status.as<uint32_t>(), sl.d_small + kSmCtrProj, sl.d_small + kSmErr, s,
@@ -559,13 +563,22 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     std::memcpy(&nk64, sl.h_small + kSmProj + 2, 8);
     const int64_t n_keys = (int64_t)nk64;
     if (n_keys >= (1ll << 30)) return fail(LODGE_E_OVERFLOW, "%lld tile keys exceed 2^30", (long long)n_keys);
-    const size_t nv1 = (size_t)std::max<int64_t>(n_vis, 1), nk1 = (size_t)std::max<int64_t>(n_keys, 1);
+    // key lists per bin: the tile itself (bl = 0) or a square of 2^bl tiles
+    int64_t n_bkeys = n_keys;
+    if (bl > 0) {
+        std::memcpy(&nk64, sl.h_small + kSmProj + 4, 8);
+        n_bkeys = (int64_t)nk64;
+    }
+    const int32_t bins_x = (cam.tiles_x + (1 << bl) - 1) >> bl;
+    const int32_t bins_y = (cam.tiles_y + (1 << bl) - 1) >> bl;
+    const int64_t nbins = (int64_t)bins_x * bins_y;
+    const size_t nv1 = (size_t)std::max<int64_t>(n_vis, 1), nk1 = (size_t)std::max<int64_t>(n_bkeys, 1);
 
     // ---- K5 depth sort of the visible records
     TRY(ensure(ctx, ws.dkey2, sizeof(uint32_t) * nv1, s));
     TRY(ensure(ctx, ws.dval2, sizeof(uint32_t) * nv1, s));
-    const int tbits = bits_for((uint32_t)(ntiles_img - 1));
-    TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_keys, tbits)), s));
+    const int tbits = bits_for((uint32_t)std::max<int64_t>(nbins - 1, 0));
+    TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_bkeys, tbits)), s));
     prof_begin(sl, LODGE_STAGE_DEPTH_SORT, s);
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
                              ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s);
@@ -573,10 +586,10 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
 
-    // ---- K4 emit (tile, record) in depth order, with the tile sort's digit
-    // counts.  When tile and record index fit in one word together, each pair
-    // is one packed key (tile << rbits | record) and the tile sort moves keys
-    // only; otherwise tile and record are sorted as a (key, value) pair.
+    // ---- K4 emit (bin, record) in depth order, with the bin sort's digit
+    // counts.  When bin and record index fit in one word together, each pair
+    // is one packed key (bin << rbits | record) and the bin sort moves keys
+    // only; otherwise bin and record are sorted as a (key, value) pair.
     const int rbits_need = bits_for((uint32_t)std::max<int64_t>(n_vis - 1, 0));
     const int rbits = tbits + rbits_need <= 32 ? rbits_need : 0;
     TRY(ensure(ctx, ws.tkey, sizeof(uint32_t) * nk1, s));
@@ -594,36 +607,36 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
     prof_begin(sl, LODGE_STAGE_EMIT, s);
-    launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), cam.tiles_x, cam.tiles_y,
-                ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_keys,
+    launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), bins_x, bl,
+                ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_bkeys,
                 ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits, ws.doffs.as<uint32_t>(),
                 ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
-    prof_end(sl, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_keys > 0 ? 2 : 0));
+    prof_end(sl, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_bkeys > 0 ? 2 : 0));
 
-    // ---- K6 tile ranges: recorded by the tile sort's last pass (begin by
+    // ---- K6 bin ranges: recorded by the bin sort's last pass (begin by
     // atomic minimum from 0xffffffff, end by atomic maximum from 0); with at
     // most one key the sort does not run and K6 scans the key list instead
-    const bool fused_ranges = n_keys > 1;
-    TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)ntiles_img, s));
-    CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)ntiles_img, s));
-    if (fused_ranges && ntiles_img)
-        CUDA_TRY(cudaMemset2DAsync(ws.ranges.p, sizeof(uint2), 0xff, sizeof(uint32_t), (size_t)ntiles_img, s));
+    const bool fused_ranges = n_bkeys > 1;
+    TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(nbins, 1), s));
+    CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)nbins, s));
+    if (fused_ranges && nbins)
+        CUDA_TRY(cudaMemset2DAsync(ws.ranges.p, sizeof(uint2), 0xff, sizeof(uint32_t), (size_t)nbins, s));
 
-    // ---- K5 tile sort (stable: keeps depth order within a tile)
+    // ---- K5 bin sort (stable: keeps depth order within a bin)
     prof_begin(sl, LODGE_STAGE_TILE_SORT, s);
     int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), rbits ? nullptr : ws.tval.as<uint32_t>(),
-                             ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_keys,
+                             ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_bkeys,
                              tbits, ws.sort.p, sl.d_small + kSmErr, s, ws.doffs.as<uint32_t>(), true, rbits,
-                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)ntiles_img);
-    prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_keys, tbits, true));
+                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins);
+    prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_bkeys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
     const uint32_t* rec_of_pair = rbits ? ks.as<uint32_t>() : vs.as<uint32_t>();
     const uint32_t vmask = rbits ? (1u << rbits) - 1u : 0xffffffffu;
     if (!fused_ranges) {
         prof_begin(sl, LODGE_STAGE_RANGES, s);
-        launch_ranges(ks.as<uint32_t>(), n_keys, ws.ranges.as<uint2>(), ntiles_img, rbits, s);
-        prof_end(sl, LODGE_STAGE_RANGES, s, n_keys > 0 ? 1 : 0);
+        launch_ranges(ks.as<uint32_t>(), n_bkeys, ws.ranges.as<uint2>(), nbins, rbits, s);
+        prof_end(sl, LODGE_STAGE_RANGES, s, n_bkeys > 0 ? 1 : 0);
     }
 
     // ---- K7 blend
@@ -636,8 +649,9 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         bo.last = ws.last.as<uint32_t>();
     }
     if (job) {
-        *job = blend_frame(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
-                           ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo);
+        *job = blend_frame(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_bkeys, ws.rec_a.as<float4>(),
+                           ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, bl,
+                           ws.rec_rect.as<uint2>());
         end_sync = false;
     }
     prof_begin(sl, LODGE_STAGE_BLEND, s);
@@ -650,8 +664,8 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
                           ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, ws.rec_gid.as<uint32_t>(),
                           d_rgb, ws.iscore.as<uint32_t>(), dsc.n_total, importance, s);
     } else {
-        launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_keys, ws.rec_a.as<float4>(),
-                     ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s);
+        launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_bkeys, ws.rec_a.as<float4>(),
+                     ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s, bl, ws.rec_rect.as<uint2>());
     }
     prof_end(sl, LODGE_STAGE_BLEND, s, job ? 0 : ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
     CUDA_TRY(cudaGetLastError());
@@ -667,7 +681,9 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
 
     sl.prof.frames += 1;
     sl.prof.keys += n_keys;
-    if (rbits) sl.prof.packed_keys += n_keys;
+    sl.prof.bin_keys += n_bkeys;
+    if (rbits) sl.prof.packed_keys += n_bkeys;
+    sl.prof.bin_sort_passes += n_bkeys > 1 ? (tbits + 7) / 8 : 0;
     sl.prof.visible += n_vis;
     sl.prof.active += na;
     if (st) {
@@ -1751,6 +1767,8 @@ lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
         p.visible += q.visible;
         p.active += q.active;
         p.packed_keys += q.packed_keys;
+        p.bin_keys += q.bin_keys;
+        p.bin_sort_passes += q.bin_sort_passes;
     }
     *out = p;
     return LODGE_OK;
@@ -1767,6 +1785,13 @@ lodge_status lodge_residency_stats(lodge_ctx* ctx, lodge_residency* out) {
     out->failed_uploads = ctx->res.failed_uploads;
     out->hbm_used = (int64_t)ctx->used;
     out->hbm_budget = (int64_t)ctx->budget;
+    return LODGE_OK;
+}
+
+lodge_status lodge_set_bin_size(lodge_ctx* ctx, int32_t log2_tiles) {
+    if (!ctx || log2_tiles < 0 || log2_tiles > 3) return fail(LODGE_E_INVALID, "bad argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->bin_log2 = log2_tiles;
     return LODGE_OK;
 }
 

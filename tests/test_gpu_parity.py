@@ -344,3 +344,71 @@ def test_camera_list_equals_single_frames(ctx, torch_cuda):
             one, st1 = ctx.render(sid, mode, cam)
             assert torch_cuda.equal(one, img)
             assert st1["n_keys"] == st["n_keys"]
+
+
+# ---------------------------------------------------------------------------
+# key lists per bin of 2^k x 2^k tiles
+
+
+def _bin_keys(rect, k):
+    """Keys of one frame with bins of 2^k tiles square, from the oracle's
+    tile rects (tx0, ty0, tx1, ty1): one per (record, bin) the rect touches."""
+    r = rect.astype(np.int64) >> k
+    return int(((r[:, 2] - r[:, 0] + 1) * (r[:, 3] - r[:, 1] + 1)).sum())
+
+
+@pytest.mark.parametrize("log2", [0, 1, 2, 3])
+def test_binned_lists_same_image(ctx, outdoor, torch_cuda, log2):
+    """Compositing from per-bin lists gives the per-tile lists' image bit for
+    bit and matches the oracle; the keys emitted and sorted are exactly one
+    per (visible Gaussian, bin its tile rect touches)."""
+    from paper_2505_23158_gb300.api import CHUNK_BLEND, FULL
+    scene, cams, osc, sid = outdoor
+    try:
+        for mode in (FULL, CHUNK_BLEND):
+            for i in (0, 4):
+                cam = cams[i]
+                ctx.set_bin_size(0)
+                per_tile, st0 = ctx.render(sid, mode, cam)
+                ctx.set_bin_size(log2)
+                ctx.profile_enable(True)
+                img, st = ctx.render(sid, mode, cam)
+                prof = ctx.profile_read()
+                ctx.profile_enable(False)
+                assert torch_cuda.equal(img, per_tile), f"mode {mode} pose {i}"
+                assert st["n_keys"] == st0["n_keys"]
+                g_ref, m_ref, info = O.active_set(osc, mode, cam)
+                pr = O.project(osc, cam, g_ref, m_ref)
+                assert prof["frames"] == 1
+                assert prof["keys"] == st["n_keys"]
+                assert prof["bin_keys"] == _bin_keys(pr["rect"][pr["visible"]], log2)
+                ref = O.render(osc, cam, g_ref, m_ref)
+                compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"bins {log2} pose {i}")
+    finally:
+        ctx.set_bin_size(2)
+
+
+@pytest.mark.parametrize("wh", [(17, 33), (1, 1), (257, 129), (100, 70)])
+def test_binned_lists_ragged_sizes(ctx, plain_loaded, torch_cuda, wh):
+    """Bins that overhang the image edge (tiles_x, tiles_y not multiples of
+    the bin size): same image as per-tile lists for every bin size."""
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    cam = synth.plain_camera(*wh)
+    try:
+        ctx.set_bin_size(0)
+        ref, _ = ctx.render(sid, FULL, cam)
+        for k in (1, 2, 3):
+            ctx.set_bin_size(k)
+            img, _ = ctx.render(sid, FULL, cam)
+            assert torch_cuda.equal(img, ref), f"bins {k}"
+    finally:
+        ctx.set_bin_size(2)
+
+
+def test_bin_size_argument_checked(ctx):
+    from paper_2505_23158_gb300.api import LodgeError
+    for bad in (-1, 4):
+        with pytest.raises(LodgeError):
+            ctx.set_bin_size(bad)
+    ctx.set_bin_size(2)
