@@ -355,8 +355,14 @@ def run_lodge(args, rank, world, local_rank):
     # event timing per stage, the stage breakdown and the roofline (frames of
     # one call overlap on two streams, which would blur per-stage events)
     ctx.profile_enable(True)
-    lat = frame_latency(CHUNK_BLEND, min(len(cams), 100))
+    n_lat = min(len(cams), 100)
+    lat = frame_latency(CHUNK_BLEND, n_lat)
     prof = ctx.profile_read()
+    # the same frames again in counting mode (untimed): the compositing's
+    # evaluated and composited (pixel, Gaussian) pairs, for its roofline
+    ctx.profile_enable(True, count_pairs=True)
+    frame_latency(CHUNK_BLEND, n_lat)
+    prof_cnt = ctx.profile_read()
     ctx.profile_enable(True)
     lat_full = frame_latency(FULL, 10)
     prof_full = ctx.profile_read()
@@ -380,15 +386,23 @@ def run_lodge(args, rank, world, local_rank):
     launches = sum(prof_timed["launches"].values())
     roof = None
     if dom == "blend":
-        # ALU-bound: bound by the FP32 pipes; report against the SM count x
-        # 128 lanes x 2 flops x max clock.  Evaluated pairs are not counted in
-        # this build, so report the pipe-peak and leave achieved to the
-        # counters (see profiles/).
+        # bound by FP32 arithmetic: algorithmic flops per evaluated pair (Eq. 1
+        # alpha: 9.5, the shared dx counted once per two pixels) and per
+        # composited pair (transmittance and colour: 9), FMA = 2 flops, the
+        # exp2 on the MUFU not counted; peak = 152 SMs x 128 FP32 lanes x 2 x
+        # the maximum SM clock
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": None, "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "kernel": "blend",
-                "peak_source": f"{pk_kind}: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
+        nf = max(prof_cnt["frames"], 1)
+        flops = (9.5 * prof_cnt["blend_pairs"] + 9.0 * prof_cnt["blend_pairs_used"]) / nf
+        t_launch = ms["blend"] / max(prof["frames"], 1) / 1e3
+        ach = flops / t_launch / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None, "kernel": "blend",
+                "flops_per_launch": round(flops), "pairs_per_launch": prof_cnt["blend_pairs"] // nf,
+                "composited_pairs_per_launch": prof_cnt["blend_pairs_used"] // nf,
+                "avg_launch_ms": round(t_launch * 1e3, 5),
+                "peak_source": f"{pk_kind} sm_max_mhz x 152 SMs x 128 FP32 lanes x 2"}
     else:
         by = stage_bytes(dom, prof)
         ach = by / (ms[dom] / 1e3) / 1e9

@@ -221,7 +221,7 @@ lodge_status lodge_kmeans_centers(const double* positions, int32_t n, int32_t k,
 
 /* Size of the bins whose key lists the renders of this context sort and
  * composite from: squares of 2^log2_tiles x 2^log2_tiles 16x16 tiles
- * (0..3; the context starts at 2, 64x64 pixels).  A Gaussian is keyed once
+ * (0..3; the context starts at 3, 128x128 pixels).  A Gaussian is keyed once
  * per bin its tile rect touches (Sec. 3, "Preliminaries: 3DGS", assigns it
  * to every tile it overlaps); compositing walks the bin's list for each of
  * the bin's tiles and skips the Gaussians whose tile rect misses the tile,
@@ -464,10 +464,18 @@ typedef struct {
     int64_t bin_keys;    /* sum of per-frame keys emitted and sorted (one per
                           * record and bin; equals keys for per-tile bins) */
     int64_t bin_sort_passes; /* sum of per-frame passes of the bin sort */
+    int64_t blend_pairs;      /* counting mode: (pixel, Gaussian) pairs the
+                               * compositing evaluated (Eq. 1 alpha) */
+    int64_t blend_pairs_used; /* counting mode: pairs composited (alpha >=
+                               * 1/255 and the pixel not yet saturated) */
 } lodge_profile;
 
 /* Start (enable != 0, counters reset) or stop collecting the profile.
- * Launch counts are always collected; event timing only while enabled. */
+ * Launch counts are always collected; event timing only while enabled.
+ * enable = 2 is the counting mode: single-frame compositing also counts its
+ * (pixel, Gaussian) pairs (blend_pairs, blend_pairs_used) with a counting
+ * variant of the kernel and every frame synchronises, so stage times taken
+ * in this mode are not those of the plain kernels. */
 lodge_status lodge_profile_enable(lodge_ctx* ctx, int enable);
 
 /* Copy the accumulated profile to *out (host). */

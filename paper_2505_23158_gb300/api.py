@@ -355,8 +355,10 @@ class Lodge:
     def inject_upload_failures(self, n: int):
         A.call("lodge_inject_upload_failures", self._h, int(n))
 
-    def profile_enable(self, enable: bool = True):
-        A.call("lodge_profile_enable", self._h, int(enable))
+    def profile_enable(self, enable: bool = True, count_pairs: bool = False):
+        """Event timing per stage (counters reset); count_pairs: the counting
+        mode (compositing counts its pixel-Gaussian pairs; times not plain)."""
+        A.call("lodge_profile_enable", self._h, 2 if (enable and count_pairs) else int(enable))
 
     def profile_read(self) -> dict:
         p = A.lodge_profile()
@@ -365,7 +367,8 @@ class Lodge:
                     launches={n: p.launches[i] for i, n in enumerate(A.STAGE_NAMES)},
                     frames=p.frames, keys=p.keys, visible=p.visible, active=p.active,
                     packed_keys=p.packed_keys, bin_keys=p.bin_keys,
-                    bin_sort_passes=p.bin_sort_passes)
+                    bin_sort_passes=p.bin_sort_passes, blend_pairs=p.blend_pairs,
+                    blend_pairs_used=p.blend_pairs_used)
 
     def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
         """Stable in-place sort of int32 (bit pattern = uint32) keys and values."""

@@ -175,6 +175,8 @@ struct ProjectOut {
     uint32_t* counts;     // 8-byte aligned: [0] = visible (u32), [2..3] = tile keys (u64),
                           // [4..5] = bin keys (u64, only when bin_log2 > 0)
     int32_t bin_log2 = 0; // bins of 2^bin_log2 x 2^bin_log2 tiles (see launch_emit)
+    uint32_t* depth_hist = nullptr;  // null, or 4 x 256 zeroed words: += the digit counts
+                                     // of the visible records' depth keys (the depth sort's)
 };
 constexpr int kProjThreads = 256;
 // Attribute sources for streamed scenes: list entries index into chunk block
@@ -254,6 +256,10 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s);
 
+int emit_launches(int64_t n_vis, int64_t n_keys, int bin_log2);
+// exclusive scan, in place, of `passes` 256-bin digit histograms (one launch)
+void launch_digit_scan(uint32_t* hist, int passes, cudaStream_t s);
+
 // K6: per tile [begin, end) of the sorted keys (tile = key >> shift);
 // ranges zeroed by the caller.
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,
@@ -274,9 +280,10 @@ struct BlendOut {
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2 = 0,
-                  const uint2* rec_rect = nullptr);
+                  const uint2* rec_rect = nullptr, unsigned long long* pairs = nullptr);
 // Everything one frame's compositing reads and writes; a batch of frames is
-// composited by one launch over all their tiles (at most kMaxBlendBatch).
+// composited by one launch over all their tiles (at most kMaxBlendBatch);
+// frames of a batch write images only (no T_final, no last).
 struct BlendFrame {
     int32_t width, height, tiles_x, ntiles;
     uint32_t tile_base;        // first tile of this frame in a batch launch
@@ -285,6 +292,7 @@ struct BlendFrame {
     const uint2* ranges;       // per bin
     const uint32_t* tile_val;
     const uint2* rec_rect;     // pixel ranges (read when bin_log2 > 0)
+    unsigned long long* pairs; // null, or [0] += pairs evaluated, [1] += pairs composited
     const float4* rec_a;
     const float4* rec_b;
     const float* rec_c;

@@ -103,6 +103,7 @@ enum : int {
     kSmCtrUnion = 9,
     kSmCtrProj = 10,
     kSmCtrEmit = 11,
+    kSmPairs = 12,      // [12..13] pairs evaluated, [14..15] composited (u64, counting mode)
     kSmWords = 64
 };
 
@@ -121,6 +122,7 @@ struct Slot {
     uint32_t* h_tail = nullptr;   // pinned
     bool tail_pending = false;
     bool prof_on = false;
+    bool prof_count = false;   // compositing counts its (pixel, Gaussian) pairs
     lodge_profile prof{};
     cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};
     cudaEvent_t ev_end[LODGE_NUM_STAGES] = {};
@@ -165,7 +167,7 @@ struct lodge_ctx {
     cudaStream_t upload_stream = nullptr;
     lodge::ResidencyStats res;
     int fail_next_uploads = 0;       // host-side fault injection
-    int bin_log2 = 2;                // key lists per bin of 2^bin_log2 x 2^bin_log2 tiles
+    int bin_log2 = 3;                // key lists per bin of 2^bin_log2 x 2^bin_log2 tiles
 };
 
 namespace lodge {

@@ -221,6 +221,126 @@ emit_keys_rect_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restr
     }
 }
 
+// Coarse bins (a few keys per record): offsets and emission in one pass.
+// A CTA takes 256 depth-sorted records, scans their bin counts and finds
+// its key offset by decoupled look-back.  A record of at most 32 keys is
+// written by its own thread; larger ones (the nearest records, which all
+// fall in the first CTAs) go to a shared list that the CTA's warps take one
+// record at a time, the lanes striding over the record's keys.  The bin
+// sort's digit counts are kept in shared memory and flushed once.
+constexpr uint32_t kFusedThreadKeys = 32;
+__global__ void __launch_bounds__(kEmitThreads)
+emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
+                  const uint2* __restrict__ rec_rect, int bin_log2, int32_t bins_x, int64_t n_keys,
+                  uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits,
+                  int passes, uint32_t last_mask, uint32_t* __restrict__ digit_hist,
+                  uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
+                  uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_tile, s_prefix, s_nbig;
+    __shared__ uint32_t s_big[kEmitThreads];
+    __shared__ uint32_t s_off[kEmitThreads];
+    __shared__ uint32_t s_cnt[kEmitThreads];
+    __shared__ uint2 s_rect[kEmitThreads];
+    __shared__ uint32_t s_rec[kEmitThreads];
+    __shared__ uint32_t s_hist[3][256];
+    for (int i = threadIdx.x; i < 3 * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+    if (threadIdx.x == 0) { s_tile = atomicAdd(counter, 1u); s_nbig = 0; }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t ntiles = (uint32_t)((n_vis + kEmitThreads - 1) / kEmitThreads);
+    const int64_t i = (int64_t)tile * kEmitThreads + threadIdx.x;
+    uint32_t cnt = 0, rec = 0, x0 = 0, y0 = 0, w = 1;
+    if (i < n_vis) {
+        rec = sorted_rec[i];
+        if ((int64_t)rec >= n_vis) { atomicOr(err, kErrBadIndex); rec = 0; }
+        const uint2 p = rec_rect[rec];   // pixel range -> tile range -> bin range
+        x0 = ((p.x & 0xffffu) / kTile) >> bin_log2;
+        y0 = ((p.x >> 16) / kTile) >> bin_log2;
+        const uint32_t x1 = ((p.y & 0xffffu) / kTile) >> bin_log2, y1 = ((p.y >> 16) / kTile) >> bin_log2;
+        w = x1 - x0 + 1u;
+        cnt = w * (y1 - y0 + 1u);
+    }
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan(cnt, s_scan, &total);
+    if (cnt > kFusedThreadKeys) {
+        const uint32_t slot = atomicAdd(&s_nbig, 1u);
+        s_big[slot] = threadIdx.x;
+        s_off[threadIdx.x] = excl;
+        s_cnt[threadIdx.x] = cnt;
+        s_rect[threadIdx.x] = make_uint2(x0 | (y0 << 16), w);   // bin coordinates < 2^12
+        s_rec[threadIdx.x] = rec;
+    }
+    if (threadIdx.x < 32) {
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) st_volatile(status, kStInc | total);
+        } else {
+            if (threadIdx.x == 0) st_volatile(status + tile, kStAgg | total);
+            prefix = warp_lookback(status, tile, err);
+            if (threadIdx.x == 0) st_volatile(status + tile, kStInc | (prefix + total));
+        }
+        if (threadIdx.x == 0) {
+            s_prefix = prefix;
+            if (tile == ntiles - 1 && (int64_t)prefix + total != n_keys) atomicOr(err, kErrOverflow);
+        }
+    }
+    __syncthreads();
+    const int64_t base = s_prefix;
+    if ((int64_t)base + total > n_keys) {   // never for consistent counts
+        if (threadIdx.x == 0) atomicOr(err, kErrOverflow);
+        return;
+    }
+    // small records: the owning thread
+    if (cnt <= kFusedThreadKeys) {
+        uint32_t row = 0, col = 0;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t bin = (y0 + row) * (uint32_t)bins_x + x0 + col;
+            const int64_t at = base + excl + k;
+            if (rbits) {
+                tile_key[at] = (bin << rbits) | rec;
+            } else {
+                tile_key[at] = bin;
+                tile_val[at] = rec;
+            }
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_hist[p][(bin >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+            if (++col == w) { col = 0; ++row; }
+        }
+    }
+    // large records: one warp each
+    const int lane = threadIdx.x & 31;
+    const uint32_t nbig = s_nbig;
+    for (uint32_t b = threadIdx.x >> 5; b < nbig; b += kEmitThreads / 32) {
+        const uint32_t t = s_big[b];
+        const uint2 rr = s_rect[t];
+        const uint32_t bx0 = rr.x & 0xffffu, by0 = rr.x >> 16, bw = rr.y, bc = s_cnt[t];
+        const uint32_t brec = s_rec[t];
+        const int64_t at0 = base + s_off[t];
+        uint32_t row = lane / bw, col = lane - row * bw;
+        const uint32_t drow = 32u / bw, dcol = 32u - drow * bw;
+        for (uint32_t k = lane; k < bc; k += 32) {
+            const uint32_t bin = (by0 + row) * (uint32_t)bins_x + bx0 + col;
+            if (rbits) {
+                tile_key[at0 + k] = (bin << rbits) | brec;
+            } else {
+                tile_key[at0 + k] = bin;
+                tile_val[at0 + k] = brec;
+            }
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_hist[p][(bin >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+            row += drow;
+            col += dcol;
+            if (col >= bw) { col -= bw; ++row; }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < passes * 256; j += kEmitThreads) {
+        const uint32_t c = (&s_hist[0][0])[j];
+        if (c) atomicAdd(digit_hist + j, c);
+    }
+}
+
 // exclusive scan of each pass's 256-bin digit histogram, in place
 __global__ void digit_scan_kernel(uint32_t* hist) {
     __shared__ uint32_t s_scan[33];
@@ -260,12 +380,20 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
     const int32_t tiles_x = bins_x;   // the emit kernels index bins as tiles
     int64_t nb = (n_vis + kEmitThreads - 1) / kEmitThreads;
     if (nb == 0) return;
-    emit_offsets_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, koff, srec,
-                                                              srect, bin_log2, status, tile_counter, err);
-    if (n_keys == 0) return;
     const int P = (key_bits + 7) / 8;
     const int last_bits = key_bits - 8 * (P - 1);
     const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
+    if (n_keys > 0 && n_keys < kEmitWarpMinKeys * n_vis && bin_log2 > 0) {
+        // coarse bins: a few keys per record, one fused pass
+        emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, bin_log2, bins_x,
+                                                                n_keys, tile_key, tile_val, rbits, P, last_mask,
+                                                                digit_hist, status, tile_counter, err);
+        digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
+        return;
+    }
+    emit_offsets_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, koff, srec,
+                                                              srect, bin_log2, status, tile_counter, err);
+    if (n_keys == 0) return;
     if (n_keys >= kEmitWarpMinKeys * n_vis) {
         // records average a warp's worth of keys or more: one warp per record
         const unsigned grid = (unsigned)std::min<int64_t>((n_vis + kEmitThreads / 32 - 1) / (kEmitThreads / 32),
@@ -280,6 +408,16 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
                                                               digit_hist, err);
     }
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
+}
+
+void launch_digit_scan(uint32_t* hist, int passes, cudaStream_t s) {
+    if (passes > 0) digit_scan_kernel<<<passes, 256, 0, s>>>(hist);
+}
+
+int emit_launches(int64_t n_vis, int64_t n_keys, int bin_log2) {
+    if (n_vis == 0) return 0;
+    if (n_keys > 0 && n_keys < kEmitWarpMinKeys * n_vis && bin_log2 > 0) return 2;
+    return n_keys > 0 ? 3 : 1;
 }
 
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,

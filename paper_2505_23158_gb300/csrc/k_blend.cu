@@ -14,6 +14,8 @@
 // ballots which of the 128 records touch the tile (the same test as tile
 // binning: the record's tile rect contains the tile) and the walk visits
 // only those, so a tile composites exactly its own list, in the same order.
+// This walk is branch-free: a pixel that stops gets T = 0, which makes every
+// later step a no-op.
 //
 // Per pixel and Gaussian (record = mean', upper-triangular U with
 // U^T U = (1/2) log2(e) Sigma'^-1, opacity o', colour):
@@ -52,10 +54,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// one record of the batch against one pixel (Eq. 1)
+// one record of the batch against one pixel (Eq. 1); kCount: count the
+// evaluation and, if the pixel composites it, the composited pair
+template <bool kCount, bool kLast>
 __device__ __forceinline__ void blend_px(const float4 a, const float4 bb, const float cz, float dx,
                                          float py, float& T, float& C0, float& C1, float& C2,
-                                         bool& done, uint32_t& last, uint32_t pos) {
+                                         bool& done, uint32_t& last, uint32_t pos, uint32_t& n_eval,
+                                         uint32_t& n_used) {
+    if (kCount) ++n_eval;
     const float dy = py - a.y;
     const float t = fmaf(a.z, dx, a.w * dy);
     const float wq = bb.x * dy;
@@ -71,12 +77,40 @@ __device__ __forceinline__ void blend_px(const float4 a, const float4 bb, const 
             C1 = fmaf(wgt, bb.w, C1);
             C2 = fmaf(wgt, cz, C2);
             T = Tn;
-            last = pos;
+            if (kLast) last = pos;
+            if (kCount) ++n_used;
         }
     }
 }
 
-template <bool kBins>
+// The same step without branches, for walks that need neither the final
+// transmittance nor list positions: a pixel that stops gets T = 0, after
+// which every step leaves it unchanged (its weight is 0 and T stays 0).
+// While T > 0 the arithmetic and decisions are blend_px's.
+template <bool kCount>
+__device__ __forceinline__ void blend_px_flat(const float4 a, const float4 bb, const float cz, float dx,
+                                              float py, float& T, float& C0, float& C1, float& C2,
+                                              uint32_t& n_eval, uint32_t& n_used) {
+    const float dy = py - a.y;
+    const float t = fmaf(a.z, dx, a.w * dy);
+    const float wq = bb.x * dy;
+    const float q = fmaf(t, t, wq * wq);
+    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+    const float Tn = T * (1.f - alpha);
+    const bool ok = alpha >= (1.0f / 255.0f);
+    const bool go = ok && !(Tn < 1e-4f);
+    const float wgt = go ? T * alpha : 0.f;
+    C0 = fmaf(wgt, bb.z, C0);
+    C1 = fmaf(wgt, bb.w, C1);
+    C2 = fmaf(wgt, cz, C2);
+    if (kCount) {
+        n_eval += T > 0.f ? 1u : 0u;
+        n_used += go ? 1u : 0u;
+    }
+    T = go ? Tn : (ok ? 0.f : T);
+}
+
+template <bool kBins, bool kCount = false>
 __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     __shared__ float4 sa[2][kBlendBatch];
     __shared__ float4 sb[2][kBlendBatch];
@@ -109,10 +143,15 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     const int n = (int)(rg.y - rg.x);
     const int nb = (n + kBlendBatch - 1) / kBlendBatch;
 
-    float T0 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f;
-    float T1 = 1.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+    // the binned walk marks a pixel outside the image or stopped by T = 0
+    float T0 = (kBins && !in0) ? 0.f : 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f;
+    float T1 = (kBins && !in1) ? 0.f : 1.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
     bool done0 = !in0, done1 = !in1;
     uint32_t last0 = 0, last1 = 0;
+    uint32_t n_eval = 0, n_used = 0;   // counting mode only
+    // per-pixel list positions are wanted only by the adjoint, whose frames
+    // always have per-tile lists
+    constexpr bool kLast = !kBins;
 
     if (nb > 0) {
         if (tid < n) {
@@ -154,21 +193,25 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                 }
                 m[w] = __ballot_sync(0xffffffffu, hit);
             }
-            if (!__all_sync(0xffffffffu, done0 && done1)) {
-#pragma unroll
-                for (int w = 0; w < kBlendBatch / 32; ++w) {
-                    uint32_t mm = m[w];
-                    while (mm && !(done0 && done1)) {
-                        const int k = w * 32 + __ffs(mm) - 1;
-                        mm &= mm - 1u;
+            // flat walk over the hits, 8 batch positions at a time, the warp
+            // leaving once all its pixels have stopped (T = 0)
+            if (!__all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) {
+#pragma unroll 1
+                for (int g = 0; g < kBlendBatch / 8; ++g) {
+                    const uint32_t mw = g < 8 ? (g < 4 ? m[0] : m[1]) : (g < 12 ? m[2] : m[3]);
+                    uint32_t mb = (mw >> (8 * (g & 3))) & 0xffu;
+                    if (!mb) continue;
+                    do {
+                        const int k = g * 8 + __ffs(mb) - 1;
+                        mb &= mb - 1u;
                         const float4 a = sa[buf][k];
                         const float4 bb = sb[buf][k];
                         const float cz = sc[buf][k];
                         const float dx = pxf - a.x;
-                        const uint32_t pos = (uint32_t)(b * kBlendBatch + k + 1);
-                        if (!done0) blend_px(a, bb, cz, dx, py0, T0, C00, C01, C02, done0, last0, pos);
-                        if (!done1) blend_px(a, bb, cz, dx, py1, T1, C10, C11, C12, done1, last1, pos);
-                    }
+                        blend_px_flat<kCount>(a, bb, cz, dx, py0, T0, C00, C01, C02, n_eval, n_used);
+                        blend_px_flat<kCount>(a, bb, cz, dx, py1, T1, C10, C11, C12, n_eval, n_used);
+                    } while (mb);
+                    if (__all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) break;
                 }
             }
         } else if (!__all_sync(0xffffffffu, done0 && done1)) {
@@ -178,34 +221,50 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                 const float cz = sc[buf][k];
                 const float dx = pxf - a.x;
                 const uint32_t pos = (uint32_t)(b * kBlendBatch + k + 1);
-                if (!done0) blend_px(a, bb, cz, dx, py0, T0, C00, C01, C02, done0, last0, pos);
-                if (!done1) blend_px(a, bb, cz, dx, py1, T1, C10, C11, C12, done1, last1, pos);
+                if (!done0)
+                    blend_px<kCount, kLast>(a, bb, cz, dx, py0, T0, C00, C01, C02, done0, last0, pos, n_eval, n_used);
+                if (!done1)
+                    blend_px<kCount, kLast>(a, bb, cz, dx, py1, T1, C10, C11, C12, done1, last1, pos, n_eval, n_used);
             }
         }
-        if (__syncthreads_count(done0 && done1) == kBlendThreads) break;
+        if (kBins) {
+            if (__syncthreads_count(T0 == 0.f && T1 == 0.f) == kBlendThreads) break;
+        } else if (__syncthreads_count(done0 && done1) == kBlendThreads) {
+            break;
+        }
     }
     cp_async_wait0();
+    if (kCount) {
+        for (int off = 16; off > 0; off >>= 1) {
+            n_eval += __shfl_xor_sync(0xffffffffu, n_eval, off);
+            n_used += __shfl_xor_sync(0xffffffffu, n_used, off);
+        }
+        if (lane == 0 && f.pairs) {
+            atomicAdd(f.pairs, (unsigned long long)n_eval);
+            atomicAdd(f.pairs + 1, (unsigned long long)n_used);
+        }
+    }
     if (in0) {
         const int64_t pix = (int64_t)y0 * width + x;
         out_rgb[3 * pix + 0] = C00;
         out_rgb[3 * pix + 1] = C01;
         out_rgb[3 * pix + 2] = C02;
-        if (out_T) out_T[pix] = T0;
-        if (out_last) out_last[pix] = last0;
+        if (!kBins && out_T) out_T[pix] = T0;
+        if (kLast && out_last) out_last[pix] = last0;
     }
     if (in1) {
         const int64_t pix = (int64_t)y1 * width + x;
         out_rgb[3 * pix + 0] = C10;
         out_rgb[3 * pix + 1] = C11;
         out_rgb[3 * pix + 2] = C12;
-        if (out_T) out_T[pix] = T1;
-        if (out_last) out_last[pix] = last1;
+        if (!kBins && out_T) out_T[pix] = T1;
+        if (kLast && out_last) out_last[pix] = last1;
     }
 }
 
-template <bool kBins>
+template <bool kBins, bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) {
-    blend_tile<kBins>(f, blockIdx.x);
+    blend_tile<kBins, kCount>(f, blockIdx.x);
 }
 
 // One launch for the tiles of several frames (a serving step): CTA b
@@ -326,11 +385,13 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
     f.vmask = vmask;
     f.n_keys = (uint32_t)n_keys;
     f.n_rec = (uint32_t)std::max<int64_t>(n_rec, 1);
-    f.bin_log2 = rec_rect ? bin_log2 : 0;
+    // the binned walk keeps neither the final transmittance nor positions
+    f.bin_log2 = (rec_rect && !o.T_final && !o.last) ? bin_log2 : 0;
     f.bins_x = (cam.tiles_x + (1 << f.bin_log2) - 1) >> f.bin_log2;
     f.ranges = ranges;
     f.tile_val = tile_val;
     f.rec_rect = rec_rect;
+    f.pairs = nullptr;
     f.rec_a = rec_a;
     f.rec_b = rec_b;
     f.rec_c = rec_c;
@@ -342,14 +403,22 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
 
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
-                  int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2, const uint2* rec_rect) {
-    const BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o,
-                                     bin_log2, rec_rect);
+                  int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2, const uint2* rec_rect,
+                  unsigned long long* pairs) {
+    BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o,
+                               bin_log2, rec_rect);
     if (f.ntiles == 0) return;
-    if (f.bin_log2 > 0)
-        blend_kernel<true><<<f.ntiles, kBlendThreads, 0, s>>>(f);
-    else
-        blend_kernel<false><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+    f.pairs = pairs;
+    if (pairs) {   // counting variant (profiling), same walk
+        if (f.bin_log2 > 0)
+            blend_kernel<true, true><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+        else
+            blend_kernel<false, true><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+    } else if (f.bin_log2 > 0) {
+        blend_kernel<true, false><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+    } else {
+        blend_kernel<false, false><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+    }
 }
 
 void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s) {

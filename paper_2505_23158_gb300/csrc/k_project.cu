@@ -175,7 +175,10 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_scan[33];
     __shared__ unsigned long long s_keys, s_bkeys;
+    __shared__ uint32_t s_dh[4][256];   // depth-key digit counts (the depth sort's histogram)
     if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_keys = 0ull; s_bkeys = 0ull; }
+    if (P.o.depth_hist)
+        for (int j = threadIdx.x; j < 4 * 256; j += kProjThreads) (&s_dh[0][0])[j] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t ntiles = (uint32_t)((P.n_active + kProjThreads - 1) / kProjThreads);
@@ -233,14 +236,23 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         }
     }
 
-    // ---- compaction of visible records (gid order preserved)
+    // ---- compaction of visible records (gid order preserved).  The CTA's
+    // count is published as soon as it is known and the look-back comes
+    // after the attribute work below, so successors rarely wait on it and
+    // this CTA's own look-back finds its predecessors' counts in place.
     uint32_t total;
     uint32_t excl = block_exclusive_scan(vis ? 1u : 0u, s_scan, &total);
+    if (threadIdx.x == 0) st_volatile(status + tile, (tile == 0 ? kStInc : kStAgg) | total);
     uint32_t nk = vis ? (rx1 - rx0 + 1) * (ry1 - ry0 + 1) : 0u;
     {
         uint32_t wsum = nk;
         for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
+    }
+    if (vis && P.o.depth_hist) {
+        const uint32_t zb = __float_as_uint(z);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_dh[p][(zb >> (8 * p)) & 0xffu], 1u);
     }
     const int bl = P.o.bin_log2;
     if (bl > 0) {   // keys of the coarse bins (squares of 2^bl tiles)
@@ -248,12 +260,49 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_bkeys, (unsigned long long)wsum);
     }
+
+    float u00 = 0.f, u01 = 0.f, u11 = 0.f;
+    float rgb[3] = {0.5f, 0.5f, 0.5f};
+    if (vis) {
+        // ---- inverse 2D covariance in Cholesky form, with (1/2) log2(e)
+        // folded in: alpha = o' * 2^-((u00 dx + u01 dy)^2 + (u11 dy)^2).  The
+        // determinant uses the Cauchy-Binet sum of squared 2x2 minors, which
+        // has no cancellation (Sigma' = B B^T + 0.3 I).
+        const float aB = B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2];
+        const float cB = B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2];
+        const float bB = B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2];
+        const float m01 = fmaf(B0[0], B1[1], -B0[1] * B1[0]);
+        const float m02 = fmaf(B0[0], B1[2], -B0[2] * B1[0]);
+        const float m12 = fmaf(B0[1], B1[2], -B0[2] * B1[1]);
+        const float D = m01 * m01 + m02 * m02 + m12 * m12 + 0.3f * (aB + cB) + 0.09f;
+        const float c = cB + 0.3f;
+        const float rD = 1.0f / sqrtf(D);
+        u11 = sqrtf(kHalfLog2e / c);
+        u00 = u11 * c * rD;
+        u01 = -u11 * bB * rD;
+
+        // ---- colour: real SH up to degree 3 at the unit direction camera -> mean
+        float dx = d0 - cam.clo[0], dy = d1 - cam.clo[1], dz = d2 - cam.clo[2];
+        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis(dx * inv, dy * inv, dz * inv, Y);
+        const int nf = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            if (4 * j >= nf) break;
+            float4 v4 = __ldcs(ssh + (int64_t)j * npad + idx);
+            float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int idx = 4 * j + cc;
+                if (idx < nf) rgb[idx % 3] = fmaf(Y[idx / 3], vv[cc], rgb[idx % 3]);
+            }
+        }
+    }
+
     if (threadIdx.x < 32) {
         uint32_t prefix = 0;
-        if (tile == 0) {
-            if (threadIdx.x == 0) st_volatile(status, kStInc | total);
-        } else {
-            if (threadIdx.x == 0) st_volatile(status + tile, kStAgg | total);
+        if (tile != 0) {
             prefix = warp_lookback(status, tile, err);
             if (threadIdx.x == 0) st_volatile(status + tile, kStInc | (prefix + total));
         }
@@ -267,43 +316,13 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 2), s_keys);
     if (threadIdx.x == 0 && s_bkeys)
         atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 4), s_bkeys);
-    if (!vis) return;
-
-    // ---- inverse 2D covariance in Cholesky form, with (1/2) log2(e) folded
-    // in: alpha = o' * 2^-((u00 dx + u01 dy)^2 + (u11 dy)^2).  The
-    // determinant uses the Cauchy-Binet sum of squared 2x2 minors, which has
-    // no cancellation (Sigma' = B B^T + 0.3 I).
-    const float aB = B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2];
-    const float cB = B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2];
-    const float bB = B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2];
-    const float m01 = fmaf(B0[0], B1[1], -B0[1] * B1[0]);
-    const float m02 = fmaf(B0[0], B1[2], -B0[2] * B1[0]);
-    const float m12 = fmaf(B0[1], B1[2], -B0[2] * B1[1]);
-    const float D = m01 * m01 + m02 * m02 + m12 * m12 + 0.3f * (aB + cB) + 0.09f;
-    const float c = cB + 0.3f;
-    const float rD = 1.0f / sqrtf(D);
-    const float u11 = sqrtf(kHalfLog2e / c);
-    const float u00 = u11 * c * rD;
-    const float u01 = -u11 * bB * rD;
-
-    // ---- colour: real SH up to degree 3 at the unit direction camera -> mean
-    float dx = d0 - cam.clo[0], dy = d1 - cam.clo[1], dz = d2 - cam.clo[2];
-    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float Y[16];
-    sh_basis(dx * inv, dy * inv, dz * inv, Y);
-    const int nf = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
-    float rgb[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        if (4 * j >= nf) break;
-        float4 v4 = __ldcs(ssh + (int64_t)j * npad + idx);
-        float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const int idx = 4 * j + cc;
-            if (idx < nf) rgb[idx % 3] = fmaf(Y[idx / 3], vv[cc], rgb[idx % 3]);
+    if (P.o.depth_hist && total) {
+        for (int j = threadIdx.x; j < 4 * 256; j += kProjThreads) {
+            const uint32_t c = (&s_dh[0][0])[j];
+            if (c) atomicAdd(P.o.depth_hist + j, c);
         }
     }
+    if (!vis) return;
     const uint32_t pos = s_prefix + excl;
     P.o.rec_a[pos] = make_float4(mxp, myp, u00, u01);
     P.o.rec_b[pos] = make_float4(u11, o, fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));

@@ -170,6 +170,7 @@ lodge_status second_slot(lodge_ctx* ctx, Slot** out) {
     if (!sl->own) CUDA_TRY(cudaStreamCreateWithFlags(&sl->own, cudaStreamNonBlocking));
     if (!sl->fence) CUDA_TRY(cudaEventCreateWithFlags(&sl->fence, cudaEventDisableTiming));
     sl->prof_on = ctx->slots[0]->prof_on;
+    sl->prof_count = ctx->slots[0]->prof_count;
     *out = sl;
     return LODGE_OK;
 }
@@ -547,6 +548,11 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     po.depth_key = ws.dkey.as<uint32_t>();
     po.depth_val = ws.dval.as<uint32_t>();
     po.counts = sl.d_small + kSmProj;
+    // digit counts: [0, 1024) the bin sort's (from K4), [1024, 2048) the
+    // depth sort's (from K3)
+    TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 8 * 256, s));
+    CUDA_TRY(cudaMemsetAsync(ws.doffs.p, 0, sizeof(uint32_t) * 8 * 256, s));
+    po.depth_hist = ws.doffs.as<uint32_t>() + 4 * 256;
     // frames kept for the adjoint and the importance walk use per-tile lists
     // (their per-pixel positions index the tile's own list)
     const int bl = (save || importance) ? 0 : ctx->bin_log2;
@@ -580,9 +586,11 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     const int tbits = bits_for((uint32_t)std::max<int64_t>(nbins - 1, 0));
     TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_bkeys, tbits)), s));
     prof_begin(sl, LODGE_STAGE_DEPTH_SORT, s);
+    if (n_vis > 1) launch_digit_scan(po.depth_hist, 4, s);
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
-                             ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s);
-    prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, onesweep_launches(n_vis, 32, false));
+                             ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s,
+                             po.depth_hist);
+    prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, (n_vis > 1 ? 1 : 0) + onesweep_launches(n_vis, 32, true));
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
 
@@ -598,8 +606,6 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         TRY(ensure(ctx, ws.tval, sizeof(uint32_t) * nk1, s));
         TRY(ensure(ctx, ws.tval2, sizeof(uint32_t) * nk1, s));
     }
-    TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 4 * 256, s));
-    CUDA_TRY(cudaMemsetAsync(ws.doffs.p, 0, sizeof(uint32_t) * 4 * 256, s));
     TRY(ensure(ctx, ws.koff, sizeof(uint32_t) * (nv1 + 1), s));
     TRY(ensure(ctx, ws.srec, sizeof(uint32_t) * nv1, s));
     TRY(ensure(ctx, ws.srect, sizeof(uint2) * nv1, s));
@@ -611,7 +617,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
                 ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_bkeys,
                 ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits, ws.doffs.as<uint32_t>(),
                 ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
-    prof_end(sl, LODGE_STAGE_EMIT, s, (n_vis > 0 ? 1 : 0) + (n_bkeys > 0 ? 2 : 0));
+    prof_end(sl, LODGE_STAGE_EMIT, s, emit_launches(n_vis, n_bkeys, bl));
 
     // ---- K6 bin ranges: recorded by the bin sort's last pass (begin by
     // atomic minimum from 0xffffffff, end by atomic maximum from 0); with at
@@ -665,7 +671,9 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
                           d_rgb, ws.iscore.as<uint32_t>(), dsc.n_total, importance, s);
     } else {
         launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_bkeys, ws.rec_a.as<float4>(),
-                     ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s, bl, ws.rec_rect.as<uint2>());
+                     ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s, bl, ws.rec_rect.as<uint2>(),
+                     sl.prof_count ? reinterpret_cast<unsigned long long*>(sl.d_small + kSmPairs) : nullptr);
+        if (sl.prof_count) end_sync = true;   // the counts are read back with the frame
     }
     prof_end(sl, LODGE_STAGE_BLEND, s, job ? 0 : ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
     CUDA_TRY(cudaGetLastError());
@@ -684,6 +692,13 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     sl.prof.bin_keys += n_bkeys;
     if (rbits) sl.prof.packed_keys += n_bkeys;
     sl.prof.bin_sort_passes += n_bkeys > 1 ? (tbits + 7) / 8 : 0;
+    if (sl.prof_count && !job && !importance) {
+        uint64_t pe, pu;
+        std::memcpy(&pe, sl.h_small + kSmPairs, 8);
+        std::memcpy(&pu, sl.h_small + kSmPairs + 2, 8);
+        sl.prof.blend_pairs += (int64_t)pe;
+        sl.prof.blend_pairs_used += (int64_t)pu;
+    }
     sl.prof.visible += n_vis;
     sl.prof.active += na;
     if (st) {
@@ -1747,6 +1762,7 @@ lodge_status lodge_profile_enable(lodge_ctx* ctx, int enable) {
         sl.prof = lodge_profile{};
         for (int k = 0; k < LODGE_NUM_STAGES; ++k) sl.ev_pending[k] = false;
         sl.prof_on = enable != 0;
+        sl.prof_count = enable == 2;
     }
     return LODGE_OK;
 }
@@ -1769,6 +1785,8 @@ lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
         p.packed_keys += q.packed_keys;
         p.bin_keys += q.bin_keys;
         p.bin_sort_passes += q.bin_sort_passes;
+        p.blend_pairs += q.blend_pairs;
+        p.blend_pairs_used += q.blend_pairs_used;
     }
     *out = p;
     return LODGE_OK;

@@ -385,7 +385,7 @@ def test_binned_lists_same_image(ctx, outdoor, torch_cuda, log2):
                 ref = O.render(osc, cam, g_ref, m_ref)
                 compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"bins {log2} pose {i}")
     finally:
-        ctx.set_bin_size(2)
+        ctx.set_bin_size(3)
 
 
 @pytest.mark.parametrize("wh", [(17, 33), (1, 1), (257, 129), (100, 70)])
@@ -403,7 +403,7 @@ def test_binned_lists_ragged_sizes(ctx, plain_loaded, torch_cuda, wh):
             img, _ = ctx.render(sid, FULL, cam)
             assert torch_cuda.equal(img, ref), f"bins {k}"
     finally:
-        ctx.set_bin_size(2)
+        ctx.set_bin_size(3)
 
 
 def test_bin_size_argument_checked(ctx):
@@ -411,4 +411,31 @@ def test_bin_size_argument_checked(ctx):
     for bad in (-1, 4):
         with pytest.raises(LodgeError):
             ctx.set_bin_size(bad)
-    ctx.set_bin_size(2)
+    ctx.set_bin_size(3)
+
+
+@pytest.mark.parametrize("log2", [0, 2])
+def test_counting_mode_pairs(ctx, outdoor, torch_cuda, log2):
+    """Counting mode: the compositing's composited (pixel, Gaussian) pairs
+    equal the oracle's per-pixel contributor counts summed (up to knife-edge
+    pixels), evaluations lie between that and the full per-tile walk, and
+    the image is the plain kernel's."""
+    from paper_2505_23158_gb300.api import CHUNK_BLEND
+    scene, cams, osc, sid = outdoor
+    cam = cams[2]
+    try:
+        ctx.set_bin_size(log2)
+        plain, _ = ctx.render(sid, CHUNK_BLEND, cam)
+        ctx.profile_enable(True, count_pairs=True)
+        img, st = ctx.render(sid, CHUNK_BLEND, cam)
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+    finally:
+        ctx.set_bin_size(3)
+    assert torch_cuda.equal(img, plain)
+    g_ref, m_ref, info = O.active_set(osc, CHUNK_BLEND, cam)
+    ref = O.render(osc, cam, g_ref, m_ref)
+    used_ref = int(ref["ncontrib"].sum())
+    assert used_ref > 0
+    assert abs(prof["blend_pairs_used"] - used_ref) <= max(10, 1e-3 * used_ref), (prof, used_ref)
+    assert prof["blend_pairs_used"] <= prof["blend_pairs"] <= ref["n_pairs_eval"]
