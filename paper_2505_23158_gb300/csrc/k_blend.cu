@@ -10,11 +10,13 @@
 // the batch, and the CTA leaves as soon as all 256 have stopped.
 //
 // With coarse bins (squares of 2^bin_log2 tiles) the tile walks its bin's
-// key list: each batch also stages the records' pixel rects, every warp
-// ballots which of the 128 records touch the tile (the same test as tile
-// binning: the record's tile rect contains the tile) and the walk visits
-// only those, so a tile composites exactly its own list, in the same order.
-// This walk is branch-free: a pixel that stops gets T = 0, which makes every
+// key list: each batch also stages the records' pixel rects, and every warp
+// ballots which of the 128 records have a pixel rect meeting its own 8x8
+// block (such a record's tile rect holds the tile, so it is on the tile's
+// own list) and visits only those, in list order.  A record whose rect
+// misses the block would be skipped by every pixel of it (alpha < 1/255
+// outside the rect), so the image is the per-tile lists' bit for bit.  This
+// walk is branch-free: a pixel that stops gets T = 0, which makes every
 // later step a no-op.
 //
 // Per pixel and Gaussian (record = mean', upper-triangular U with
@@ -134,6 +136,8 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     const int y0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3), y1 = y0 + 4;
     const bool in0 = x < width && y0 < height, in1 = x < width && y1 < height;
     const float pxf = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
+    const uint32_t wx0 = tx * kTile + (warp & 1) * 8, wx1 = wx0 + 7;   // the warp's 8x8 block
+    const uint32_t wy0 = ty * kTile + (warp >> 1) * 8, wy1 = wy0 + 7;
     const uint2* __restrict__ rec_rect = f.rec_rect;
     // a frame of a binned batch launch may still have per-tile lists
     const bool binned = kBins && f.bin_log2 > 0 && rec_rect != nullptr;
@@ -187,9 +191,12 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                 const int k = w * 32 + lane;
                 bool hit = k < cnt;
                 if (hit && binned) {
+                    // the record's pixel rect meets this warp's 8x8 block (so
+                    // its tile rect holds the tile); outside the rect every
+                    // pixel would skip it (alpha < 1/255), so no result changes
                     const uint2 r = sr[buf][k];
-                    hit = ((r.x & 0xffffu) / kTile) <= (uint32_t)tx && ((r.y & 0xffffu) / kTile) >= (uint32_t)tx &&
-                          ((r.x >> 16) / kTile) <= (uint32_t)ty && ((r.y >> 16) / kTile) >= (uint32_t)ty;
+                    hit = (r.x & 0xffffu) <= wx1 && (r.y & 0xffffu) >= wx0 && (r.x >> 16) <= wy1 &&
+                          (r.y >> 16) >= wy0;
                 }
                 m[w] = __ballot_sync(0xffffffffu, hit);
             }

@@ -168,8 +168,11 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
     return true;
 }
 
+// six CTAs per SM (at most 42 registers): the kernel is bound by the
+// latency of its dependent gathers, so resident warps matter more than the
+// few spilled words
 template <bool kBlocks>
-__global__ void __launch_bounds__(kProjThreads)
+__global__ void __launch_bounds__(kProjThreads, 6)
 project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
                uint32_t* __restrict__ err) {
     __shared__ uint32_t s_tile, s_prefix;
