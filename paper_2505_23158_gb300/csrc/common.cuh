@@ -230,12 +230,16 @@ constexpr int64_t sort_scratch_words(int64_t n, int passes) {
 // tile (tile = key >> shift0), the last pass also records each tile's
 // [begin, end) in the output for tiles < range_tiles; .x must start at
 // 0xffffffff and .y at 0 (a tile without keys keeps begin > end).  Not
-// written if n <= 1.
+// written if n <= 1.  d_count: optional device word (u64) holding the number
+// of pairs, at most n; n is then a capacity that sizes the grid and the
+// scratch, tiles past the count exit at once, and digit_offsets must be
+// given (the sort then runs for any count, 0 and 1 included).
 size_t sort_scratch_bytes(int64_t n, int key_bits);
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
                     const uint32_t* digit_offsets = nullptr, bool final_keys = true, int shift0 = 0,
-                    uint2* ranges = nullptr, uint32_t range_tiles = 0);
+                    uint2* ranges = nullptr, uint32_t range_tiles = 0,
+                    const unsigned long long* d_count = nullptr);
 int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
 // K4: emit (bin, record) pairs in depth order.  A bin is a square of
@@ -255,6 +259,16 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
                  int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s);
+// The same emission with the counts on the device (bins of several tiles
+// only, one fused launch plus the digit scan): n_vis_cap and key_cap are
+// capacities (key_tile/tile_val hold key_cap words); d_nvis and d_nkeys
+// (u64) the frame's visible records and bin keys.  A frame whose keys exceed
+// key_cap writes none and sets kErrOverflow.
+void launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
+                         const uint2* rec_rect, int32_t bins_x, int bin_log2, int64_t key_cap,
+                         const unsigned long long* d_nkeys, uint32_t* tile_key, uint32_t* tile_val,
+                         int rbits, int key_bits, uint32_t* digit_hist, uint32_t* status,
+                         uint32_t* tile_counter, uint32_t* err, cudaStream_t s);
 
 int emit_launches(int64_t n_vis, int64_t n_keys, int bin_log2);
 // exclusive scan, in place, of `passes` 256-bin digit histograms (one launch)

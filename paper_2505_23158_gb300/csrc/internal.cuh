@@ -121,6 +121,26 @@ struct Slot {
     // stream after its last kernel, checked at the slot's next sync
     uint32_t* h_tail = nullptr;   // pinned
     bool tail_pending = false;
+    // Frames rendered with their counts left on the device (no mid-frame
+    // sync): scratch is sized by capacities, the bin keys by key_cap (grown
+    // from the frames that did sync).  Each such frame copies its status
+    // words into a pinned ring entry; the slot's harvest reads them.
+    int64_t key_cap = 0;
+    static constexpr int kRing = 32;
+    uint32_t* h_ring = nullptr;   // pinned, kRing x kSmWords
+    int ring_next = 0;
+    struct Pending {
+        int ring = 0;                   // ring entry
+        int frame = 0;                  // index in the caller's list (set by the caller)
+        bool used = false;              // the frame took this path
+        lodge_frame_stats* st = nullptr;
+        int64_t n_active = 0, n_tiles = 0;
+        int A = -1, B = -1;
+        double tA = 1.0, tB = 1.0;
+        bool packed = false;            // bin keys packed with the record
+        int sort_passes = 0;
+    };
+    std::vector<Pending> pending;
     bool prof_on = false;
     bool prof_count = false;   // compositing counts its (pixel, Gaussian) pairs
     lodge_profile prof{};
@@ -199,6 +219,11 @@ struct BatchItem {
     lodge_status status = LODGE_OK;
 };
 lodge_status render_batch(lodge_ctx* ctx, BatchItem* items, int n, int first, cudaStream_t s);
+// select and render one camera on a slot (lodge_capi.cu); pend != null lets
+// a frame of a resident scene skip its mid-frame sync (Slot::Pending)
+lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode, const lodge_camera& cam,
+                        float* d_rgb, cudaStream_t s, Saved* save, lodge_frame_stats* st, bool end_sync,
+                        float* importance, Slot::Pending* pend = nullptr);
 
 // residency (residency.cu)
 lodge_status acquire_block(lodge_ctx* ctx, Slot& sl, Scene* sc, int chunk, cudaStream_t s,

@@ -235,7 +235,16 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
                   uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits,
                   int passes, uint32_t last_mask, uint32_t* __restrict__ digit_hist,
                   uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
-                  uint32_t* __restrict__ err) {
+                  uint32_t* __restrict__ err, const unsigned long long* __restrict__ d_nvis,
+                  const unsigned long long* __restrict__ d_nkeys) {
+    // with device counts, n_vis and n_keys are capacities: the counts decide
+    // which CTAs work and the keys must fit n_keys
+    if (d_nvis) {
+        const unsigned long long c = *d_nvis;
+        if (c < (unsigned long long)n_vis) n_vis = (int64_t)c;
+    }
+    const int64_t key_cap = n_keys;
+    if (d_nkeys) n_keys = (int64_t)*d_nkeys;
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_tile, s_prefix, s_nbig;
     __shared__ uint32_t s_big[kEmitThreads];
@@ -249,6 +258,7 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t ntiles = (uint32_t)((n_vis + kEmitThreads - 1) / kEmitThreads);
+    if (tile >= ntiles) return;   // past the device count (later tiles too)
     const int64_t i = (int64_t)tile * kEmitThreads + threadIdx.x;
     uint32_t cnt = 0, rec = 0, x0 = 0, y0 = 0, w = 1;
     if (i < n_vis) {
@@ -287,7 +297,8 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     }
     __syncthreads();
     const int64_t base = s_prefix;
-    if ((int64_t)base + total > n_keys) {   // never for consistent counts
+    if ((int64_t)base + total > n_keys || (int64_t)base + total > key_cap) {
+        // more keys than counted (never for consistent counts) or than fit
         if (threadIdx.x == 0) atomicOr(err, kErrOverflow);
         return;
     }
@@ -387,7 +398,8 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
         // coarse bins: a few keys per record, one fused pass
         emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, bin_log2, bins_x,
                                                                 n_keys, tile_key, tile_val, rbits, P, last_mask,
-                                                                digit_hist, status, tile_counter, err);
+                                                                digit_hist, status, tile_counter, err, nullptr,
+                                                                nullptr);
         digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
         return;
     }
@@ -407,6 +419,23 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
                                                               tile_key, tile_val, rbits, P, last_mask,
                                                               digit_hist, err);
     }
+    digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
+}
+
+void launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
+                         const uint2* rec_rect, int32_t bins_x, int bin_log2, int64_t key_cap,
+                         const unsigned long long* d_nkeys, uint32_t* tile_key, uint32_t* tile_val,
+                         int rbits, int key_bits, uint32_t* digit_hist, uint32_t* status,
+                         uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
+    const int64_t nb = (n_vis_cap + kEmitThreads - 1) / kEmitThreads;
+    if (nb == 0) return;
+    const int P = (key_bits + 7) / 8;
+    const int last_bits = key_bits - 8 * (P - 1);
+    const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
+    emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, rec_rect, bin_log2, bins_x,
+                                                            key_cap, tile_key, tile_val, rbits, P, last_mask,
+                                                            digit_hist, status, tile_counter, err, d_nvis,
+                                                            d_nkeys);
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
 }
 

@@ -66,7 +66,7 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
               uint32_t dmask, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ status,
               uint32_t* __restrict__ counter, uint32_t* __restrict__ err, uint2* __restrict__ ranges,
-              int range_shift, uint32_t range_tiles) {
+              int range_shift, uint32_t range_tiles, const unsigned long long* __restrict__ d_count) {
     constexpr int kTileN = kSortThreads * kIPT;
     __shared__ uint32_t s_whist[kWarps][kRadix];
     __shared__ uint32_t s_keys[kTileN];
@@ -81,6 +81,11 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (d_count) {   // n is a capacity; the device count (<= n) decides
+        const unsigned long long c = *d_count;
+        if (c < (unsigned long long)n) n = (int64_t)c;
+        if ((int64_t)tile * kTileN >= n) return;   // all later tiles are empty too
+    }
     const int64_t seg = (int64_t)tile * kTileN + (int64_t)warp * 32 * kIPT;
     const int64_t base = seg + lane;
     const int64_t nvalid = n - seg;   // items of this warp's segment that exist (may be <= 0)
@@ -225,13 +230,13 @@ template <bool kWK, bool kV>
 void launch_pass(bool small, int64_t ntiles, const uint32_t* ki, const uint32_t* vi, uint32_t* ko,
                  uint32_t* vo, int64_t n, int shift, uint32_t dm, const uint32_t* off, uint32_t* st,
                  uint32_t* ctr, uint32_t* err, uint2* ranges, int range_shift, uint32_t range_tiles,
-                 cudaStream_t s) {
+                 const unsigned long long* d_count, cudaStream_t s) {
     if (small)
         onesweep_pass<kSmallIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles);
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles, d_count);
     else
         onesweep_pass<kSortIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles);
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles, d_count);
 }
 
 }  // namespace
@@ -243,9 +248,10 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
                     const uint32_t* digit_offsets, bool final_keys, int shift0, uint2* ranges,
-                    uint32_t range_tiles) {
+                    uint32_t range_tiles, const unsigned long long* d_count) {
     const int P = passes_for(key_bits);
-    if (n <= 1 || P == 0) return 0;
+    if (P == 0 || (d_count ? n < 1 : n <= 1)) return 0;
+    if (d_count && !digit_offsets) return 0;   // device counts need supplied digit offsets
     const bool small = sort_tile_for(n) == kSortTileSmall;
     const int64_t ntiles = (n + sort_tile_for(n) - 1) / sort_tile_for(n);
     const bool values = vals != nullptr;
@@ -273,10 +279,10 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
         const int sh = shift0 + 8 * p;
         uint2* rg = p == P - 1 ? ranges : nullptr;
         if (values) {
-            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, s);
-            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, s);
+            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, s);
+            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, s);
         } else {
-            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, s);
+            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, s);
         }
         std::swap(ki, ko);
         std::swap(vi, vo);

@@ -185,6 +185,7 @@ lodge_status create_slot(lodge_ctx* ctx, Slot** out) {
     CUDA_TRY(cudaMemset(sl->d_small, 0, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMallocHost((void**)&sl->h_small, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMallocHost((void**)&sl->h_tail, sizeof(uint32_t) * kSmWords));
+    CUDA_TRY(cudaMallocHost((void**)&sl->h_ring, sizeof(uint32_t) * kSmWords * Slot::kRing));
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
         CUDA_TRY(cudaEventCreate(&sl->ev_beg[k]));
         CUDA_TRY(cudaEventCreate(&sl->ev_end[k]));
@@ -204,6 +205,7 @@ static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
     if (sl.d_small) cudaFree(sl.d_small);
     if (sl.h_small) cudaFreeHost(sl.h_small);
     if (sl.h_tail) cudaFreeHost(sl.h_tail);
+    if (sl.h_ring) cudaFreeHost(sl.h_ring);
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
         if (sl.ev_beg[k]) cudaEventDestroy(sl.ev_beg[k]);
         if (sl.ev_end[k]) cudaEventDestroy(sl.ev_end[k]);
@@ -515,10 +517,14 @@ static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
 // importance[gid] (n_total floats) to each Gaussian's largest weight.
 // job != null: stop before compositing and describe it in *job (the caller
 // composites a batch of frames with one launch and then syncs their slots).
+// pend != null allows the frame to run without its mid-frame sync (counts
+// left on the device, scratch sized by capacities; see Slot::Pending): it
+// then sets pend->used, appends *pend to the slot's pending list, and its
+// stats and profile counts are taken when the slot is harvested.
 static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, const Active& act,
                                  const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
                                  lodge_frame_stats* st, bool end_sync, float* importance = nullptr,
-                                 BlendFrame* job = nullptr) {
+                                 BlendFrame* job = nullptr, Slot::Pending* pend = nullptr) {
     Workspace& ws = sl.ws;
     TRY(check_cam(c));
     DevCamera cam = make_cam(c);
@@ -557,23 +563,41 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     // (their per-pixel positions index the tile's own list)
     const int bl = (save || importance) ? 0 : ctx->bin_log2;
     po.bin_log2 = bl;
+    // no mid-frame sync: plain coarse-binned frames once the slot knows a key
+    // capacity (the fused emission needs bins of several tiles)
+    const bool deferred = pend && !save && !importance && !job && !sl.prof_count && bl > 0 &&
+                          sl.key_cap > 0 && na > 0 && (int)sl.pending.size() < Slot::kRing;
+    if (pend) pend->used = false;
     prof_begin(sl, LODGE_STAGE_PROJECT, s);
     launch_project(dsc, cam, act.list, na, (float)act.tA, (float)act.tB, po,
                    ws.status.as<uint32_t>(), sl.d_small + kSmCtrProj, sl.d_small + kSmErr, s,
                    act.blocks ? &act.src : nullptr);
     prof_end(sl, LODGE_STAGE_PROJECT, s, na > 0 ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
-    TRY(sync_slot(ctx, sl, s));
-    const int64_t n_vis = sl.h_small[kSmProj];
-    uint64_t nk64;
-    std::memcpy(&nk64, sl.h_small + kSmProj + 2, 8);
-    const int64_t n_keys = (int64_t)nk64;
-    if (n_keys >= (1ll << 30)) return fail(LODGE_E_OVERFLOW, "%lld tile keys exceed 2^30", (long long)n_keys);
-    // key lists per bin: the tile itself (bl = 0) or a square of 2^bl tiles
-    int64_t n_bkeys = n_keys;
-    if (bl > 0) {
-        std::memcpy(&nk64, sl.h_small + kSmProj + 4, 8);
-        n_bkeys = (int64_t)nk64;
+    int64_t n_vis = 0, n_keys = 0, n_bkeys = 0;
+    // device counts (u64 words: the visible count's high word stays 0)
+    const unsigned long long* d_nvis = nullptr;
+    const unsigned long long* d_nbk = nullptr;
+    if (deferred) {
+        n_vis = na;              // capacities
+        n_bkeys = sl.key_cap;
+        d_nvis = reinterpret_cast<const unsigned long long*>(sl.d_small + kSmProj);
+        d_nbk = reinterpret_cast<const unsigned long long*>(sl.d_small + kSmProj + 4);
+    } else {
+        TRY(sync_slot(ctx, sl, s));
+        n_vis = sl.h_small[kSmProj];
+        uint64_t nk64;
+        std::memcpy(&nk64, sl.h_small + kSmProj + 2, 8);
+        n_keys = (int64_t)nk64;
+        if (n_keys >= (1ll << 30)) return fail(LODGE_E_OVERFLOW, "%lld tile keys exceed 2^30", (long long)n_keys);
+        // key lists per bin: the tile itself (bl = 0) or a square of 2^bl tiles
+        n_bkeys = n_keys;
+        if (bl > 0) {
+            std::memcpy(&nk64, sl.h_small + kSmProj + 4, 8);
+            n_bkeys = (int64_t)nk64;
+            // capacity for later frames of this slot that skip the sync
+            sl.key_cap = std::max<int64_t>(sl.key_cap, n_bkeys + n_bkeys / 2 + 65536);
+        }
     }
     const int32_t bins_x = (cam.tiles_x + (1 << bl) - 1) >> bl;
     const int32_t bins_y = (cam.tiles_y + (1 << bl) - 1) >> bl;
@@ -589,7 +613,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     if (n_vis > 1) launch_digit_scan(po.depth_hist, 4, s);
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
                              ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s,
-                             po.depth_hist);
+                             po.depth_hist, true, 0, nullptr, 0, d_nvis);
     prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, (n_vis > 1 ? 1 : 0) + onesweep_launches(n_vis, 32, true));
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
@@ -613,16 +637,23 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
     CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
     prof_begin(sl, LODGE_STAGE_EMIT, s);
-    launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), bins_x, bl,
-                ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_bkeys,
-                ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits, ws.doffs.as<uint32_t>(),
-                ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
-    prof_end(sl, LODGE_STAGE_EMIT, s, emit_launches(n_vis, n_bkeys, bl));
+    if (deferred) {
+        launch_emit_counted(rs.as<uint32_t>(), n_vis, d_nvis, ws.rec_rect.as<uint2>(), bins_x, bl, n_bkeys,
+                            d_nbk, ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits,
+                            ws.doffs.as<uint32_t>(), ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit,
+                            sl.d_small + kSmErr, s);
+    } else {
+        launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), bins_x, bl,
+                    ws.koff.as<uint32_t>(), ws.srec.as<uint32_t>(), ws.srect.as<uint2>(), n_bkeys,
+                    ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits, ws.doffs.as<uint32_t>(),
+                    ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
+    }
+    prof_end(sl, LODGE_STAGE_EMIT, s, deferred ? 2 : emit_launches(n_vis, n_bkeys, bl));
 
     // ---- K6 bin ranges: recorded by the bin sort's last pass (begin by
     // atomic minimum from 0xffffffff, end by atomic maximum from 0); with at
     // most one key the sort does not run and K6 scans the key list instead
-    const bool fused_ranges = n_bkeys > 1;
+    const bool fused_ranges = deferred || n_bkeys > 1;
     TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(nbins, 1), s));
     CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)nbins, s));
     if (fused_ranges && nbins)
@@ -633,7 +664,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), rbits ? nullptr : ws.tval.as<uint32_t>(),
                              ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_bkeys,
                              tbits, ws.sort.p, sl.d_small + kSmErr, s, ws.doffs.as<uint32_t>(), true, rbits,
-                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins);
+                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins, d_nbk);
     prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_bkeys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
@@ -677,6 +708,26 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     }
     prof_end(sl, LODGE_STAGE_BLEND, s, job ? 0 : ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
     CUDA_TRY(cudaGetLastError());
+    if (deferred) {
+        // status words and counts into the slot's ring; read at its harvest
+        const int ring = sl.ring_next;
+        sl.ring_next = (sl.ring_next + 1) % Slot::kRing;
+        CUDA_TRY(cudaMemcpyAsync(sl.h_ring + (size_t)ring * kSmWords, sl.d_small, sizeof(uint32_t) * kSmWords,
+                                 cudaMemcpyDeviceToHost, s));
+        pend->ring = ring;
+        pend->used = true;
+        pend->st = st;
+        pend->n_active = na;
+        pend->n_tiles = ntiles_img;
+        pend->A = act.A;
+        pend->B = act.B;
+        pend->tA = act.tA;
+        pend->tB = act.tB;
+        pend->packed = rbits != 0;
+        pend->sort_passes = (tbits + 7) / 8;
+        sl.pending.push_back(*pend);
+        return LODGE_OK;
+    }
     if (job) {
         // the caller syncs after the batch launch
     } else if (end_sync || save) {
@@ -732,17 +783,72 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     return LODGE_OK;
 }
 
+// Wait for a slot's stream and take the status words and counts of its
+// deferred frames (stats, profile).  A frame whose bin keys outgrew the
+// slot's capacity wrote no keys: the capacity grows and the frame's index is
+// appended to *redo, to be rendered again with its mid-frame sync.
+static lodge_status harvest(lodge_ctx* ctx, Slot& sl, cudaStream_t s, std::vector<int>* redo) {
+    (void)ctx;
+    if (sl.pending.empty()) return LODGE_OK;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    prof_collect(sl);
+    lodge_status r = LODGE_OK;
+    for (const Slot::Pending& p : sl.pending) {
+        const uint32_t* w = sl.h_ring + (size_t)p.ring * kSmWords;
+        const uint32_t err = w[kSmErr];
+        uint64_t nk, nb;
+        std::memcpy(&nk, w + kSmProj + 2, 8);
+        std::memcpy(&nb, w + kSmProj + 4, 8);
+        const int64_t n_vis = w[kSmProj];
+        // keep the capacity half a frame ahead of the largest seen
+        sl.key_cap = std::max<int64_t>(sl.key_cap, (int64_t)(nb + nb / 2 + 65536));
+        if (err & kErrOverflow) {
+            sl.prof.redone += 1;
+            if (redo) redo->push_back(p.frame);
+            continue;
+        }
+        if (r == LODGE_OK && (err & kErrTimeout))
+            r = fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
+        if (r == LODGE_OK && (err & kErrBadIndex))
+            r = fail(LODGE_E_INVALID, "out-of-range index in an active list (status 0x%x)", err);
+        sl.prof.frames += 1;
+        sl.prof.keys += (int64_t)nk;
+        sl.prof.bin_keys += (int64_t)nb;
+        if (p.packed) sl.prof.packed_keys += (int64_t)nb;
+        sl.prof.bin_sort_passes += nb > 1 ? p.sort_passes : 0;
+        sl.prof.visible += n_vis;
+        sl.prof.active += p.n_active;
+        if (p.st) {
+            p.st->n_active = p.n_active;
+            p.st->n_visible = n_vis;
+            p.st->n_keys = (int64_t)nk;
+            p.st->n_tiles = p.n_tiles;
+            p.st->chunk_a = p.A;
+            p.st->chunk_b = p.B;
+            p.st->t_a = p.tA;
+            p.st->t_b = p.tB;
+        }
+    }
+    sl.pending.clear();
+    return r;
+}
+
 // Select and render one camera of a scene on a slot; blocks of streamed
-// scenes are held for the frame and released after it.
+// scenes are held for the frame and released after it.  pend: see
+// render_frame (resident scenes only).
 lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
                         const lodge_camera& cam, float* d_rgb, cudaStream_t s, Saved* save,
-                        lodge_frame_stats* st, bool end_sync, float* importance) {
+                        lodge_frame_stats* st, bool end_sync, float* importance, Slot::Pending* pend) {
     Active act;
     lodge_status r = select_active(ctx, sl, sc, mode, cam, s, &act);
     // blocks of a streamed scene are released after the frame: wait for it
-    if (sc->residency == kStreamed) end_sync = true;
+    if (sc->residency == kStreamed) {
+        end_sync = true;
+        pend = nullptr;
+    }
+    if (pend) pend->used = false;
     if (r == LODGE_OK)
-        r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st, end_sync, importance);
+        r = render_frame(ctx, sl, sc->dev, act, cam, d_rgb, s, save, st, end_sync, importance, nullptr, pend);
     if (sc->residency == kStreamed) {
         if (r != LODGE_OK) cudaStreamSynchronize(s);
         release_blocks(ctx, sl);
@@ -1378,7 +1484,23 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
         CUDA_TRY(cudaEventRecord(sl1->fence, s));
         CUDA_TRY(cudaStreamWaitEvent(s1, sl1->fence, 0));
     }
-    size_t off = 0;
+    // Frames of a resident scene that are not kept for the adjoint run
+    // without their mid-frame sync once their slot knows a key capacity:
+    // their counts stay on the device and are read when the slot is
+    // harvested (when its ring is full and at the end of the call).
+    const bool defer = !save_for_backward && sc->residency == kResident;
+    std::vector<size_t> offs((size_t)n_cams + 1, 0);
+    for (int i = 0; i < n_cams; ++i) offs[i + 1] = offs[i] + (size_t)cams[i].width * cams[i].height * 3;
+    std::vector<int> redo;
+    auto drain = [&]() {   // after a failure: nothing of this call stays in flight
+        for (Slot* q : {&sl0, sl1}) {
+            if (!q) continue;
+            cudaStream_t qs = q == &sl0 ? s : s1;
+            if (q->tail_pending || !q->pending.empty()) cudaStreamSynchronize(qs);
+            q->tail_pending = false;
+            q->pending.clear();
+        }
+    };
     for (int i = 0; i < n_cams; ++i) {
         std::unique_ptr<Saved> sv;
         if (save_for_backward) sv.reset(new Saved());
@@ -1387,18 +1509,17 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
         // consecutive frames of one call are not waited for one by one: the
         // host prepares frame i + 1 while frame i's last kernels run
         const bool last = sl1 ? i + 2 >= n_cams : i + 1 == n_cams;
-        lodge_status r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + off, si, sv.get(),
-                                    stats ? stats + i : nullptr, last, nullptr);
+        Slot::Pending pd;
+        pd.frame = i;
+        lodge_status r = LODGE_OK;
+        if (defer && (int)sl.pending.size() >= Slot::kRing) r = harvest(ctx, sl, si, &redo);
+        if (r == LODGE_OK)
+            r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + offs[i], si, sv.get(),
+                           stats ? stats + i : nullptr, last, nullptr, defer ? &pd : nullptr);
         if (r != LODGE_OK) {
-            for (Slot* q : {&sl0, sl1}) {
-                if (q && q->tail_pending) {
-                    cudaStreamSynchronize(q == &sl0 ? s : s1);
-                    q->tail_pending = false;
-                }
-            }
+            drain();
             return r;
         }
-        off += (size_t)cams[i].width * cams[i].height * 3;
         if (sv) {
             std::lock_guard<std::recursive_mutex> lk(ctx->mu);
             int64_t h = ctx->next_handle++;
@@ -1406,9 +1527,25 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
             *handle_out = h;
         }
     }
+    // counts of the deferred frames; frames whose keys outgrew their slot's
+    // capacity are rendered again, one by one with their sync
+    lodge_status r = harvest(ctx, sl0, s, &redo);
+    if (r == LODGE_OK && sl1) r = harvest(ctx, *sl1, s1, &redo);
+    if (r != LODGE_OK) {
+        drain();
+        return r;
+    }
     if (sl1) {   // the caller's stream ends after the second stream's frames
         CUDA_TRY(cudaEventRecord(sl1->fence, s1));
         CUDA_TRY(cudaStreamWaitEvent(s, sl1->fence, 0));
+    }
+    for (int i : redo) {
+        r = render_one(ctx, sl0, sc, mode, cams[i], d_rgb + offs[i], s, nullptr, stats ? stats + i : nullptr,
+                       true, nullptr, nullptr);
+        if (r != LODGE_OK) {
+            drain();
+            return r;
+        }
     }
     return LODGE_OK;
 }
@@ -1787,6 +1924,7 @@ lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
         p.bin_sort_passes += q.bin_sort_passes;
         p.blend_pairs += q.blend_pairs;
         p.blend_pairs_used += q.blend_pairs_used;
+        p.redone += q.redone;
     }
     *out = p;
     return LODGE_OK;

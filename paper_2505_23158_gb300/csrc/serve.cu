@@ -16,14 +16,6 @@
 
 #include "internal.cuh"
 
-namespace lodge {
-
-lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
-                        const lodge_camera& cam, float* d_rgb, cudaStream_t s, Saved* save,
-                        lodge_frame_stats* st, bool end_sync, float* importance);
-
-}  // namespace lodge
-
 using namespace lodge;
 
 extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, int32_t n,

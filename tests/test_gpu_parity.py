@@ -439,3 +439,30 @@ def test_counting_mode_pairs(ctx, outdoor, torch_cuda, log2):
     assert used_ref > 0
     assert abs(prof["blend_pairs_used"] - used_ref) <= max(10, 1e-3 * used_ref), (prof, used_ref)
     assert prof["blend_pairs_used"] <= prof["blend_pairs"] <= ref["n_pairs_eval"]
+
+
+def test_deferred_frames_overflow_rendered_again(torch_cuda):
+    """A camera list whose first frames see nothing sizes its streams' key
+    capacity small; the later frames outgrow it, are rendered again, and
+    every image and count equals the camera rendered alone."""
+    from paper_2505_23158_gb300 import api
+    scene, cams = synth.workload_outdoor(seed=8, n_poses=12, scale=0.02, width=320, height_px=180)
+    c0 = cams[0]
+    up = np.asarray(c0.center, np.float64)
+    away = synth.look_at(up + np.array([0.0, 0.0, 1000.0]), up + np.array([0.0, 0.0, 2000.0]), (1, 0, 0),
+                         320, 180, 70.0)
+    seq = [away, away] + list(cams[:6])
+    with api.Lodge(0) as c2:
+        sid = c2.load_scene(scene)
+        c2.set_bin_size(1)
+        c2.profile_enable(True)
+        imgs, stats = c2.render(sid, api.FULL, seq)
+        prof = c2.profile_read()
+        c2.profile_enable(False)
+        assert stats[0]["n_visible"] == 0 and stats[2]["n_keys"] > 0
+        assert prof["redone"] >= 1, prof
+        assert prof["frames"] == len(seq)
+        for cam, img, st in zip(seq, imgs, stats):
+            one, st1 = c2.render(sid, api.FULL, cam)
+            assert torch_cuda.equal(one, img)
+            assert st1["n_keys"] == st["n_keys"] and st1["n_visible"] == st["n_visible"]
