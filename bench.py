@@ -220,10 +220,11 @@ def stage_bytes(stage: str, prof: dict) -> float:
 
 def measured_traffic(kernel_stage: str, units_per_launch: float):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary (profiles/traffic_*.txt), scaled to this run's units per launch;
-    None if there is no summary for it or its kernel source changed since."""
+    summary (profiles/traffic_*.txt), scaled to this run's units per launch
+    where the summary gives bytes per unit; None if there is no summary for
+    it or its kernel source changed since."""
     import hashlib
-    files = {"tile_sort": "traffic_onesweep_tile_sort.txt"}
+    files = {"tile_sort": "traffic_onesweep_tile_sort.txt", "blend": "traffic_blend_kernel.txt"}
     f = files.get(kernel_stage)
     if f is None:
         return None
@@ -241,6 +242,8 @@ def measured_traffic(kernel_stage: str, units_per_launch: float):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv.get("source_sha256_16"):
         return None
+    if "dram_bytes_per_launch" in kv:
+        return float(kv["dram_bytes_per_launch"])
     return float(kv["dram_bytes_per_key"]) * units_per_launch
 
 
@@ -369,12 +372,12 @@ def run_lodge(args, rank, world, local_rank):
     ctx.profile_enable(False)
 
     # ---- end to end through the host-buffer entry point (camera H2D, image D2H)
-    host = torch.empty(npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)
+    host = torch.empty(P * npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)
     e2e_steps = max(1, min(args.steps, 3))
     def run_e2e():
+        # one host-buffer call per step: its cameras in, its images out
         for s in range(e2e_steps):
-            for cam in frames(s):
-                ctx.render_host(sid, CHUNK_BLEND, [cam], host)
+            ctx.render_host(sid, CHUNK_BLEND, frames(s), host)
 
     t_e2e = timed_region(run_e2e, world, sync=torch.cuda.synchronize, device=dev)
     e2e_fps = job_throughput(e2e_steps * P, world, t_e2e)
@@ -397,8 +400,9 @@ def run_lodge(args, rank, world, local_rank):
         flops = (9.5 * prof_cnt["blend_pairs"] + 9.0 * prof_cnt["blend_pairs_used"]) / nf
         t_launch = ms["blend"] / max(prof["frames"], 1) / 1e3
         ach = flops / t_launch / 1e12
+        tr = measured_traffic("blend", 0)
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": None, "kernel": "blend",
+                "frac": round(ach / peak, 4), "traffic": None if tr is None else round(tr), "kernel": "blend",
                 "flops_per_launch": round(flops), "pairs_per_launch": prof_cnt["blend_pairs"] // nf,
                 "composited_pairs_per_launch": prof_cnt["blend_pairs_used"] // nf,
                 "avg_launch_ms": round(t_launch * 1e3, 5),

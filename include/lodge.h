@@ -260,9 +260,12 @@ lodge_status lodge_render_batch(lodge_ctx* ctx, int32_t n, const int32_t* scene_
                                 void* stream, lodge_frame_stats* stats, int32_t* statuses);
 
 /* Same as lodge_render but cameras and the image live in HOST memory: the
- * call copies the image back (device -> host) before returning.  h_rgb:
- * n_cams images, H x W x 3 float32 each.  Intended for callers that do not
- * manage device memory; device scratch is owned by the context. */
+ * call copies the images back (device -> host) before returning, each one
+ * as soon as its frame is done, so that the copies of earlier frames overlap
+ * the rendering of later ones (page-locked h_rgb lets them run
+ * asynchronously).  h_rgb: n_cams images, H x W x 3 float32 each.  Intended
+ * for callers that do not manage device memory; device scratch is owned by
+ * the context. */
 lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
                                const lodge_camera* cams, int32_t n_cams, float* h_rgb,
                                void* stream, lodge_frame_stats* stats);

@@ -159,14 +159,14 @@ static void prof_collect(Slot& sl) {
     }
 }
 
-// Slot 1 with its own stream and fence event (created on first use; the
-// request loop and batches reuse it as their first slot).
-lodge_status second_slot(lodge_ctx* ctx, Slot** out) {
-    while (ctx->slots.size() < 2) {
+// Slot k >= 1 with its own stream and fence event (created on first use;
+// the request loop and batches reuse slot 1 as their first slot).
+lodge_status stream_slot(lodge_ctx* ctx, int k, Slot** out) {
+    while ((int)ctx->slots.size() < k + 1) {
         Slot* sl = nullptr;
         TRY(create_slot(ctx, &sl));
     }
-    Slot* sl = ctx->slots[1].get();
+    Slot* sl = ctx->slots[k].get();
     if (!sl->own) CUDA_TRY(cudaStreamCreateWithFlags(&sl->own, cudaStreamNonBlocking));
     if (!sl->fence) CUDA_TRY(cudaEventCreateWithFlags(&sl->fence, cudaEventDisableTiming));
     sl->prof_on = ctx->slots[0]->prof_on;
@@ -1460,9 +1460,12 @@ lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
     return LODGE_OK;
 }
 
-lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
-                          int32_t n_cams, float* d_rgb, void* stream, int32_t save_for_backward,
-                          int64_t* handle_out, lodge_frame_stats* stats) {
+// The body of lodge_render; h_rgb != null also copies each frame's image to
+// h_rgb (same layout as d_rgb) on the frame's stream right after the frame,
+// so the copies of earlier frames overlap the rendering of later ones.
+static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
+                                int32_t n_cams, float* d_rgb, void* stream, int32_t save_for_backward,
+                                int64_t* handle_out, lodge_frame_stats* stats, float* h_rgb) {
     if (!ctx || !cams || !d_rgb || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
     if (save_for_backward && (n_cams != 1 || !handle_out))
         return fail(LODGE_E_INVALID, "save_for_backward needs n_cams == 1 and handle_out");
@@ -1471,19 +1474,25 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Slot& sl0 = *ctx->slots[0];
-    // Several frames of a resident scene alternate between two slots, the
-    // second on its own stream: while the host waits for one frame's counts,
-    // the device runs the other frame's stages.  The second stream starts
+    // Several frames of a resident scene take turns on kRenderStreams slots,
+    // slot 0 on the caller's stream and the others on their own: the device
+    // runs the stages of several frames at once.  The other streams start
     // after the work already queued on the caller's stream and the caller's
     // stream ends after all of it.
-    Slot* sl1 = nullptr;
-    cudaStream_t s1 = nullptr;
+    std::vector<Slot*> rsl{&sl0};
+    std::vector<cudaStream_t> rst{s};
     if (n_cams > 1 && !save_for_backward && sc->residency == kResident) {
-        TRY(second_slot(ctx, &sl1));
-        s1 = sl1->own;
-        CUDA_TRY(cudaEventRecord(sl1->fence, s));
-        CUDA_TRY(cudaStreamWaitEvent(s1, sl1->fence, 0));
+        const int m = std::min<int>(mode == LODGE_FULL ? kRenderStreamsFull : kRenderStreams, n_cams);
+        for (int k = 1; k < m; ++k) {
+            Slot* q = nullptr;
+            TRY(stream_slot(ctx, k, &q));
+            CUDA_TRY(cudaEventRecord(q->fence, s));
+            CUDA_TRY(cudaStreamWaitEvent(q->own, q->fence, 0));
+            rsl.push_back(q);
+            rst.push_back(q->own);
+        }
     }
+    const int m = (int)rsl.size();
     // Frames of a resident scene that are not kept for the adjoint run
     // without their mid-frame sync once their slot knows a key capacity:
     // their counts stay on the device and are read when the slot is
@@ -1493,10 +1502,9 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     for (int i = 0; i < n_cams; ++i) offs[i + 1] = offs[i] + (size_t)cams[i].width * cams[i].height * 3;
     std::vector<int> redo;
     auto drain = [&]() {   // after a failure: nothing of this call stays in flight
-        for (Slot* q : {&sl0, sl1}) {
-            if (!q) continue;
-            cudaStream_t qs = q == &sl0 ? s : s1;
-            if (q->tail_pending || !q->pending.empty()) cudaStreamSynchronize(qs);
+        for (int k = 0; k < m; ++k) {
+            Slot* q = rsl[k];
+            if (q->tail_pending || !q->pending.empty()) cudaStreamSynchronize(rst[k]);
             q->tail_pending = false;
             q->pending.clear();
         }
@@ -1504,11 +1512,11 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     for (int i = 0; i < n_cams; ++i) {
         std::unique_ptr<Saved> sv;
         if (save_for_backward) sv.reset(new Saved());
-        Slot& sl = (sl1 && (i & 1)) ? *sl1 : sl0;
-        cudaStream_t si = (sl1 && (i & 1)) ? s1 : s;
+        Slot& sl = *rsl[i % m];
+        cudaStream_t si = rst[i % m];
         // consecutive frames of one call are not waited for one by one: the
-        // host prepares frame i + 1 while frame i's last kernels run
-        const bool last = sl1 ? i + 2 >= n_cams : i + 1 == n_cams;
+        // host prepares the next frames while earlier ones run
+        const bool last = i + m >= n_cams;
         Slot::Pending pd;
         pd.frame = i;
         lodge_status r = LODGE_OK;
@@ -1520,6 +1528,9 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
             drain();
             return r;
         }
+        if (h_rgb && offs[i + 1] > offs[i])
+            CUDA_TRY(cudaMemcpyAsync(h_rgb + offs[i], d_rgb + offs[i], sizeof(float) * (offs[i + 1] - offs[i]),
+                                     cudaMemcpyDeviceToHost, si));
         if (sv) {
             std::lock_guard<std::recursive_mutex> lk(ctx->mu);
             int64_t h = ctx->next_handle++;
@@ -1529,15 +1540,15 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
     }
     // counts of the deferred frames; frames whose keys outgrew their slot's
     // capacity are rendered again, one by one with their sync
-    lodge_status r = harvest(ctx, sl0, s, &redo);
-    if (r == LODGE_OK && sl1) r = harvest(ctx, *sl1, s1, &redo);
+    lodge_status r = LODGE_OK;
+    for (int k = 0; k < m && r == LODGE_OK; ++k) r = harvest(ctx, *rsl[k], rst[k], &redo);
     if (r != LODGE_OK) {
         drain();
         return r;
     }
-    if (sl1) {   // the caller's stream ends after the second stream's frames
-        CUDA_TRY(cudaEventRecord(sl1->fence, s1));
-        CUDA_TRY(cudaStreamWaitEvent(s, sl1->fence, 0));
+    for (int k = 1; k < m; ++k) {   // the caller's stream ends after the other streams' frames
+        CUDA_TRY(cudaEventRecord(rsl[k]->fence, rst[k]));
+        CUDA_TRY(cudaStreamWaitEvent(s, rsl[k]->fence, 0));
     }
     for (int i : redo) {
         r = render_one(ctx, sl0, sc, mode, cams[i], d_rgb + offs[i], s, nullptr, stats ? stats + i : nullptr,
@@ -1546,8 +1557,18 @@ lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, con
             drain();
             return r;
         }
+        if (h_rgb && offs[i + 1] > offs[i])
+            CUDA_TRY(cudaMemcpyAsync(h_rgb + offs[i], d_rgb + offs[i], sizeof(float) * (offs[i + 1] - offs[i]),
+                                     cudaMemcpyDeviceToHost, s));
     }
     return LODGE_OK;
+}
+
+lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
+                          int32_t n_cams, float* d_rgb, void* stream, int32_t save_for_backward,
+                          int64_t* handle_out, lodge_frame_stats* stats) {
+    return render_cams(ctx, scene_id, mode, cams, n_cams, d_rgb, stream, save_for_backward, handle_out, stats,
+                       nullptr);
 }
 
 lodge_status lodge_render_batch(lodge_ctx* ctx, int32_t n, const int32_t* scene_ids, const int32_t* modes,
@@ -1590,8 +1611,8 @@ lodge_status lodge_render_host(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode
     }
     Slot& sl = *ctx->slots[0];
     TRY(ensure(ctx, sl.ws.img, sizeof(float) * std::max<size_t>(total, 1), s));
-    TRY(lodge_render(ctx, scene_id, mode, cams, n_cams, sl.ws.img.as<float>(), stream, 0, nullptr, stats));
-    if (total) CUDA_TRY(cudaMemcpyAsync(h_rgb, sl.ws.img.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+    // each frame's image is copied back as soon as it is done
+    TRY(render_cams(ctx, scene_id, mode, cams, n_cams, sl.ws.img.as<float>(), stream, 0, nullptr, stats, h_rgb));
     CUDA_TRY(cudaStreamSynchronize(s));
     return LODGE_OK;
 }
