@@ -166,7 +166,7 @@ void launch_chunk_union(const uint32_t* a, int64_t na, const uint32_t* b, int64_
 // K3: projection + SH + visibility compaction.
 struct ProjectOut {
     float4* rec_a;      // (mean'x, mean'y, u00, u01)
-    float4* rec_b;      // (u11, opacity', r, g)
+    float4* rec_b;      // (u11, log2 opacity', r, g)
     float* rec_c;       // b
     uint2* rec_rect;    // pixel range (x0 | y0 << 16, x1 | y1 << 16), inclusive
     uint32_t* rec_gid;  // gid of the record

@@ -9,8 +9,9 @@
 // composited behind i, normalised by T_{i+1}, follows
 // B_{i-1} = alpha_i c_i + (1 - alpha_i) B_i.  With C = P + T_i alpha_i c_i +
 // T_i (1 - alpha_i) B_i:  dC/dc_i = T_i alpha_i,  dC/dalpha_i = T_i (c_i - B_i).
-// alpha = min(0.99, o' 2^-q) is recomputed with the forward's exact FP32
-// operations, so the skip (alpha < 1/255) and the clamp decide identically.
+// alpha = min(0.99, 2^(log2 o' - q)) is recomputed with the forward's exact
+// FP32 operations, so the skip (alpha < 1/255) and the clamp decide
+// identically.
 // Per-Gaussian sums are warp-reduced, then added with atomics.
 //
 // K9 project_bwd: per visible record, the gradients of (mean', U, o', rgb)
@@ -103,9 +104,8 @@ blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __
                 const float dx = pxf - a.x, dy = pyf - a.y;
                 const float t = fmaf(a.z, dx, a.w * dy);
                 const float wq = bb.x * dy;
-                const float q = fmaf(t, t, wq * wq);
-                const float G = ex2_approx(-q);
-                const float raw = bb.y * G;
+                // the forward's alpha (same operations), raw = o' 2^-q
+                const float raw = ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y)));
                 const float alpha = fminf(0.99f, raw);
                 if (alpha >= (1.0f / 255.0f)) {
                     contrib = true;
@@ -121,8 +121,9 @@ blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __
                     B2 = alpha * cb + (1.f - alpha) * B2;
                     T = Ti;
                     if (raw < 0.99f) {
+                        const float G = ex2_approx(-fmaf(t, t, wq * wq));   // 2^-q = d alpha / d o'
                         d_o = dA * G;
-                        const float dq = -kLn2 * G * bb.y * dA;
+                        const float dq = -kLn2 * raw * dA;
                         const float dt = 2.f * t * dq, dw = 2.f * wq * dq;
                         d_u00 = dt * dx;
                         d_u01 = dt * dy;

@@ -20,8 +20,9 @@
 // later step a no-op.
 //
 // Per pixel and Gaussian (record = mean', upper-triangular U with
-// U^T U = (1/2) log2(e) Sigma'^-1, opacity o', colour):
-//   q = (u00 dx + u01 dy)^2 + (u11 dy)^2,  alpha = min(0.99, o' 2^-q)
+// U^T U = (1/2) log2(e) Sigma'^-1, log2 o', colour):
+//   q = (u00 dx + u01 dy)^2 + (u11 dy)^2,  alpha = min(0.99, 2^(log2 o' - q))
+//   (= o' 2^-q; the exponent is formed by two FMAs and the product is saved)
 //   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
 //   C += T alpha rgb; T = T'.
 #include "common.cuh"
@@ -67,8 +68,7 @@ __device__ __forceinline__ void blend_px(const float4 a, const float4 bb, const 
     const float dy = py - a.y;
     const float t = fmaf(a.z, dx, a.w * dy);
     const float wq = bb.x * dy;
-    const float q = fmaf(t, t, wq * wq);
-    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+    const float alpha = fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y))));
     if (alpha >= (1.0f / 255.0f)) {
         const float Tn = T * (1.f - alpha);
         if (Tn < 1e-4f) {
@@ -96,8 +96,7 @@ __device__ __forceinline__ void blend_px_flat(const float4 a, const float4 bb, c
     const float dy = py - a.y;
     const float t = fmaf(a.z, dx, a.w * dy);
     const float wq = bb.x * dy;
-    const float q = fmaf(t, t, wq * wq);
-    const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+    const float alpha = fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y))));
     const float Tn = T * (1.f - alpha);
     const bool ok = alpha >= (1.0f / 255.0f);
     const bool go = ok && !(Tn < 1e-4f);
@@ -340,8 +339,7 @@ importance_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* _
                 const float t = fmaf(a.z, dx, a.w * dy);
                 const float4 bb = sb[k];
                 const float wq = bb.x * dy;
-                const float q = fmaf(t, t, wq * wq);
-                const float alpha = fminf(0.99f, bb.y * ex2_approx(-q));
+                const float alpha = fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y))));
                 if (alpha >= (1.0f / 255.0f)) {
                     const float Tn = T * (1.f - alpha);
                     if (Tn < 1e-4f) {

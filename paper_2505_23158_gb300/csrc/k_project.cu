@@ -328,7 +328,8 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     if (!vis) return;
     const uint32_t pos = s_prefix + excl;
     P.o.rec_a[pos] = make_float4(mxp, myp, u00, u01);
-    P.o.rec_b[pos] = make_float4(u11, o, fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
+    // log2 of the opacity: compositing forms alpha as 2^(log2 o' - q)
+    P.o.rec_b[pos] = make_float4(u11, log2f(o), fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
     P.o.rec_c[pos] = fmaxf(rgb[2], 0.f);
     P.o.rec_rect[pos] = make_uint2(pr0, pr1);   // pixel range
     P.o.rec_gid[pos] = g;

@@ -957,7 +957,7 @@ __global__ void debug_records_kernel(int64_t n, const float4* ra, const float4* 
         conic[3 * i + 1] = u00 * u01 / s;
         conic[3 * i + 2] = (u01 * u01 + u11 * u11) / s;
     }
-    if (opac) opac[i] = b.y;
+    if (opac) opac[i] = exp2f(b.y);   // records hold log2 of the opacity
     if (rgb) { rgb[3 * i] = b.z; rgb[3 * i + 1] = b.w; rgb[3 * i + 2] = rc[i]; }
 }
 
