@@ -207,16 +207,21 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                     const uint32_t mw = g < 8 ? (g < 4 ? m[0] : m[1]) : (g < 12 ? m[2] : m[3]);
                     uint32_t mb = (mw >> (8 * (g & 3))) & 0xffu;
                     if (!mb) continue;
-                    do {
-                        const int k = g * 8 + __ffs(mb) - 1;
-                        mb &= mb - 1u;
-                        const float4 a = sa[buf][k];
-                        const float4 bb = sb[buf][k];
-                        const float cz = sc[buf][k];
+                    // the eight positions unrolled (a warp-uniform test each),
+                    // so that the records' shared addresses are immediates
+                    const float4* ga = &sa[buf][g * 8];
+                    const float4* gb = &sb[buf][g * 8];
+                    const float* gc = &sc[buf][g * 8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (!(mb & (1u << j))) continue;
+                        const float4 a = ga[j];
+                        const float4 bb = gb[j];
+                        const float cz = gc[j];
                         const float dx = pxf - a.x;
                         blend_px_flat<kCount>(a, bb, cz, dx, py0, T0, C00, C01, C02, n_eval, n_used);
                         blend_px_flat<kCount>(a, bb, cz, dx, py1, T1, C10, C11, C12, n_eval, n_used);
-                    } while (mb);
+                    }
                     if (__all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) break;
                 }
             }
