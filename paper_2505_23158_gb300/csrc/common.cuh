@@ -279,6 +279,47 @@ void launch_digit_scan(uint32_t* hist, int passes, cudaStream_t s);
 void launch_ranges(const uint32_t* tile_key, int64_t n_keys, uint2* ranges, int64_t ntiles,
                    int shift, cudaStream_t s);
 
+// Alpha of a projection record at a pixel (Eq. 1 with the record's
+// Cholesky form): alpha = min(0.99, 2^(log2 o' - (u00 dx + u01 dy)^2 -
+// (u11 dy)^2)), a = (mean', u00, u01), b = (u11, log2 o', ...).  The
+// compositing thread owns the pixels of rows y and y + 4 of an 8-row block
+// and forms the second row's t and w from the first's by the row step (one
+// FMA each), so a pixel whose row within its tile has bit 2 set takes that
+// form here too: every walk (compositing, adjoint, importance) then decides
+// skip and stop on the same FP32 values.  t and w are returned for the
+// adjoint.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float alpha_of(float4 b, float t, float w) {
+    return fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-w, w, b.y))));
+}
+// t and w at row py0 (a pixel-centre y) and at py0 + 4
+__device__ __forceinline__ void row_pair_tw(float4 a, float4 b, float dx, float py0, float& t0, float& w0,
+                                            float& t1, float& w1) {
+    const float dy = py0 - a.y;
+    t0 = fmaf(a.z, dx, a.w * dy);
+    w0 = b.x * dy;
+    t1 = fmaf(4.f, a.w, t0);
+    w1 = fmaf(4.f, b.x, w0);
+}
+// t and w at pixel row y (image row; tiles start at multiples of 16, so bit
+// 2 of y is bit 2 of the row within the tile)
+__device__ __forceinline__ void pixel_tw(float4 a, float4 b, float dx, int y, float& t, float& w) {
+    float t0, w0, t1, w1;
+    if (y & 4) {
+        row_pair_tw(a, b, dx, (float)(y - 4) + 0.5f, t0, w0, t1, w1);
+        t = t1;
+        w = w1;
+    } else {
+        row_pair_tw(a, b, dx, (float)y + 0.5f, t0, w0, t1, w1);
+        t = t0;
+        w = w0;
+    }
+}
+
 // K7: per tile front-to-back compositing.
 struct BlendOut {
     float* rgb;        // H x W x 3

@@ -29,11 +29,6 @@ constexpr int kBatch = 256;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kHalfLog2e = 0.7213475204444817f;
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -102,9 +97,9 @@ blend_bwd_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* __
                 const float4 a = sa[k];
                 const float4 bb = sb[k];
                 const float dx = pxf - a.x, dy = pyf - a.y;
-                const float t = fmaf(a.z, dx, a.w * dy);
-                const float wq = bb.x * dy;
-                // the forward's alpha (same operations), raw = o' 2^-q
+                // the forward's t, w and alpha (same operations), raw = o' 2^-q
+                float t, wq;
+                pixel_tw(a, bb, dx, y, t, wq);
                 const float raw = ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y)));
                 const float alpha = fminf(0.99f, raw);
                 if (alpha >= (1.0f / 255.0f)) {

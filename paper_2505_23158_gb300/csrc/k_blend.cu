@@ -35,11 +35,6 @@ constexpr int kBatch = 256;        // importance kernel: records per batch
 constexpr int kBlendThreads = 128; // blend: two pixels per thread
 constexpr int kBlendBatch = 128;   // blend: records per batch (one per thread)
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -60,15 +55,10 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // one record of the batch against one pixel (Eq. 1); kCount: count the
 // evaluation and, if the pixel composites it, the composited pair
 template <bool kCount, bool kLast>
-__device__ __forceinline__ void blend_px(const float4 a, const float4 bb, const float cz, float dx,
-                                         float py, float& T, float& C0, float& C1, float& C2,
-                                         bool& done, uint32_t& last, uint32_t pos, uint32_t& n_eval,
-                                         uint32_t& n_used) {
+__device__ __forceinline__ void blend_px(const float alpha, const float4 bb, const float cz, float& T,
+                                         float& C0, float& C1, float& C2, bool& done, uint32_t& last,
+                                         uint32_t pos, uint32_t& n_eval, uint32_t& n_used) {
     if (kCount) ++n_eval;
-    const float dy = py - a.y;
-    const float t = fmaf(a.z, dx, a.w * dy);
-    const float wq = bb.x * dy;
-    const float alpha = fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y))));
     if (alpha >= (1.0f / 255.0f)) {
         const float Tn = T * (1.f - alpha);
         if (Tn < 1e-4f) {
@@ -90,13 +80,9 @@ __device__ __forceinline__ void blend_px(const float4 a, const float4 bb, const 
 // which every step leaves it unchanged (its weight is 0 and T stays 0).
 // While T > 0 the arithmetic and decisions are blend_px's.
 template <bool kCount>
-__device__ __forceinline__ void blend_px_flat(const float4 a, const float4 bb, const float cz, float dx,
-                                              float py, float& T, float& C0, float& C1, float& C2,
-                                              uint32_t& n_eval, uint32_t& n_used) {
-    const float dy = py - a.y;
-    const float t = fmaf(a.z, dx, a.w * dy);
-    const float wq = bb.x * dy;
-    const float alpha = fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y))));
+__device__ __forceinline__ void blend_px_flat(const float alpha, const float4 bb, const float cz, float& T,
+                                              float& C0, float& C1, float& C2, uint32_t& n_eval,
+                                              uint32_t& n_used) {
     const float Tn = T * (1.f - alpha);
     const bool ok = alpha >= (1.0f / 255.0f);
     const bool go = ok && !(Tn < 1e-4f);
@@ -134,7 +120,7 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     const int x = tx * kTile + (warp & 1) * 8 + (lane & 7);
     const int y0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3), y1 = y0 + 4;
     const bool in0 = x < width && y0 < height, in1 = x < width && y1 < height;
-    const float pxf = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
+    const float pxf = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     const uint32_t wx0 = tx * kTile + (warp & 1) * 8, wx1 = wx0 + 7;   // the warp's 8x8 block
     const uint32_t wy0 = ty * kTile + (warp >> 1) * 8, wy1 = wy0 + 7;
     const uint2* __restrict__ rec_rect = f.rec_rect;
@@ -218,9 +204,10 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                         const float4 a = ga[j];
                         const float4 bb = gb[j];
                         const float cz = gc[j];
-                        const float dx = pxf - a.x;
-                        blend_px_flat<kCount>(a, bb, cz, dx, py0, T0, C00, C01, C02, n_eval, n_used);
-                        blend_px_flat<kCount>(a, bb, cz, dx, py1, T1, C10, C11, C12, n_eval, n_used);
+                        float t0, w0, t1, w1;
+                        row_pair_tw(a, bb, pxf - a.x, py0, t0, w0, t1, w1);
+                        blend_px_flat<kCount>(alpha_of(bb, t0, w0), bb, cz, T0, C00, C01, C02, n_eval, n_used);
+                        blend_px_flat<kCount>(alpha_of(bb, t1, w1), bb, cz, T1, C10, C11, C12, n_eval, n_used);
                     }
                     if (__all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) break;
                 }
@@ -230,12 +217,15 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                 const float4 a = sa[buf][k];
                 const float4 bb = sb[buf][k];
                 const float cz = sc[buf][k];
-                const float dx = pxf - a.x;
                 const uint32_t pos = (uint32_t)(b * kBlendBatch + k + 1);
+                float t0, w0, t1, w1;
+                row_pair_tw(a, bb, pxf - a.x, py0, t0, w0, t1, w1);
                 if (!done0)
-                    blend_px<kCount, kLast>(a, bb, cz, dx, py0, T0, C00, C01, C02, done0, last0, pos, n_eval, n_used);
+                    blend_px<kCount, kLast>(alpha_of(bb, t0, w0), bb, cz, T0, C00, C01, C02, done0, last0, pos,
+                                            n_eval, n_used);
                 if (!done1)
-                    blend_px<kCount, kLast>(a, bb, cz, dx, py1, T1, C10, C11, C12, done1, last1, pos, n_eval, n_used);
+                    blend_px<kCount, kLast>(alpha_of(bb, t1, w1), bb, cz, T1, C10, C11, C12, done1, last1, pos,
+                                            n_eval, n_used);
             }
         }
         if (kBins) {
@@ -316,7 +306,7 @@ importance_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* _
     const int x = tx * kTile + (warp & 1) * 8 + (lane & 7);
     const int y = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = x < width && y < height;
-    const float pxf = (float)x + 0.5f, pyf = (float)y + 0.5f;
+    const float pxf = (float)x + 0.5f;
     uint2 rg = ranges[tile];
     if (rg.y > n_keys || rg.x > rg.y) rg = make_uint2(0, 0);
     const int n = (int)(rg.y - rg.x);
@@ -340,11 +330,10 @@ importance_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* _
             float w = 0.f;
             if (!done) {
                 const float4 a = sa[k];
-                const float dx = pxf - a.x, dy = pyf - a.y;
-                const float t = fmaf(a.z, dx, a.w * dy);
                 const float4 bb = sb[k];
-                const float wq = bb.x * dy;
-                const float alpha = fminf(0.99f, ex2_approx(fmaf(-t, t, fmaf(-wq, wq, bb.y))));
+                float t, wq;
+                pixel_tw(a, bb, pxf - a.x, y, t, wq);
+                const float alpha = alpha_of(bb, t, wq);
                 if (alpha >= (1.0f / 255.0f)) {
                     const float Tn = T * (1.f - alpha);
                     if (Tn < 1e-4f) {
