@@ -431,6 +431,7 @@ def run_lodge(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_blend / args.steps * 1e3, 3), "higher_is_better": True,
+        "host_enqueue_ms_per_step": round(prof_timed["host_ms"] / args.steps, 3),
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"outdoor LOD scene {n_total} Gaussians "
                                f"({', '.join(str(l.n) for l in scene.levels)}), 16x16 chunks, "

@@ -479,6 +479,8 @@ typedef struct {
     int64_t redone;           /* frames of multi-camera calls rendered again
                                * because their bin keys outgrew the capacity
                                * sized from earlier frames */
+    double host_ms;           /* host time lodge_render spent enqueuing its
+                               * frames, up to the wait for their counts */
 } lodge_profile;
 
 /* Start (enable != 0, counters reset) or stop collecting the profile.

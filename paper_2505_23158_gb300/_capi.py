@@ -61,7 +61,7 @@ class lodge_profile(C.Structure):
                 ("frames", C.c_int64), ("keys", C.c_int64), ("visible", C.c_int64),
                 ("active", C.c_int64), ("packed_keys", C.c_int64), ("bin_keys", C.c_int64),
                 ("bin_sort_passes", C.c_int64), ("blend_pairs", C.c_int64),
-                ("blend_pairs_used", C.c_int64), ("redone", C.c_int64)]
+                ("blend_pairs_used", C.c_int64), ("redone", C.c_int64), ("host_ms", C.c_double)]
 
 
 class lodge_frame_stats(C.Structure):

@@ -368,7 +368,7 @@ class Lodge:
                     frames=p.frames, keys=p.keys, visible=p.visible, active=p.active,
                     packed_keys=p.packed_keys, bin_keys=p.bin_keys,
                     bin_sort_passes=p.bin_sort_passes, blend_pairs=p.blend_pairs,
-                    blend_pairs_used=p.blend_pairs_used, redone=p.redone)
+                    blend_pairs_used=p.blend_pairs_used, redone=p.redone, host_ms=p.host_ms)
 
     def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
         """Stable in-place sort of int32 (bit pattern = uint32) keys and values."""

@@ -2,6 +2,7 @@
 // choice (Eq. 4), per-chunk active-set precompute (Eq. 2 at chunk centres,
 // Sec. 3 "Chunk-based rendering") and the per-frame orchestration of the
 // kernels K1..K7 on the caller's stream.
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1469,6 +1470,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
     if (!ctx || !cams || !d_rgb || n_cams < 0) return fail(LODGE_E_INVALID, "bad argument");
     if (save_for_backward && (n_cams != 1 || !handle_out))
         return fail(LODGE_E_INVALID, "save_for_backward needs n_cams == 1 and handle_out");
+    const auto t_call = std::chrono::steady_clock::now();
     Scene* sc = get_scene(ctx, scene_id);
     if (!sc) return fail(LODGE_E_INVALID, "no scene %d", scene_id);
     CUDA_TRY(cudaSetDevice(ctx->device));
@@ -1538,6 +1540,9 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
             *handle_out = h;
         }
     }
+    // host time spent enqueuing the call's frames (before waiting for them)
+    ctx->slots[0]->prof.host_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_call).count();
     // counts of the deferred frames; frames whose keys outgrew their slot's
     // capacity are rendered again, one by one with their sync
     lodge_status r = LODGE_OK;
@@ -1946,6 +1951,7 @@ lodge_status lodge_profile_read(lodge_ctx* ctx, lodge_profile* out) {
         p.blend_pairs += q.blend_pairs;
         p.blend_pairs_used += q.blend_pairs_used;
         p.redone += q.redone;
+        p.host_ms += q.host_ms;
     }
     *out = p;
     return LODGE_OK;
