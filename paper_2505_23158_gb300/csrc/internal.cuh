@@ -104,6 +104,7 @@ enum : int {
     kSmCtrProj = 10,
     kSmCtrEmit = 11,
     kSmPairs = 12,      // [12..13] pairs evaluated, [14..15] composited (u64, counting mode)
+    kSmCtrBlend = 16,   // next tile of the compositing CTAs
     kSmWords = 64
 };
 

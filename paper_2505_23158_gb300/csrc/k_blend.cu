@@ -264,8 +264,21 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
 }
 
 template <bool kBins, bool kCount>
-__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) {
-    blend_tile<kBins, kCount>(f, blockIdx.x);
+__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f, uint32_t* __restrict__ tile_ctr) {
+    if (!tile_ctr) {
+        blend_tile<kBins, kCount>(f, blockIdx.x);
+        return;
+    }
+    // fewer CTAs than tiles: each takes the next tile from the counter
+    __shared__ int s_t;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (int)atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();   // s_t is rewritten for the next tile
+        if (t >= f.ntiles) break;
+        blend_tile<kBins, kCount>(f, t);
+    }
 }
 
 // One launch for the tiles of several frames (a serving step): CTA b
@@ -403,20 +416,27 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2, const uint2* rec_rect,
-                  unsigned long long* pairs) {
+                  unsigned long long* pairs, uint32_t* tile_ctr) {
     BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o,
                                bin_log2, rec_rect);
     if (f.ntiles == 0) return;
     f.pairs = pairs;
+    unsigned grid = (unsigned)f.ntiles;
+    if (tile_ctr) {
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = (unsigned)std::min<int64_t>(f.ntiles, (int64_t)sms * kBlendCtasPerSM);
+    }
     if (pairs) {   // counting variant (profiling), same walk
         if (f.bin_log2 > 0)
-            blend_kernel<true, true><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+            blend_kernel<true, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
         else
-            blend_kernel<false, true><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+            blend_kernel<false, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
     } else if (f.bin_log2 > 0) {
-        blend_kernel<true, false><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+        blend_kernel<true, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
     } else {
-        blend_kernel<false, false><<<f.ntiles, kBlendThreads, 0, s>>>(f);
+        blend_kernel<false, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
     }
 }
 

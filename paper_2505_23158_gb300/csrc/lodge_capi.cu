@@ -704,7 +704,8 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     } else {
         launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_bkeys, ws.rec_a.as<float4>(),
                      ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s, bl, ws.rec_rect.as<uint2>(),
-                     sl.prof_count ? reinterpret_cast<unsigned long long*>(sl.d_small + kSmPairs) : nullptr);
+                     sl.prof_count ? reinterpret_cast<unsigned long long*>(sl.d_small + kSmPairs) : nullptr,
+                     sl.d_small + kSmCtrBlend);
         if (sl.prof_count) end_sync = true;   // the counts are read back with the frame
     }
     prof_end(sl, LODGE_STAGE_BLEND, s, job ? 0 : ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
