@@ -339,7 +339,9 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
                   uint32_t* tile_ctr = nullptr);
 // tile_ctr (a zeroed device word) makes the compositing a grid of
 // kBlendCtasPerSM CTAs per SM that take tiles from the counter, so that
-// other streams' kernels keep room on every SM while it runs (1080p chunk
+// other streams' kernels keep room on every SM while it runs (used when
+// frames of other slots run at the same time; a lone frame takes one CTA
+// per tile and the whole GPU).  Measured with 1080p chunk
 // frames on four streams: 2 / 3 / 4 / 6 / 8 / 12 CTAs per SM gave 5790 /
 // 5936 / 5894 / 5775 / 5706 / 5729 frames/s; the single-frame compositing
 // time grows from 0.081 ms at 8 to 0.090 ms at 4).

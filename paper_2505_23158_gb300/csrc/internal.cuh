@@ -144,6 +144,9 @@ struct Slot {
     std::vector<Pending> pending;
     bool prof_on = false;
     bool prof_count = false;   // compositing counts its (pixel, Gaussian) pairs
+    // other slots' frames run at the same time (several render streams, the
+    // request loop): compositing then leaves room on every SM for them
+    bool share_sms = false;
     lodge_profile prof{};
     cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};
     cudaEvent_t ev_end[LODGE_NUM_STAGES] = {};

@@ -264,12 +264,13 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
 }
 
 template <bool kBins, bool kCount>
-__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f, uint32_t* __restrict__ tile_ctr) {
-    if (!tile_ctr) {
-        blend_tile<kBins, kCount>(f, blockIdx.x);
-        return;
-    }
-    // fewer CTAs than tiles: each takes the next tile from the counter
+__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) {
+    blend_tile<kBins, kCount>(f, blockIdx.x);
+}
+
+// fewer CTAs than tiles: each takes the next tile from the counter
+template <bool kBins, bool kCount>
+__global__ void __launch_bounds__(kBlendThreads) blend_loop_kernel(BlendFrame f, uint32_t* __restrict__ tile_ctr) {
     __shared__ int s_t;
     for (;;) {
         if (threadIdx.x == 0) s_t = (int)atomicAdd(tile_ctr, 1u);
@@ -428,15 +429,26 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = (unsigned)std::min<int64_t>(f.ntiles, (int64_t)sms * kBlendCtasPerSM);
     }
-    if (pairs) {   // counting variant (profiling), same walk
+    if (tile_ctr) {
+        if (pairs) {   // counting variant (profiling), same walk
+            if (f.bin_log2 > 0)
+                blend_loop_kernel<true, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+            else
+                blend_loop_kernel<false, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+        } else if (f.bin_log2 > 0) {
+            blend_loop_kernel<true, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+        } else {
+            blend_loop_kernel<false, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+        }
+    } else if (pairs) {
         if (f.bin_log2 > 0)
-            blend_kernel<true, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+            blend_kernel<true, true><<<grid, kBlendThreads, 0, s>>>(f);
         else
-            blend_kernel<false, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+            blend_kernel<false, true><<<grid, kBlendThreads, 0, s>>>(f);
     } else if (f.bin_log2 > 0) {
-        blend_kernel<true, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+        blend_kernel<true, false><<<grid, kBlendThreads, 0, s>>>(f);
     } else {
-        blend_kernel<false, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
+        blend_kernel<false, false><<<grid, kBlendThreads, 0, s>>>(f);
     }
 }
 

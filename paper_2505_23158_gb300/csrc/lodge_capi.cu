@@ -705,7 +705,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         launch_blend(cam, ws.ranges.as<uint2>(), rec_of_pair, vmask, n_bkeys, ws.rec_a.as<float4>(),
                      ws.rec_b.as<float4>(), ws.rec_c.as<float>(), n_vis, bo, s, bl, ws.rec_rect.as<uint2>(),
                      sl.prof_count ? reinterpret_cast<unsigned long long*>(sl.d_small + kSmPairs) : nullptr,
-                     sl.d_small + kSmCtrBlend);
+                     sl.share_sms ? sl.d_small + kSmCtrBlend : nullptr);
         if (sl.prof_count) end_sync = true;   // the counts are read back with the frame
     }
     prof_end(sl, LODGE_STAGE_BLEND, s, job ? 0 : ntiles_img > 0 ? (importance ? 1 + (n_vis > 0) : 1) : 0);
@@ -1496,6 +1496,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
         }
     }
     const int m = (int)rsl.size();
+    for (Slot* q : rsl) q->share_sms = m > 1;
     // Frames of a resident scene that are not kept for the adjoint run
     // without their mid-frame sync once their slot knows a key capacity:
     // their counts stay on the device and are read when the slot is

@@ -42,6 +42,7 @@ extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, i
     }
     for (int w = 1; w <= need; ++w) {   // slots made by lodge_render_batch have no stream yet
         Slot& sl = *ctx->slots[w];
+        sl.share_sms = opts->slots > 1;   // requests run side by side
         if (!sl.own) {
             e = cudaStreamCreateWithFlags(&sl.own, cudaStreamNonBlocking);
             if (e != cudaSuccess) return fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e));

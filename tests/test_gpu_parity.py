@@ -331,19 +331,25 @@ def test_compensated_2d_filter(ctx, torch_cuda, which):
         compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"filter2d {which}")
 
 
-def test_camera_list_equals_single_frames(ctx, torch_cuda):
-    """A render call over several cameras (its frames alternate between two
-    streams) gives each camera's single-frame image bit for bit, for every
-    mode."""
+@pytest.mark.parametrize("log2", [3, 0])
+def test_camera_list_equals_single_frames(ctx, torch_cuda, log2):
+    """A render call over several cameras (its frames take turns on several
+    streams, without mid-frame syncs for binned lists, and their compositing
+    shares the SMs) gives each camera's single-frame image bit for bit, for
+    every mode, with binned and per-tile key lists."""
     from paper_2505_23158_gb300.api import CHUNK, CHUNK_BLEND, FULL, LOD
     scene, cams = synth.workload_outdoor(seed=8, n_poses=12, scale=0.02, width=320, height_px=180)
     sid = ctx.load_scene(scene)
-    for mode in (FULL, LOD, CHUNK, CHUNK_BLEND):
-        imgs, stats = ctx.render(sid, mode, list(cams[:7]))
-        for cam, img, st in zip(cams[:7], imgs, stats):
-            one, st1 = ctx.render(sid, mode, cam)
-            assert torch_cuda.equal(one, img)
-            assert st1["n_keys"] == st["n_keys"]
+    try:
+        ctx.set_bin_size(log2)
+        for mode in (FULL, LOD, CHUNK, CHUNK_BLEND):
+            imgs, stats = ctx.render(sid, mode, list(cams[:7]))
+            for cam, img, st in zip(cams[:7], imgs, stats):
+                one, st1 = ctx.render(sid, mode, cam)
+                assert torch_cuda.equal(one, img)
+                assert st1["n_keys"] == st["n_keys"]
+    finally:
+        ctx.set_bin_size(3)
 
 
 # ---------------------------------------------------------------------------
