@@ -142,6 +142,32 @@ def test_render_host_matches_device(ctx, plain_loaded):
     assert np.array_equal(out, img.cpu().numpy())
 
 
+def test_render_host_pinned_several_cameras(ctx, torch_cuda):
+    """Host-buffer calls over several cameras into page-locked and pageable
+    memory (each image copied back on its frame's stream as soon as it is
+    done): each image equals the device render, for images of several sizes."""
+    from paper_2505_23158_gb300.api import CHUNK_BLEND
+    scene, cams = synth.workload_outdoor(seed=3, n_poses=8, scale=0.02, width=320, height_px=180)
+    sid = ctx.load_scene(scene)
+    sizes = [(320, 180), (17, 33), (64, 48), (33, 17), (320, 180)]
+    cl = [synth.look_at(c.center, c.R[2].astype(np.float64), (0, 0, 1), w, h, 70.0)
+          for c, (w, h) in zip(cams, sizes)]
+    total = sum(c.width * c.height * 3 for c in cl)
+    for pinned in (True, False):
+        if pinned:
+            host = torch_cuda.empty(total, dtype=torch_cuda.float32, pin_memory=True).numpy()
+        else:
+            host = np.empty(total, np.float32)
+        host[:] = np.nan
+        ctx.render_host(sid, CHUNK_BLEND, cl, host)
+        off = 0
+        for c in cl:
+            k = c.width * c.height * 3
+            one, _ = ctx.render(sid, CHUNK_BLEND, c)
+            assert np.array_equal(host[off:off + k].reshape(c.height, c.width, 3), one.cpu().numpy()), (pinned, c.width)
+            off += k
+
+
 def test_repeatable(ctx, plain_loaded):
     from paper_2505_23158_gb300.api import FULL
     scene, cams, osc, sid = plain_loaded
