@@ -1541,8 +1541,11 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
             drain();
             return r;
         }
-        if (h_rgb)
-            TRY(copy_back(h_rgb + offs[i], d_rgb + offs[i], offs[i + 1] - offs[i], si));
+        if (h_rgb) r = copy_back(h_rgb + offs[i], d_rgb + offs[i], offs[i + 1] - offs[i], si);
+        if (r != LODGE_OK) {
+            drain();
+            return r;
+        }
         if (sv) {
             std::lock_guard<std::recursive_mutex> lk(ctx->mu);
             int64_t h = ctx->next_handle++;
@@ -1572,8 +1575,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
             drain();
             return r;
         }
-        if (h_rgb)
-            TRY(copy_back(h_rgb + offs[i], d_rgb + offs[i], offs[i + 1] - offs[i], s));
+        if (h_rgb) TRY(copy_back(h_rgb + offs[i], d_rgb + offs[i], offs[i + 1] - offs[i], s));
     }
     return LODGE_OK;
 }
