@@ -498,3 +498,26 @@ def test_deferred_frames_overflow_rendered_again(torch_cuda):
             one, st1 = c2.render(sid, api.FULL, cam)
             assert torch_cuda.equal(one, img)
             assert st1["n_keys"] == st["n_keys"] and st1["n_visible"] == st["n_visible"]
+
+
+def test_deferred_frames_with_nothing_visible(torch_cuda):
+    """Frames that see nothing in the middle of a camera list (their counts
+    stay on the device: every sort and the emission run with a count of 0)
+    render black and leave the following frames unchanged."""
+    from paper_2505_23158_gb300 import api
+    scene, cams = synth.workload_outdoor(seed=5, n_poses=12, scale=0.02, width=320, height_px=180)
+    up = np.asarray(cams[0].center, np.float64)
+    away = synth.look_at(up + np.array([0.0, 0.0, 1000.0]), up + np.array([0.0, 0.0, 2000.0]), (1, 0, 0),
+                         320, 180, 70.0)
+    seq = list(cams[:4]) + [away] * 4 + list(cams[4:8])
+    with api.Lodge(0) as c2:
+        sid = c2.load_scene(scene)
+        for mode in (api.CHUNK_BLEND, api.FULL):
+            imgs, stats = c2.render(sid, mode, seq)
+            for k in range(4, 8):
+                assert stats[k]["n_visible"] == 0 and stats[k]["n_keys"] == 0
+                assert float(imgs[k].abs().max()) == 0.0
+            for cam, img, st in zip(seq, imgs, stats):
+                one, st1 = c2.render(sid, mode, cam)
+                assert torch_cuda.equal(one, img)
+                assert st1["n_keys"] == st["n_keys"]
