@@ -234,12 +234,13 @@ constexpr int64_t sort_scratch_words(int64_t n, int passes) {
 // of pairs, at most n; n is then a capacity that sizes the grid and the
 // scratch, tiles past the count exit at once, and digit_offsets must be
 // given (the sort then runs for any count, 0 and 1 included).
+// scratch_cleared: the caller has zeroed the scratch (no memset here).
 size_t sort_scratch_bytes(int64_t n, int key_bits);
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
                     const uint32_t* digit_offsets = nullptr, bool final_keys = true, int shift0 = 0,
                     uint2* ranges = nullptr, uint32_t range_tiles = 0,
-                    const unsigned long long* d_count = nullptr);
+                    const unsigned long long* d_count = nullptr, bool scratch_cleared = false);
 int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
 // K4: emit (bin, record) pairs in depth order.  A bin is a square of

@@ -86,11 +86,13 @@ struct Saved {
 struct Workspace {
     DBuf list, marks, status, rec_a, rec_b, rec_c, rec_rect, rec_gid, dkey, dval, dkey2, dval2,
         tkey, tval, tkey2, tval2, ranges, sort, T, last, img, act_so, act_q, mtmp, koff, srec,
-        srect, doffs, grec, bonly, iscore;
+        srect, doffs, grec, bonly, iscore,
+        status2, sort2;   // frames without a mid-frame sync: emission and bin-sort scratch of their own
     std::vector<DBuf*> all() {
         return {&list, &marks, &status, &rec_a, &rec_b, &rec_c, &rec_rect, &rec_gid, &dkey, &dval,
                 &dkey2, &dval2, &tkey, &tval, &tkey2, &tval2, &ranges, &sort, &T, &last, &img,
-                &act_so, &act_q, &mtmp, &koff, &srec, &srect, &doffs, &grec, &bonly, &iscore};
+                &act_so, &act_q, &mtmp, &koff, &srec, &srect, &doffs, &grec, &bonly, &iscore,
+                &status2, &sort2};
     }
 };
 

@@ -248,7 +248,7 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
                     const uint32_t* digit_offsets, bool final_keys, int shift0, uint2* ranges,
-                    uint32_t range_tiles, const unsigned long long* d_count) {
+                    uint32_t range_tiles, const unsigned long long* d_count, bool scratch_cleared) {
     const int P = passes_for(key_bits);
     if (P == 0 || (d_count ? n < 1 : n <= 1)) return 0;
     if (d_count && !digit_offsets) return 0;   // device counts need supplied digit offsets
@@ -262,8 +262,9 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
     const uint32_t* offs = hist;
     if (digit_offsets) {
         // exclusive digit offsets supplied: clear only counters and look-back words
-        cudaMemsetAsync(counters, 0,
-                        sort_scratch_bytes(n, key_bits) - sizeof(uint32_t) * kMaxPasses * kRadix, s);
+        if (!scratch_cleared)
+            cudaMemsetAsync(counters, 0,
+                            sort_scratch_bytes(n, key_bits) - sizeof(uint32_t) * kMaxPasses * kRadix, s);
         offs = digit_offsets;
     } else {
         cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bits), s);

@@ -518,6 +518,29 @@ static void take(DBuf& dst, DBuf& src) { dst = src; src = DBuf{}; }
 // importance[gid] (n_total floats) to each Gaussian's largest weight.
 // job != null: stop before compositing and describe it in *job (the caller
 // composites a batch of frames with one launch and then syncs their slots).
+// The scratch words a frame starts from, set by one launch: segment k of
+// n[k] words gets v0[k] at even and v1[k] at odd word indices.
+struct FillPlan {
+    static constexpr int kMax = 8;
+    uint32_t* p[kMax];
+    int64_t n[kMax];
+    uint32_t v0[kMax], v1[kMax];
+    int count = 0;
+    void add(uint32_t* ptr, int64_t words, uint32_t a = 0u, uint32_t b = 0u) {
+        if (count < kMax && ptr && words > 0) {
+            p[count] = ptr; n[count] = words; v0[count] = a; v1[count] = b; ++count;
+        }
+    }
+};
+__global__ void fill_kernel(FillPlan f) {
+    const int k = blockIdx.y;
+    uint32_t* __restrict__ p = f.p[k];
+    const int64_t n = f.n[k];
+    const uint32_t a = f.v0[k], b = f.v1[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (i & 1) ? b : a;
+}
+
 // pend != null allows the frame to run without its mid-frame sync (counts
 // left on the device, scratch sized by capacities; see Slot::Pending): it
 // then sets pend->used, appends *pend to the slot's pending list, and its
@@ -544,8 +567,46 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     TRY(ensure(ctx, ws.dval, sizeof(uint32_t) * na1, s));
     int64_t ptiles = std::max<int64_t>((na + kProjThreads - 1) / kProjThreads, 1);
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)ptiles, s));
-    CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)ptiles, s));
-    CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
+    TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 8 * 256, s));
+    // frames kept for the adjoint and the importance walk use per-tile lists
+    // (their per-pixel positions index the tile's own list)
+    const int bl = (save || importance) ? 0 : ctx->bin_log2;
+    // no mid-frame sync: plain coarse-binned frames once the slot knows a key
+    // capacity (the fused emission needs bins of several tiles)
+    const bool deferred = pend && !save && !importance && !job && !sl.prof_count && bl > 0 &&
+                          sl.key_cap > 0 && na > 0 && (int)sl.pending.size() < Slot::kRing;
+    if (pend) pend->used = false;
+    const int32_t bins_x = (cam.tiles_x + (1 << bl) - 1) >> bl;
+    const int32_t bins_y = (cam.tiles_y + (1 << bl) - 1) >> bl;
+    const int64_t nbins = (int64_t)bins_x * bins_y;
+    const int tbits = bits_for((uint32_t)std::max<int64_t>(nbins - 1, 0));
+    if (deferred) {
+        // every scratch word the frame starts from, sized by capacities and
+        // set by one launch: look-back words of the projection and the
+        // emission, the slot's small words, both digit histograms, both sorts'
+        // counters and look-back words, the bin ranges (begin ~0, end 0)
+        const int64_t etiles = std::max<int64_t>((na + kEmitThreads - 1) / kEmitThreads, 1);
+        TRY(ensure(ctx, ws.status2, sizeof(uint32_t) * (size_t)etiles, s));
+        TRY(ensure(ctx, ws.sort, sort_scratch_bytes(na, 32), s));
+        TRY(ensure(ctx, ws.sort2, sort_scratch_bytes(sl.key_cap, tbits), s));
+        TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(nbins, 1), s));
+        FillPlan fp;
+        fp.add(ws.status.as<uint32_t>(), ptiles);
+        fp.add(sl.d_small, kSmWords);
+        fp.add(ws.doffs.as<uint32_t>(), 8 * 256);
+        fp.add(ws.status2.as<uint32_t>(), etiles);
+        fp.add(ws.sort.as<uint32_t>(), (int64_t)(sort_scratch_bytes(na, 32) / sizeof(uint32_t)));
+        fp.add(ws.sort2.as<uint32_t>(), (int64_t)(sort_scratch_bytes(sl.key_cap, tbits) / sizeof(uint32_t)));
+        fp.add(reinterpret_cast<uint32_t*>(ws.ranges.p), 2 * nbins, 0xffffffffu, 0u);
+        int64_t most = 0;
+        for (int k = 0; k < fp.count; ++k) most = std::max(most, fp.n[k]);
+        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((most + 255) / 256, 512));
+        fill_kernel<<<dim3(gx, (unsigned)fp.count), 256, 0, s>>>(fp);
+    } else {
+        CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)ptiles, s));
+        CUDA_TRY(cudaMemsetAsync(sl.d_small, 0, sizeof(uint32_t) * kSmWords, s));
+        CUDA_TRY(cudaMemsetAsync(ws.doffs.p, 0, sizeof(uint32_t) * 8 * 256, s));
+    }
     ProjectOut po;
     po.rec_a = ws.rec_a.as<float4>();
     po.rec_b = ws.rec_b.as<float4>();
@@ -557,23 +618,14 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     po.counts = sl.d_small + kSmProj;
     // digit counts: [0, 1024) the bin sort's (from K4), [1024, 2048) the
     // depth sort's (from K3)
-    TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 8 * 256, s));
-    CUDA_TRY(cudaMemsetAsync(ws.doffs.p, 0, sizeof(uint32_t) * 8 * 256, s));
     po.depth_hist = ws.doffs.as<uint32_t>() + 4 * 256;
-    // frames kept for the adjoint and the importance walk use per-tile lists
-    // (their per-pixel positions index the tile's own list)
-    const int bl = (save || importance) ? 0 : ctx->bin_log2;
     po.bin_log2 = bl;
-    // no mid-frame sync: plain coarse-binned frames once the slot knows a key
-    // capacity (the fused emission needs bins of several tiles)
-    const bool deferred = pend && !save && !importance && !job && !sl.prof_count && bl > 0 &&
-                          sl.key_cap > 0 && na > 0 && (int)sl.pending.size() < Slot::kRing;
-    if (pend) pend->used = false;
     prof_begin(sl, LODGE_STAGE_PROJECT, s);
     launch_project(dsc, cam, act.list, na, (float)act.tA, (float)act.tB, po,
                    ws.status.as<uint32_t>(), sl.d_small + kSmCtrProj, sl.d_small + kSmErr, s,
                    act.blocks ? &act.src : nullptr);
-    prof_end(sl, LODGE_STAGE_PROJECT, s, na > 0 ? 1 : 0);
+    // (the launch count of the projection stage includes the frame's fill)
+    prof_end(sl, LODGE_STAGE_PROJECT, s, (na > 0 ? 1 : 0) + (deferred ? 1 : 0));
     CUDA_TRY(cudaGetLastError());
     int64_t n_vis = 0, n_keys = 0, n_bkeys = 0;
     // device counts (u64 words: the visible count's high word stays 0)
@@ -600,21 +652,18 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
             sl.key_cap = std::max<int64_t>(sl.key_cap, n_bkeys + n_bkeys / 2 + 65536);
         }
     }
-    const int32_t bins_x = (cam.tiles_x + (1 << bl) - 1) >> bl;
-    const int32_t bins_y = (cam.tiles_y + (1 << bl) - 1) >> bl;
-    const int64_t nbins = (int64_t)bins_x * bins_y;
     const size_t nv1 = (size_t)std::max<int64_t>(n_vis, 1), nk1 = (size_t)std::max<int64_t>(n_bkeys, 1);
 
     // ---- K5 depth sort of the visible records
     TRY(ensure(ctx, ws.dkey2, sizeof(uint32_t) * nv1, s));
     TRY(ensure(ctx, ws.dval2, sizeof(uint32_t) * nv1, s));
-    const int tbits = bits_for((uint32_t)std::max<int64_t>(nbins - 1, 0));
-    TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_bkeys, tbits)), s));
+    if (!deferred)   // (frames without a sync set up their own sort scratch above)
+        TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_bkeys, tbits)), s));
     prof_begin(sl, LODGE_STAGE_DEPTH_SORT, s);
     if (n_vis > 1) launch_digit_scan(po.depth_hist, 4, s);
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
                              ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s,
-                             po.depth_hist, true, 0, nullptr, 0, d_nvis);
+                             po.depth_hist, true, 0, nullptr, 0, d_nvis, deferred);
     prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, (n_vis > 1 ? 1 : 0) + onesweep_launches(n_vis, 32, true));
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
@@ -634,14 +683,16 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     TRY(ensure(ctx, ws.koff, sizeof(uint32_t) * (nv1 + 1), s));
     TRY(ensure(ctx, ws.srec, sizeof(uint32_t) * nv1, s));
     TRY(ensure(ctx, ws.srect, sizeof(uint2) * nv1, s));
-    int64_t etiles = std::max<int64_t>((n_vis + kEmitThreads - 1) / kEmitThreads, 1);
-    TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
-    CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
+    if (!deferred) {
+        int64_t etiles = std::max<int64_t>((n_vis + kEmitThreads - 1) / kEmitThreads, 1);
+        TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)etiles, s));
+        CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
+    }
     prof_begin(sl, LODGE_STAGE_EMIT, s);
     if (deferred) {
         launch_emit_counted(rs.as<uint32_t>(), n_vis, d_nvis, ws.rec_rect.as<uint2>(), bins_x, bl, n_bkeys,
                             d_nbk, ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits,
-                            ws.doffs.as<uint32_t>(), ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit,
+                            ws.doffs.as<uint32_t>(), ws.status2.as<uint32_t>(), sl.d_small + kSmCtrEmit,
                             sl.d_small + kSmErr, s);
     } else {
         launch_emit(rs.as<uint32_t>(), n_vis, ws.rec_rect.as<uint2>(), bins_x, bl,
@@ -655,17 +706,20 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     // atomic minimum from 0xffffffff, end by atomic maximum from 0); with at
     // most one key the sort does not run and K6 scans the key list instead
     const bool fused_ranges = deferred || n_bkeys > 1;
-    TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(nbins, 1), s));
-    CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)nbins, s));
-    if (fused_ranges && nbins)
-        CUDA_TRY(cudaMemset2DAsync(ws.ranges.p, sizeof(uint2), 0xff, sizeof(uint32_t), (size_t)nbins, s));
+    if (!deferred) {   // (set up by the frame's fill when deferred)
+        TRY(ensure(ctx, ws.ranges, sizeof(uint2) * (size_t)std::max<int64_t>(nbins, 1), s));
+        CUDA_TRY(cudaMemsetAsync(ws.ranges.p, 0, sizeof(uint2) * (size_t)nbins, s));
+        if (fused_ranges && nbins)
+            CUDA_TRY(cudaMemset2DAsync(ws.ranges.p, sizeof(uint2), 0xff, sizeof(uint32_t), (size_t)nbins, s));
+    }
 
     // ---- K5 bin sort (stable: keeps depth order within a bin)
     prof_begin(sl, LODGE_STAGE_TILE_SORT, s);
     int w2 = launch_onesweep(ws.tkey.as<uint32_t>(), rbits ? nullptr : ws.tval.as<uint32_t>(),
                              ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_bkeys,
-                             tbits, ws.sort.p, sl.d_small + kSmErr, s, ws.doffs.as<uint32_t>(), true, rbits,
-                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins, d_nbk);
+                             tbits, deferred ? ws.sort2.p : ws.sort.p, sl.d_small + kSmErr, s,
+                             ws.doffs.as<uint32_t>(), true, rbits,
+                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins, d_nbk, deferred);
     prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_bkeys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
