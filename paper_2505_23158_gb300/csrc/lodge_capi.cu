@@ -1574,6 +1574,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
             if (q->tail_pending || !q->pending.empty()) cudaStreamSynchronize(rst[k]);
             q->tail_pending = false;
             q->pending.clear();
+            q->share_sms = false;
         }
     };
     for (int i = 0; i < n_cams; ++i) {
@@ -1622,6 +1623,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
         CUDA_TRY(cudaEventRecord(rsl[k]->fence, rst[k]));
         CUDA_TRY(cudaStreamWaitEvent(s, rsl[k]->fence, 0));
     }
+    for (Slot* q : rsl) q->share_sms = false;   // frames rendered again below run alone
     for (int i : redo) {
         r = render_one(ctx, sl0, sc, mode, cams[i], d_rgb + offs[i], s, nullptr, stats ? stats + i : nullptr,
                        true, nullptr, nullptr);
