@@ -204,11 +204,11 @@ def stage_bytes(stage: str, prof: dict) -> float:
     bk = prof.get("bin_keys", k)
     kp = prof.get("packed_keys", 0)
     if stage == "depth_sort":
-        return v * (4 + 4 * 16)          # histogram read + 4 passes of read/write key+value
+        return v * (4 * 16)              # 4 passes of read/write key+value (digits counted by the projection)
     if stage == "emit":
-        # offsets pass: read record id + rect, write offset, id, rect (28 B per
-        # visible); key pass: stage offset/id/rect (16 B), write 4 or 8 B per key
-        return v * (28 + 16) + kp * 4 + (bk - kp) * 8
+        # fused emission: read the record id and its rect (12 B per visible),
+        # write 4 or 8 B per key
+        return v * 12 + kp * 4 + (bk - kp) * 8
     if stage == "tile_sort":
         # every pass (8 bits of the bin id each) reads and writes every key (and value)
         passes = prof.get("bin_sort_passes", 2 * prof["frames"]) / max(prof["frames"], 1)
