@@ -1,5 +1,7 @@
-"""Parity at the full workload sizes, in the launch configuration bench.py
-times (resident scene, one render call per camera):
+"""Parity at the full workload sizes, in the launch configurations bench.py
+times (resident scene; one render call of 30 consecutive poses, whose frames
+take turns on several streams without mid-frame syncs, and one call per
+camera for the single-frame latency):
 
 * outdoor LOD scene, 21.25M Gaussians (16M/4M/1M/250k), 16x16 chunks,
   1920x1080 trajectory: selected sets and sorted tile keys bit-exact against
@@ -117,6 +119,23 @@ def test_outdoor_full_sampled_pixels(outdoor_full, mode_name, pose):
     ref = O.render(osc, cam, g_ref, m_ref, tiles=tiles)
     compare_tiles(img.cpu().numpy(), ref, cam, tiles, f"{mode_name} pose {pose}")
     assert st["n_keys"] == ref["n_keys"] and st["n_visible"] == ref["n_visible"]
+
+
+def test_outdoor_full_camera_list_sampled_pixels(outdoor_full):
+    """The bench's step: one call over 30 consecutive poses.  Frames 0, 11
+    and 29 of the call: sampled tiles within the pixel bars and visible and
+    key counts equal to the oracle's."""
+    torch, api, ctx, sid, scene, cams, osc = outdoor_full
+    step = list(cams[120:150])
+    imgs, stats = ctx.render(sid, api.CHUNK_BLEND, step)
+    for j in (0, 11, 29):
+        cam = step[j]
+        g_ref, m_ref, _ = O.active_set(osc, api.CHUNK_BLEND, cam)
+        tiles = tiles_of(cam, 32, 1000 + j)
+        ref = O.render(osc, cam, g_ref, m_ref, tiles=tiles)
+        compare_tiles(imgs[j].cpu().numpy(), ref, cam, tiles, f"call frame {j}")
+        assert stats[j]["n_keys"] == ref["n_keys"] and stats[j]["n_visible"] == ref["n_visible"]
+        assert stats[j]["n_active"] == g_ref.size
 
 
 # ---------------------------------------------------------------------------
