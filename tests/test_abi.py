@@ -68,3 +68,14 @@ def test_header_entry_points_document_errors():
         assert m, n
         before = src[:m.start()].rstrip()
         assert before.endswith("*/"), n
+
+
+def test_no_gpu_fails_loudly(built):
+    """Without a usable GPU the library refuses to create a context: the
+    product path has no CPU fallback (the oracle is test infrastructure)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2505_23158_gb300.api import Lodge, LodgeError
+    with pytest.raises(LodgeError):
+        Lodge(0)
