@@ -237,11 +237,12 @@ lodge_status lodge_set_bin_size(lodge_ctx* ctx, int32_t log2_tiles);
  * save_for_backward != 0 (n_cams must be 1) the frame's intermediate state
  * is kept under *handle_out until lodge_release.  Returns when every frame
  * has been enqueued and its counters read.  Frames of a resident scene
- * alternate between two streams and, once their stream has seen a frame of
- * the scene, run without a mid-frame synchronisation (scratch sized by
- * capacities, counts read at the end of the call); a frame whose keys
- * outgrow that capacity is rendered again (lodge_profile.redone), so images
- * and counters are those of rendering each camera alone. */
+ * take turns on several streams (six; two for LODGE_FULL) and, once their
+ * stream has seen a frame, run without a mid-frame synchronisation
+ * (scratch sized by capacities, counts read at the end of the call); a
+ * frame whose keys outgrow that capacity is rendered again
+ * (lodge_profile.redone), so images and counters are those of rendering
+ * each camera alone. */
 lodge_status lodge_render(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
                           const lodge_camera* cams, int32_t n_cams, float* d_rgb, void* stream,
                           int32_t save_for_backward, int64_t* handle_out,
