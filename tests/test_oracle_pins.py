@@ -241,6 +241,41 @@ def test_keys_sorted_and_match_rects(plain):
     assert np.array_equal(zb, pr["z"][g])
 
 
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_bin_lists_filtered_per_tile_give_tile_order(plain, k):
+    """Key lists per bin of 2^k x 2^k tiles, built as the library builds them
+    (a stable sort of the visible Gaussians, in index order, by their FP32
+    depth bits, then a stable partition by every bin the tile rect >> k
+    touches), filtered per tile by the tile rect, reproduce each tile's list
+    of the key spec (tile, then depth bits, then index) and nothing else."""
+    scene, cams, osc = plain
+    cam = cams[0]
+    gids = np.arange(osc.n_total)
+    k_ref, g_ref = O.keys(osc, cam, gids)
+    pr = O.project(osc, cam, gids)
+    vis = np.flatnonzero(pr["visible"])
+    zbits = pr["z"][vis].astype(np.float32).view(np.uint32)
+    order = vis[np.argsort(zbits, kind="stable")]
+    rect = pr["rect"]   # tile rect (tx0, ty0, tx1, ty1), inclusive
+    bins = {}
+    for r in order:
+        x0, y0, x1, y1 = (int(v) >> k for v in rect[r])
+        for by in range(y0, y1 + 1):
+            for bx in range(x0, x1 + 1):
+                bins.setdefault((bx, by), []).append(r)
+    tiles_x = (cam.width + 15) // 16
+    tiles_y = (cam.height + 15) // 16
+    ref_tile = (k_ref >> np.uint64(32)).astype(np.int64)
+    n_seen = 0
+    for t in range(tiles_x * tiles_y):
+        tx, ty = t % tiles_x, t // tiles_x
+        lst = [r for r in bins.get((tx >> k, ty >> k), [])
+               if rect[r, 0] <= tx <= rect[r, 2] and rect[r, 1] <= ty <= rect[r, 3]]
+        assert np.array_equal(np.asarray(lst, np.int64), g_ref[ref_tile == t]), (k, t)
+        n_seen += len(lst)
+    assert n_seen == k_ref.size > 0
+
+
 # --------------------------------------------------------------------------
 # EWA projection and SH: textbook checks
 # --------------------------------------------------------------------------
