@@ -537,7 +537,7 @@ def cpu_baseline(args, scene, cams, budget_s=None, max_frames=None):
             O.chunk_select(osc, B)
         t0 = time.perf_counter()
         g, m, _ = O.active_set(osc, O.MODE_CHUNK_BLEND, cam)
-        O.render(osc, cam, g, m)
+        O.render(osc, cam, g, m, bounds=False)
         spent += time.perf_counter() - t0
         done += 1
         idx += 1
@@ -658,7 +658,7 @@ def run_reference(args, rank, world):
             O.chunk_select(osc, B)
         t0 = time.perf_counter()
         g, m, _ = O.active_set(osc, O.MODE_CHUNK_BLEND, cam)
-        O.render(osc, cam, g, m)
+        O.render(osc, cam, g, m, bounds=False)
         return time.perf_counter() - t0
 
     for s in range(args.warmup):

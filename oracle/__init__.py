@@ -17,7 +17,9 @@ Public functions mirror the paper's steps:
   project / keys      per-Gaussian projection records, sorted tile keys
   n_keys              number of tile keys of an active list
   importance          largest blending weight per Gaussian in a view (Sec. 3)
-  render              Eq. 1 compositing (binned or brute force)
+  render              Eq. 1 compositing (binned or brute force), with the range
+                      of results over FP32-reachable knife-edge decisions
+  compare_pixels      the pixel bar against render's result and ranges
   select_thresholds   greedy depth-threshold search (Sec. 3)
   num_clusters        number of chunk clusters (supplementary Eq. 5)
   kmeans_centers      K-means chunk centres from camera positions
@@ -94,7 +96,7 @@ def _load():
                                             C.c_double, P, P]
             lib.orc_chunk_union.restype = C.c_int64
             lib.orc_render.argtypes = [P, P, C.c_int64, P, P, C.c_int32, P, C.c_int32,
-                                       C.c_double, C.c_double, P, P, P, P, P]
+                                       C.c_double, C.c_double, P, P, P, P, P, P, P]
             lib.orc_project.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_importance.argtypes = [P, P, C.c_int64, P, P, C.c_double, C.c_double, P, P]
             lib.orc_keys.argtypes = [P, P, C.c_int64, P, P, P, P, C.c_int64]
@@ -253,10 +255,24 @@ def active_set(osc: OracleScene, mode: int, cam):
     return g, m, info
 
 
+# FP32 error model of the renderer under test (orc_fp32_err in oracle.c): the
+# pixel offset d = p - mu' is off by at most ERR_DD pixels (about four ulp of
+# a 3840-pixel coordinate, the largest image of the workloads), and alpha by a
+# relative 1e-5 from everything else.  Only used to find knife-edge decisions.
+ERR_DD = 1e-3
+ERR_KE0 = 1e-5
+
+
 def render(osc: OracleScene, cam, gids, mults=None, brute=False, tiles=None,
-           ke_alpha=1e-4, ke_t=1e-4):
+           err_dd=ERR_DD, err_ke0=ERR_KE0, bounds=True):
     """Composite the active list; returns dict(rgb (H,W,3) f64, T, ncontrib,
-    knife, n_visible, n_keys, n_pairs_eval)."""
+    knife, knife_code, lo, hi, n_visible, n_keys, n_pairs_eval).
+
+    ``rgb`` takes every Eq. 1 decision (the 1/255 skip, the 1e-4 stop) as
+    FP64 does.  Where FP32 rounding may take one the other way (knife edge,
+    ``knife_code`` 1), every such choice gives a correct render, and ``lo`` /
+    ``hi`` bound the results over all of them per channel; ``knife_code`` 2
+    marks pixels with more decision paths than the oracle enumerates."""
     lib = _load()
     H, W = int(cam.height), int(cam.width)
     g = _c(gids, np.int64)
@@ -264,14 +280,61 @@ def render(osc: OracleScene, cam, gids, mults=None, brute=False, tiles=None,
     t = None if tiles is None else _c(tiles, np.int32)
     rgb = np.zeros((H, W, 3), np.float64); T = np.ones((H, W), np.float64)
     nc = np.zeros((H, W), np.int32); kn = np.zeros((H, W), np.uint8)
+    lo = np.zeros((H, W, 3), np.float64) if bounds else None
+    hi = np.zeros((H, W, 3), np.float64) if bounds else None
     st = _Stats()
     cc = _cam(cam)
     lib.orc_render(osc.ptr, C.byref(cc), g.size, _p(g), None if m is None else _p(m),
                    1 if brute else 0, None if t is None else _p(t),
-                   0 if t is None else t.size, float(ke_alpha), float(ke_t),
-                   _p(rgb), _p(T), _p(nc), _p(kn), C.byref(st))
-    return dict(rgb=rgb, T=T, ncontrib=nc, knife=kn.astype(bool), n_visible=st.n_visible,
-                n_keys=st.n_keys, n_pairs_eval=st.n_pairs_eval)
+                   0 if t is None else t.size, float(err_dd), float(err_ke0),
+                   _p(rgb), _p(T), _p(nc), _p(kn), None if lo is None else _p(lo),
+                   None if hi is None else _p(hi), C.byref(st))
+    return dict(rgb=rgb, T=T, ncontrib=nc, knife=kn.astype(bool), knife_code=kn, lo=lo, hi=hi,
+                n_visible=st.n_visible, n_keys=st.n_keys, n_pairs_eval=st.n_pairs_eval)
+
+
+def compare_pixels(img, ref, mask=None, max_abs=2e-4, mean_abs=1e-5, unresolved_frac=1e-5):
+    """Check an image against ``render``'s result on clamp(rgb, 0, 1).
+
+    Pixels without a knife-edge decision must be within ``max_abs`` of the
+    oracle per channel; knife-edge pixels within ``max_abs`` of the range
+    [lo, hi] of the results their FP32-reachable decisions give; the mean
+    of those distances over all pixels must be at most ``mean_abs``.  Pixels
+    whose decision paths exceed the enumeration (``knife_code`` 2) are left
+    out of the max and may be at most ``unresolved_frac`` of the pixels.
+    ``mask`` (H, W) restricts the check.  Returns the counts and errors;
+    raises AssertionError when a bar is missed."""
+    g = np.clip(np.asarray(img, np.float64), 0, 1)
+    r = np.clip(ref["rgb"], 0, 1)
+    code = ref["knife_code"]
+    if ref["lo"] is None:
+        raise ValueError("compare_pixels needs render(..., bounds=True)")
+    lo = np.clip(ref["lo"], 0, 1); hi = np.clip(ref["hi"], 0, 1)
+    if mask is not None:
+        g, r, code, lo, hi = g[mask], r[mask], code[mask], lo[mask], hi[mask]
+    g = g.reshape(-1, 3); r = r.reshape(-1, 3); lo = lo.reshape(-1, 3); hi = hi.reshape(-1, 3)
+    code = code.reshape(-1)
+    plain = np.abs(g - r)
+    env = np.maximum(np.maximum(lo - g, g - hi), 0.0)
+    dist = np.where((code == 0)[:, None], plain, np.where((code == 1)[:, None], env, plain))
+    checked = code != 2
+    worst = float(dist[checked].max()) if checked.any() else 0.0
+    mean = float(dist.mean()) if dist.size else 0.0
+    n_pix = int(code.size)
+    out = dict(pixels=n_pix, knife=int((code > 0).sum()), unresolved=int((code == 2).sum()),
+               took_other=int(((code == 1) & (plain.max(axis=1) > max_abs)).sum()),
+               max_abs=worst, mean_abs=mean, mean_abs_plain=float(plain.mean()) if plain.size else 0.0)
+    bad = []
+    if worst > max_abs:
+        i = int(np.argmax(np.where(checked[:, None], dist, 0).max(axis=1)))
+        bad.append(f"max-abs {worst:.3g} at pixel {i} (knife code {int(code[i])})")
+    if mean > mean_abs:
+        bad.append(f"mean-abs {mean:.3g}")
+    if out["unresolved"] > math.floor(unresolved_frac * n_pix):
+        bad.append(f"{out['unresolved']} unresolved knife-edge pixels")
+    if bad:
+        raise AssertionError("; ".join(bad) + f" ({out})")
+    return out
 
 
 def project(osc: OracleScene, cam, gids, mults=None):

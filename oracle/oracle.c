@@ -527,37 +527,118 @@ typedef struct {
     double ke_t;       /* relative band around T = 1e-4 flagged as knife edge */
 } orc_knife;
 
-/* Composite one pixel over a depth-sorted list:
+/* Error model of the FP32 renderer being checked, used only to find the
+ * decisions of Eq. 1 that FP32 may take the other way (knife edges).
+ *   dd:  bound on the error of the pixel offset d = p - mu' in pixels (the
+ *        FP32 projected mean and pixel coordinate);
+ *   ke0: bound on the relative error of alpha from everything else (the
+ *        conic, the exponent, the opacity).
+ * A pair's alpha = o' G has relative error at most e = |grad ln G| dd + ke0
+ * with |grad ln G| = |Sigma'^-1 d|; alpha clamped at 0.99 with o' G above
+ * 0.99 (1 + e) is exact.  T = prod (1 - alpha_j) then has relative error at
+ * most E = sum alpha_j / (1 - alpha_j) e_j (first order) plus one rounding
+ * per factor.  The alpha < 1/255 skip is a knife edge when
+ * |alpha - 1/255| <= e / 255, the T < 1e-4 stop when |T_next - 1e-4| <=
+ * E 1e-4. */
+typedef struct {
+    double dd;
+    double ke0;
+} orc_fp32_err;
+
+#define ORC_T_ROUND 1.2e-7  /* two FP32 roundings per transmittance factor */
+#define ORC_MAX_RUNS 256    /* decision paths enumerated per pixel at most */
+
+/* One pass of the per-pixel loop over a depth-sorted list:
  *   alpha = min(0.99, o' exp(-1/2 d^T Sigma'^-1 d)); skip alpha < 1/255;
  *   T_next = T (1 - alpha); stop (without blending) once T_next < 1e-4;
- *   C += T alpha rgb; T = T_next.  Background is black. */
-static void composite_pixel(const orc_splat* sp, const orc_item* list, int64_t n,
-                            double px, double py, const orc_knife* ke,
-                            double* rgb, double* Tout, int32_t* ncontrib, uint8_t* knife)
+ *   C += T alpha rgb; T = T_next.  Background is black.
+ * Knife-edge decisions are numbered in the order they are met on this pass;
+ * those whose bit is set in `flip` are taken the other way.  Returns the
+ * number of knife-edge decisions met. */
+static int composite_pass(const orc_splat* sp, const orc_item* list, int64_t n,
+                          double px, double py, const orc_fp32_err* fe, uint32_t flip,
+                          double* rgb, double* Tout, int32_t* ncontrib)
 {
-    double T = 1.0, C[3] = { 0, 0, 0 };
+    double T = 1.0, E = 0.0, C[3] = { 0, 0, 0 };
     int32_t nc = 0;
-    uint8_t kf = 0;
+    int nk = 0;
     for (int64_t i = 0; i < n; ++i) {
         const orc_splat* s = sp + list[i].rec;
         double dx = px - s->mx, dy = py - s->my;
         double q = s->conic[0] * dx * dx + 2.0 * s->conic[1] * dx * dy + s->conic[2] * dy * dy;
         double G = exp(-0.5 * q);
         double a = s->opacity * G;
-        if (a > ORC_ALPHA_MAX) a = ORC_ALPHA_MAX;
-        if (fabs(a - ORC_ALPHA_MIN) <= ke->ke_alpha * ORC_ALPHA_MIN) kf = 1;
-        if (a < ORC_ALPHA_MIN) continue;
+        double g0 = s->conic[0] * dx + s->conic[1] * dy;
+        double g1 = s->conic[1] * dx + s->conic[2] * dy;
+        double e = sqrt(g0 * g0 + g1 * g1) * fe->dd + fe->ke0;
+        if (a > ORC_ALPHA_MAX) {
+            if (a >= ORC_ALPHA_MAX * (1.0 + e)) e = 0.0;
+            a = ORC_ALPHA_MAX;
+        }
+        int skip = a < ORC_ALPHA_MIN;
+        if (fabs(a - ORC_ALPHA_MIN) <= e * ORC_ALPHA_MIN) {
+            if (nk < 32 && ((flip >> nk) & 1u)) skip = !skip;
+            ++nk;
+        }
+        if (skip) continue;
         double Tn = T * (1.0 - a);
-        if (fabs(Tn - ORC_T_MIN) <= ke->ke_t * ORC_T_MIN) kf = 1;
-        if (Tn < ORC_T_MIN) break;
+        double En = E + a / (1.0 - a) * e + ORC_T_ROUND;
+        int stop = Tn < ORC_T_MIN;
+        if (fabs(Tn - ORC_T_MIN) <= En * ORC_T_MIN) {
+            if (nk < 32 && ((flip >> nk) & 1u)) stop = !stop;
+            ++nk;
+        }
+        if (stop) break;
         for (int c = 0; c < 3; ++c) C[c] += T * a * s->rgb[c];
         T = Tn;
+        E = En;
         ++nc;
     }
     rgb[0] = C[0]; rgb[1] = C[1]; rgb[2] = C[2];
     *Tout = T;
     *ncontrib = nc;
-    *knife = kf;
+    return nk;
+}
+
+/* Composite one pixel.  rgb/T/ncontrib are the pass that takes every
+ * decision as FP64 does.  knife: 0 = no knife-edge decision; 1 = some, and
+ * lo/hi (when given) bound, per channel, every result reachable by taking
+ * any subset of them the other way (all of which are correct FP32 renders);
+ * 2 = more decision paths than ORC_MAX_RUNS, lo/hi incomplete. */
+static void composite_pixel(const orc_splat* sp, const orc_item* list, int64_t n,
+                            double px, double py, const orc_fp32_err* fe,
+                            double* rgb, double* Tout, int32_t* ncontrib, uint8_t* knife,
+                            double* lo, double* hi)
+{
+    int k0 = composite_pass(sp, list, n, px, py, fe, 0u, rgb, Tout, ncontrib);
+    *knife = k0 > 0;
+    if (lo) for (int c = 0; c < 3; ++c) { lo[c] = rgb[c]; hi[c] = rgb[c]; }
+    if (k0 == 0 || !lo) return;
+    /* depth-first over flip sets: a path's decisions before its highest
+     * flipped one are those of its parent, so children flip later ones */
+    uint32_t stack[ORC_MAX_RUNS + 64];
+    int sp_top = 0, runs = 1, incomplete = k0 > 32;
+    for (int j = 0; j < k0 && j < 32; ++j) stack[sp_top++] = 1u << j;
+    while (sp_top > 0) {
+        uint32_t m = stack[--sp_top];
+        if (runs >= ORC_MAX_RUNS) { incomplete = 1; break; }
+        double c3[3], Tt;
+        int32_t nct;
+        int k = composite_pass(sp, list, n, px, py, fe, m, c3, &Tt, &nct);
+        ++runs;
+        for (int c = 0; c < 3; ++c) {
+            if (c3[c] < lo[c]) lo[c] = c3[c];
+            if (c3[c] > hi[c]) hi[c] = c3[c];
+        }
+        if (k > 32) incomplete = 1;
+        int top = 31;
+        while (!((m >> top) & 1u)) --top;
+        for (int j = top + 1; j < k && j < 32; ++j) {
+            if (sp_top >= ORC_MAX_RUNS + 64) { incomplete = 1; break; }
+            stack[sp_top++] = m | (1u << j);
+        }
+    }
+    if (incomplete) *knife = 2;
 }
 
 /* ---------------------------------------------------------------------- */
@@ -577,16 +658,19 @@ typedef struct {
  *     near plane, ordered by (FP32 depth, record).
  * tiles: optional list of tile ids (ty * tiles_x + tx) to render (NULL =
  * all); pixels of other tiles are left untouched.  Outputs are full-image
- * arrays: rgb H*W*3, T H*W, ncontrib H*W, knife H*W. */
+ * arrays: rgb H*W*3, T H*W, ncontrib H*W, knife H*W, and (optional, NULL to
+ * skip the enumeration) lo, hi H*W*3: composite_pixel's bounds over the
+ * FP32-reachable decisions.  err_dd, err_ke0: the FP32 error model
+ * (orc_fp32_err). */
 int orc_render(const orc_scene* sc, const orc_camera* cam, int64_t n_active,
                const int64_t* gids, const float* mults, int32_t mode,
-               const int32_t* tiles, int32_t n_tiles, double ke_alpha, double ke_t,
+               const int32_t* tiles, int32_t n_tiles, double err_dd, double err_ke0,
                double* out_rgb, double* out_T, int32_t* out_nc, uint8_t* out_knife,
-               orc_stats* stats)
+               double* out_lo, double* out_hi, orc_stats* stats)
 {
     const int W = cam->width, H = cam->height;
     const int tx_n = (W + ORC_TILE - 1) / ORC_TILE, ty_n = (H + ORC_TILE - 1) / ORC_TILE;
-    orc_knife ke = { ke_alpha, ke_t };
+    orc_fp32_err fe = { err_dd, err_ke0 };
     orc_splat* sp = (orc_splat*)malloc(sizeof(orc_splat) * (size_t)(n_active ? n_active : 1));
     orc_key_rec* kr = (orc_key_rec*)malloc(sizeof(orc_key_rec) * (size_t)(n_active ? n_active : 1));
     uint8_t* vis = (uint8_t*)calloc((size_t)(n_active ? n_active : 1), 1);
@@ -622,8 +706,10 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, int64_t n_active,
             for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < H; ++py)
                 for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < W; ++px) {
                     int64_t pix = (int64_t)py * W + px;
-                    composite_pixel(sp, all, nvis, px + 0.5, py + 0.5, &ke, out_rgb + 3 * pix,
-                                    out_T + pix, out_nc + pix, out_knife + pix);
+                    composite_pixel(sp, all, nvis, px + 0.5, py + 0.5, &fe, out_rgb + 3 * pix,
+                                    out_T + pix, out_nc + pix, out_knife + pix,
+                                    out_lo ? out_lo + 3 * pix : NULL,
+                                    out_hi ? out_hi + 3 * pix : NULL);
                     pairs += nvis;
                 }
         }
@@ -664,8 +750,10 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, int64_t n_active,
             for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < H; ++py)
                 for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < W; ++px) {
                     int64_t pix = (int64_t)py * W + px;
-                    composite_pixel(sp, L, n, px + 0.5, py + 0.5, &ke, out_rgb + 3 * pix,
-                                    out_T + pix, out_nc + pix, out_knife + pix);
+                    composite_pixel(sp, L, n, px + 0.5, py + 0.5, &fe, out_rgb + 3 * pix,
+                                    out_T + pix, out_nc + pix, out_knife + pix,
+                                    out_lo ? out_lo + 3 * pix : NULL,
+                                    out_hi ? out_hi + 3 * pix : NULL);
                     pairs += n;
                 }
         }

@@ -50,14 +50,11 @@ def compare_tiles(img, ref, cam, tiles, tag):
     for t in tiles:
         x, y = (t % tx) * 16, (t // tx) * 16
         mask[y:y + 16, x:x + 16] = True
-    g = np.clip(img.astype(np.float64), 0, 1)[mask]
-    r = np.clip(ref["rgb"], 0, 1)[mask]
-    kn = ref["knife"][mask]
-    d = np.abs(g - r)
-    worst = d[~kn].max() if (~kn).any() else 0.0
-    assert worst <= MAX_ABS, f"{tag}: max-abs {worst:.3g}"
-    assert d.mean() <= MEAN_ABS, f"{tag}: mean-abs {d.mean():.3g}"
-    assert kn.sum() <= max(3, 0.01 * kn.size), f"{tag}: {kn.sum()} knife-edge pixels"
+    try:
+        out = O.compare_pixels(img, ref, mask=mask, max_abs=MAX_ABS, mean_abs=MEAN_ABS)
+    except AssertionError as e:
+        raise AssertionError(f"{tag}: {e}") from None
+    print(f"[pixels] {tag}: {out}")
 
 
 # ---------------------------------------------------------------------------
@@ -190,13 +187,11 @@ def test_finetune_gradients_on_crop(finetune):
         rn = max(np.linalg.norm(r), 1e-30)
         e = np.linalg.norm(gn[sub] - r.reshape(sub.size, -1)) / rn
         e32 = np.linalg.norm(r32.astype(np.float64) - r) / rn
-        # relative L2 bar: 1e-3, or three times the FP32 evaluation's own
-        # error where the input is that ill-conditioned (sums of many
-        # pixel terms of both signs); the adjoint's sequential evaluation
-        # with division-based T adds a few roundings per term
-        tol = max(1e-3, 3.0 * e32)
+        # relative L2 bar 1e-3 against the FP64 oracle gradient; the error
+        # of the same formulation evaluated in FP32 is printed beside it as
+        # a measure of the input's conditioning
         print(f"{name}: relative L2 error {e:.3g}, FP32 evaluation {e32:.3g}")
-        assert e < tol, f"{name}: relative L2 error {e:.3g} (FP32 evaluation {e32:.3g})"
+        assert e < 1e-3, f"{name}: relative L2 error {e:.3g} (FP32 evaluation {e32:.3g})"
         assert not gn[rest].any(), f"{name}: gradient outside the crop's Gaussians"
 
 

@@ -3,10 +3,13 @@
 Bars (fixed here, derived in the design notes):
   * selected sets, chunk choices, culling, tile rects, sorted tile keys:
     bit-exact;
-  * pixels: on clamp(rgb, 0, 1), max-abs <= 2e-4 per channel over pixels the
-    oracle does not flag as knife edges (an FP32/FP64 difference can flip the
-    1/255 skip or the T < 1e-4 stop there), mean-abs <= 1e-5 over all pixels,
-    and at most 0.1% of pixels flagged.
+  * pixels: on clamp(rgb, 0, 1), max-abs <= 2e-4 per channel and mean-abs
+    <= 1e-5 over all pixels.  Where the FP32 error bound of a decision of
+    Eq. 1 (the 1/255 skip, the T < 1e-4 stop) spans its threshold (a knife
+    edge), either way is a correct render: such a pixel is compared with
+    the range of the oracle's results over those choices, not left out.
+    Pixels whose choices the oracle cannot enumerate may be at most 1e-5 of
+    the image.  Each comparison prints its knife-edge counts.
 """
 import math
 
@@ -46,15 +49,13 @@ def plain_loaded(ctx):
     return scene, cams, O.OracleScene(scene), ctx.load_scene(scene)
 
 
-def compare_images(gpu, ref, knife, tag=""):
-    g = np.clip(gpu.astype(np.float64), 0, 1)
-    r = np.clip(ref, 0, 1)
-    d = np.abs(g - r)
-    ok = ~knife
-    worst = d[ok].max() if ok.any() else 0.0
-    assert worst <= MAX_ABS, f"{tag} max-abs {worst:.3g} at {np.unravel_index(np.argmax(np.where(ok[..., None], d, 0)), d.shape)}"
-    assert d.mean() <= MEAN_ABS, f"{tag} mean-abs {d.mean():.3g}"
-    assert knife.sum() <= max(3, 1e-2 * knife.size), f"{tag} knife-edge pixels {knife.sum()}"
+def compare_images(gpu, ref, tag=""):
+    try:
+        out = O.compare_pixels(gpu, ref, max_abs=MAX_ABS, mean_abs=MEAN_ABS)
+    except AssertionError as e:
+        raise AssertionError(f"{tag}: {e}") from None
+    print(f"[pixels] {tag}: {out}")
+    return out
 
 
 def oracle_keys_u64(osc, cam, gids, mults=None):
@@ -92,7 +93,9 @@ def test_plain_records(ctx, plain_loaded):
     assert np.array_equal(r["gid"].astype(np.int64), vis)
     assert np.array_equal(r["depth"].view(np.uint32), pr["z"][vis].view(np.uint32))
     assert np.array_equal(r["rect"], pr["rect"][vis])
-    assert np.abs(r["mean2"] - pr["mean2"][vis]).max() < 2e-3
+    err2 = np.abs(r["mean2"] - pr["mean2"][vis]).max()
+    print(f"[records] projected mean max error {err2:.3g} px")
+    assert err2 < 1e-4
     assert np.abs(r["opacity"] - pr["opacity"][vis]).max() < 1e-6
     assert np.abs(r["rgb"] - pr["rgb"][vis]).max() < 2e-5
     rel = np.abs(r["conic"] - pr["conic"][vis]) / (np.abs(pr["conic"][vis]).max(axis=1, keepdims=True))
@@ -104,7 +107,7 @@ def test_plain_image(ctx, plain_loaded):
     scene, cams, osc, sid = plain_loaded
     img, st = ctx.render(sid, FULL, cams[0])
     ref = O.render(osc, cams[0], np.arange(osc.n_total))
-    compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], "plain")
+    compare_images(img.cpu().numpy(), ref, "plain")
     assert st["n_visible"] == ref["n_visible"] and st["n_keys"] == ref["n_keys"]
 
 
@@ -121,7 +124,7 @@ def test_ragged_image_sizes(ctx, plain_loaded, wh):
     k_ref, g_ref = oracle_keys_u64(osc, cam, np.arange(osc.n_total))
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref)
     ref = O.render(osc, cam, np.arange(osc.n_total))
-    compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"{wh}")
+    compare_images(img.cpu().numpy(), ref, f"{wh}")
 
 
 def test_nothing_visible(ctx, plain_loaded):
@@ -271,7 +274,7 @@ def test_outdoor_render_parity(ctx, outdoor, mode_name):
         assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref), f"pose {i}"
         assert np.array_equal(kg.cpu().numpy().astype(np.int64), kg_ref)
         ref = O.render(osc, cam, g_ref, m_ref)
-        compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"{mode_name} pose {i}")
+        compare_images(img.cpu().numpy(), ref, f"{mode_name} pose {i}")
 
 
 def test_outdoor_multi_camera_batch(ctx, outdoor, torch_cuda):
@@ -327,7 +330,7 @@ def test_lod_with_randomised_thresholds(ctx, torch_cuda):
         g, _ = O.lod_select(osc, cam.center, dd)
         ref = O.render(osc, cam, g)
         assert st["n_active"] == g.size and st["n_keys"] == ref["n_keys"]
-        compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], "randomised LOD")
+        compare_images(img.cpu().numpy(), ref, "randomised LOD")
 
 
 @pytest.mark.parametrize("which", ["plain", "outdoor"])
@@ -354,7 +357,7 @@ def test_compensated_2d_filter(ctx, torch_cuda, which):
         k_ref, _ = O.keys(osc, cam, g, m)
         assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref)
         ref = O.render(osc, cam, g, m)
-        compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"filter2d {which}")
+        compare_images(img.cpu().numpy(), ref, f"filter2d {which}")
 
 
 @pytest.mark.parametrize("log2", [3, 0])
@@ -415,7 +418,7 @@ def test_binned_lists_same_image(ctx, outdoor, torch_cuda, log2):
                 assert prof["keys"] == st["n_keys"]
                 assert prof["bin_keys"] == _bin_keys(pr["rect"][pr["visible"]], log2)
                 ref = O.render(osc, cam, g_ref, m_ref)
-                compare_images(img.cpu().numpy(), ref["rgb"], ref["knife"], f"bins {log2} pose {i}")
+                compare_images(img.cpu().numpy(), ref, f"bins {log2} pose {i}")
     finally:
         ctx.set_bin_size(3)
 

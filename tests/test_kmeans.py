@@ -53,6 +53,7 @@ def test_kmeans_fixed_point_and_monotone():
     assert all(b <= a0 + 1e-9 for a0, b in zip(obj, obj[1:]))
 
 
+@pytest.mark.gpu
 def test_library_matches_oracle():
     pytest.importorskip("torch")
     from paper_2505_23158_gb300 import api, build

@@ -310,6 +310,41 @@ def test_ewa_matches_monte_carlo_projection():
     assert np.allclose(C2 @ K, np.eye(2), atol=1e-12)
 
 
+def test_quaternion_normalisation():
+    """Activation's unit quaternion: for raw q of any scale the output has unit
+    norm to FP32 rounding and is parallel to q (q_i |q^| = q^_i |q|); and a
+    Gaussian whose raw quaternion is k (cos th/2, sin th/2 a) for k far from 1
+    projects to J (Rod(a, th) diag(s^2) Rod^T) J^T + 0.3 I, with the rotation
+    built by Rodrigues' formula from the axis and angle, not from the oracle's
+    quaternion."""
+    rng = np.random.default_rng(21)
+    n = 64
+    scale = 10.0 ** rng.uniform(-6, 6, n)
+    q = (rng.normal(size=(n, 4)) * scale[:, None]).astype(np.float32)
+    _, qn, _ = O.activate(np.zeros((n, 3), np.float32), q, np.zeros(n, np.float32))
+    qd = q.astype(np.float64); qnd = qn.astype(np.float64)
+    assert np.abs(np.linalg.norm(qnd, axis=1) - 1).max() < 4 * 2.0 ** -24
+    qu = qd / np.linalg.norm(qd, axis=1, keepdims=True)
+    assert np.abs(qnd - qu).max() < 2.0 ** -24
+    # projection of a rotated anisotropic Gaussian at the image centre
+    cam = synth.plain_camera(64, 64)
+    s = np.array([0.03, 0.011, 0.02])
+    for k, (ax, th) in zip([7.25, 1e-3, 3e4], [((1, 2, 3), 0.7), ((-2, 0.5, 1), 2.1), ((0, 0, 1), -1.2)]):
+        a = np.asarray(ax, np.float64); a /= np.linalg.norm(a)
+        qr = k * np.array([math.cos(th / 2), *(math.sin(th / 2) * a)])
+        sc = _single_level_scene([[0, 0, 0]], [np.log(s)], [qr], [0.0], [_sh_for_rgb((1, 1, 1))])
+        osc = O.OracleScene(sc)
+        pr = O.project(osc, cam, np.arange(1))
+        Kx = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        Rod = np.eye(3) + math.sin(th) * Kx + (1 - math.cos(th)) * Kx @ Kx
+        se = osc.scales[0].astype(np.float64)
+        Sig = Rod @ np.diag(se ** 2) @ Rod.T
+        f = cam.fx / 3.0
+        expect = f * f * Sig[:2, :2] + 0.3 * np.eye(2)
+        got = np.array([[pr["cov"][0, 0], pr["cov"][0, 1]], [pr["cov"][0, 1], pr["cov"][0, 2]]])
+        assert np.allclose(got, expect, rtol=1e-6, atol=1e-6 * np.abs(expect).max()), (k, got, expect)
+
+
 def test_sh_basis_orthonormal():
     """The 16 real SH functions are orthonormal on the sphere (Gauss-Legendre
     in cos(theta) x uniform phi quadrature, exact for these degrees)."""
