@@ -363,19 +363,40 @@ lodge_status lodge_sort_pairs(lodge_ctx* ctx, uint32_t* d_keys, uint32_t* d_vals
  * lodge_sort_pairs: d_keys / d_vals (device, caller-owned, n pairs) are
  * sorted in place, stably, on key bits [0, key_bits).  No context is needed
  * and nothing is allocated: scratch is a fixed array in the library's device
- * memory, about 9.1 MB on every device that loads the library, kept until the
- * process exits.
+ * memory, about 12.6 MB on every device that loads the library, kept until
+ * the process exits.
  *   - n may be at most 1,048,576 (2^20); larger n returns LODGE_E_INVALID
  *     before any device work.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before capturing any stream into a graph.
+ *   - The first call on a device looks up the array's device address and
+ *     caches it for the device; make that first call before capturing any
+ *     stream.  The cached address is valid until cudaDeviceReset on that
+ *     device; do not call this function after such a reset.
  *   - Every call on a device shares the array: calls whose device work
  *     overlaps (on different streams) race and give wrong results.  The call
- *     synchronises `stream` before returning.
+ *     copies the status word to the host and synchronises `stream` before
+ *     returning.
  *   - Errors: LODGE_E_INVALID (arguments), LODGE_E_CUDA, LODGE_E_TIMEOUT (a
- *     bounded device-side wait gave up). */
+ *     bounded device-side wait gave up), LODGE_E_OVERFLOW (any other error
+ *     bit the sort's kernels set in the status word). */
 lodge_status lodge_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n,
                                       int32_t key_bits, void* stream);
+
+/* Debug: the decoupled look-back that the library's scans (projection,
+ * emission, sort passes) use to chain per-tile prefix sums, run alone over
+ * n_tiles tiles of one warp each.  Tile i contributes i + 1; tile `missing`
+ * (0 <= missing < n_tiles) never publishes its count, so its successors'
+ * waits run out; missing < 0 lets every tile publish.  Every wait gives up
+ * after spin_limit polls (1 .. 2^22; the library's own scans use 2^22),
+ * records the timeout in a status word and counts the missing tile as 0, so
+ * the kernel always ends.  h_prefix (host, n_tiles) receives each tile's
+ * exclusive prefix (the tiles before `missing` get the exact sums).  The
+ * call allocates its device words itself and synchronises `stream`.
+ * Returns LODGE_E_TIMEOUT when a wait gave up (the context stays usable),
+ * LODGE_E_INVALID for n_tiles outside 1 .. 1024 or a bad limit.  Exposed to
+ * test the bounded waits that keep a stalled predecessor from hanging the
+ * GPU (the paper has no counterpart). */
+lodge_status lodge_debug_lookback(int32_t n_tiles, int32_t missing, uint32_t spin_limit,
+                                  uint32_t* h_prefix, void* stream);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -119,6 +119,7 @@ _SIGS = {
                             C.POINTER(C.c_int64), P],
     "lodge_sort_pairs": [P, P, P, C.c_int64, C.c_int32, P],
     "lodge_sort_pairs_noalloc": [P, P, C.c_int64, C.c_int32, P],
+    "lodge_debug_lookback": [C.c_int32, C.c_int32, C.c_uint32, P, P],
     "lodge_serve": [P, P, C.c_int32, C.POINTER(lodge_serve_opts), P],
     "lodge_residency_stats": [P, C.POINTER(lodge_residency)],
     "lodge_inject_upload_failures": [P, C.c_int32],

@@ -40,10 +40,10 @@ __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
 // Warp-cooperative exclusive look-back for one counter (called by a full
 // warp).  status[tile] must have been published as AGG by this tile already
 // (except tile 0, which needs no look-back).  Returns the exclusive prefix in
-// every lane.  A predecessor that stays unpublished for kSpinLimit polls sets
+// every lane.  A predecessor that stays unpublished for `limit` polls sets
 // kErrTimeout in *err and is counted as 0, so the kernel always terminates.
 __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* status, uint32_t tile,
-                                                  uint32_t* err) {
+                                                  uint32_t* err, uint32_t limit = kSpinLimit) {
     const int lane = threadIdx.x & 31;
     uint32_t prefix = 0;
     int64_t pos = (int64_t)tile - 1;
@@ -54,7 +54,7 @@ __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* status, uint32
             uint32_t spins = 0;
             v = ld_volatile(status + idx);
             while ((v & ~kStVal) == 0u) {
-                if (++spins > kSpinLimit) { atomicOr(err, kErrTimeout); v = kStInc; break; }
+                if (++spins > limit) { atomicOr(err, kErrTimeout); v = kStInc; break; }
                 __nanosleep(32);
                 v = ld_volatile(status + idx);
             }
