@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["lodge", "reference"], default="lodge")
     ap.add_argument("--scale", type=float, default=1.0, help="scene size factor (1.0 = full)")
     ap.add_argument("--n-poses", type=int, default=300)
-    ap.add_argument("--poses-per-step", type=int, default=30)
+    ap.add_argument("--poses-per-step", type=int, default=300,
+                    help="poses per render call (one step); 300 = the whole trajectory")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--full-steps", type=int, default=None)
@@ -66,8 +67,11 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--large", action="store_true",
-                    help="also time the large scene (60M level-0 Gaussians, 64 cameras at 4K)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large scene (60M level-0 Gaussians, 64 cameras at 4K)")
+    ap.add_argument("--no-finetune", action="store_true",
+                    help="skip the fine-tuning step (2M Gaussians, 32 views at 1280x720)")
+    ap.add_argument("--finetune-steps", type=int, default=3)
     ap.add_argument("--large-scale", type=float, default=1.0)
     ap.add_argument("--serve-batch", type=int, default=16,
                     help="frames per step of the batched serving run")
@@ -373,7 +377,7 @@ def run_lodge(args, rank, world, local_rank):
 
     # ---- end to end through the host-buffer entry point (camera H2D, image D2H)
     host = torch.empty(P * npix * 3, dtype=torch.float32, pin_memory=True).numpy().reshape(-1)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps
     def run_e2e():
         # one host-buffer call per step: its cameras in, its images out
         for s in range(e2e_steps):
@@ -389,24 +393,33 @@ def run_lodge(args, rank, world, local_rank):
     launches = sum(prof_timed["launches"].values())
     roof = None
     if dom == "blend":
-        # bound by FP32 arithmetic: algorithmic flops per evaluated pair (Eq. 1
-        # alpha: 9.5, the shared dx counted once per two pixels) and per
-        # composited pair (transmittance and colour: 9), FMA = 2 flops, the
-        # exp2 on the MUFU not counted; peak = 152 SMs x 128 FP32 lanes x 2 x
-        # the maximum SM clock
+        # bound by FP32 arithmetic.  Algorithmic unit: about 15 FP32 ops per
+        # evaluated (pixel, Gaussian) pair (Eq. 1 alpha, transmittance and
+        # colour), the exp2 on the MUFU not counted; peak = SMs x 128 FP32
+        # lanes x 2 (FMA) x the maximum SM clock.  The flops this kernel's
+        # own formulation needs (9.5 per evaluated pair, the shared dx
+        # counted once per two pixels, + 9 per composited pair) are given
+        # beside it.
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         nf = max(prof_cnt["frames"], 1)
-        flops = (9.5 * prof_cnt["blend_pairs"] + 9.0 * prof_cnt["blend_pairs_used"]) / nf
+        pairs = prof_cnt["blend_pairs"] / nf
+        flops = 15.0 * pairs
+        flops_own = (9.5 * prof_cnt["blend_pairs"] + 9.0 * prof_cnt["blend_pairs_used"]) / nf
         t_launch = ms["blend"] / max(prof["frames"], 1) / 1e3
         ach = flops / t_launch / 1e12
         tr = measured_traffic("blend", 0)
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(ach / peak, 4), "traffic": None if tr is None else round(tr), "kernel": "blend",
-                "flops_per_launch": round(flops), "pairs_per_launch": prof_cnt["blend_pairs"] // nf,
+                "ops_per_evaluated_pair": 15, "flops_per_launch": round(flops),
+                "pairs_per_launch": prof_cnt["blend_pairs"] // nf,
                 "composited_pairs_per_launch": prof_cnt["blend_pairs_used"] // nf,
+                "own_count": {"flops_per_launch": round(flops_own),
+                              "achieved": round(flops_own / t_launch / 1e12, 2),
+                              "frac": round(flops_own / t_launch / 1e12 / peak, 4)},
                 "avg_launch_ms": round(t_launch * 1e3, 5),
-                "peak_source": f"{pk_kind} sm_max_mhz x 152 SMs x 128 FP32 lanes x 2"}
+                "peak_source": f"{pk_kind} sm_max_mhz x {n_sm} SMs x 128 FP32 lanes x 2"}
     else:
         by = stage_bytes(dom, prof)
         ach = by / (ms[dom] / 1e3) / 1e9
@@ -470,9 +483,12 @@ def run_lodge(args, rank, world, local_rank):
     if not args.no_serve:
         torch.cuda.empty_cache()
         res["serve_latency"] = run_serve(args, local_rank)
-    if args.large:
+    if not args.no_large:
         torch.cuda.empty_cache()
         res["large_scene"] = run_large(args, local_rank)
+    if not args.no_finetune:
+        torch.cuda.empty_cache()
+        res["finetune_step"] = run_finetune(args, local_rank)
     return res
 
 
@@ -519,17 +535,80 @@ def run_large(args, local_rank):
     return res
 
 
+def run_finetune(args, local_rank):
+    """One fine-tuning step of one level (2M Gaussians of one chunk cell, 32
+    views at 1280x720): forward, L1 against the perturbed scene's images and
+    the adjoint for every view, then an Adam update of all five parameter
+    groups.  Median device time of args.finetune_steps steps after one
+    warm-up step."""
+    import torch
+    from paper_2505_23158_gb300 import synth
+    from paper_2505_23158_gb300.api import Lodge, render_differentiable
+    t0 = time.time()
+    scene = synth.finetune_scene(seed=args.seed, n=2_000_000)
+    target = synth.perturb_scene(scene, seed=args.seed + 1)
+    cams = synth.finetune_cameras(scene, seed=args.seed, n=32)
+    t_gen = time.time() - t0
+    dev = torch.device("cuda", local_rank)
+    lv, tl = scene.levels[0], target.levels[0]
+    n = lv.n
+
+    def params(l, grad):
+        return [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev).requires_grad_(grad)
+                for a in (l.means, l.log_scales, l.quats, l.opacity_logits, l.sh.reshape(n, 48))]
+
+    with Lodge(local_rank) as ctx:
+        tps = params(tl, False)
+        targets = [ctx.render_params(*tps, cam, save=False)[0].clone() for cam in cams]
+        ps = params(lv, True)
+        opt = torch.optim.Adam(ps, lr=1e-4)
+
+        def step():
+            opt.zero_grad()
+            total = torch.zeros((), device=dev)
+            for cam, tgt in zip(cams, targets):
+                img = render_differentiable(ctx, *ps, cam)
+                loss = (img - tgt).abs().mean() / len(cams)
+                loss.backward()
+                total += loss.detach()
+            opt.step()
+            return total
+
+        losses = [float(step())]
+        ts = []
+        for _ in range(max(args.finetune_steps, 1)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            l = step()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            losses.append(float(l))
+    ms = float(np.median(ts))
+    return {"workload": "one level of 2M Gaussians (one 62.5 m chunk cell), 32 views at 1280x720, "
+                        "L1 against the scene with means + N(0, 0.05 m) and logits + N(0, 0.3); "
+                        "a step = forward + adjoint of every view + Adam on all five groups",
+            "ms_per_step": round(ms, 2), "views_per_s": round(32 / (ms / 1e3), 1),
+            "loss_per_step": [round(x, 6) for x in losses], "setup_s": round(t_gen, 1)}
+
+
 def cpu_baseline(args, scene, cams, budget_s=None, max_frames=None):
     """The oracle timed on this host's cores on a bounded sample: whole
-    CHUNK_BLEND frames of the same trajectory until the time budget is
-    spent (at least one)."""
+    CHUNK_BLEND frames of the same trajectory (poses 0, 75, 150, 225, 299
+    first, then every 37th) until the time budget is spent (at least one);
+    beside it, one full-detail frame at pose 0 and the 4,096-Gaussian plain
+    scene at 256x256."""
     import oracle as O
+    from paper_2505_23158_gb300 import synth
     budget_s = args.cpu_budget_s if budget_s is None else budget_s
     osc = O.OracleScene(scene)
     ncores = os.cpu_count()
+    n = len(cams)
+    order = [p for p in (0, 75, 150, 225, 299) if p < n]
     done, spent, idx = 0, 0.0, 0
     while (done == 0 or spent < budget_s) and (max_frames is None or done < max_frames):
-        cam = cams[(idx * 37) % len(cams)]
+        cam = cams[order[idx]] if idx < len(order) else cams[(idx * 37) % n]
         # per-chunk sets are a load-time precompute on both sides; warm them
         A, B, _, _ = O.chunk_pick(osc.centers, cam.center)
         O.chunk_select(osc, A)
@@ -541,9 +620,27 @@ def cpu_baseline(args, scene, cams, budget_s=None, max_frames=None):
         spent += time.perf_counter() - t0
         done += 1
         idx += 1
-    return {"value": round(done / spent, 4), "unit": UNIT, "cores": ncores, "kind": "oracle",
-            "sample": f"{done} whole CHUNK_BLEND {args.width}x{args.height} frames of the trajectory "
-                      f"(FP64 binned oracle, OpenMP over tiles), chunk sets precomputed"}
+    out = {"value": round(done / spent, 4), "unit": UNIT, "cores": ncores, "kind": "oracle",
+           "sample": f"{done} whole CHUNK_BLEND {args.width}x{args.height} frames of the trajectory "
+                     f"(poses 0, 75, 150, 225, 299, then every 37th; FP64 binned oracle, OpenMP over "
+                     f"tiles), chunk sets precomputed"}
+    if max_frames is None:
+        t0 = time.perf_counter()
+        g, _, _ = O.active_set(osc, O.MODE_FULL, cams[0])
+        O.render(osc, cams[0], g, None, bounds=False)
+        t_full = time.perf_counter() - t0
+        pscene, pcams = synth.workload_plain(0)
+        posc = O.OracleScene(pscene)
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 3 or time.perf_counter() - t0 < 1.0:
+            O.render(posc, pcams[0], np.arange(posc.n_total), bounds=False)
+            reps += 1
+        t_plain = (time.perf_counter() - t0) / reps
+        out["full_detail_frames_per_s"] = round(1.0 / t_full, 4)
+        out["full_detail_sample"] = f"pose 0 at full detail ({g.size} level-0 Gaussians), {args.width}x{args.height}"
+        out["plain_256_frames_per_s"] = round(1.0 / t_plain, 2)
+    return out
 
 
 SERVE_LEVEL0 = (2_000_000, 8_000_000, 16_000_000, 30_000_000)

@@ -319,6 +319,36 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
                                  float* d_rgb, void* stream, int32_t save_for_backward,
                                  int64_t* handle_out, lodge_frame_stats* stats);
 
+/* LOD rendering of levels given as raw DEVICE parameters (supplementary
+ * "LOD structure optimization steps": level l is built by fine-tuning G_l
+ * with LOD rendering of the levels up to l, the threshold d_l drawn from
+ * U(0.7 d_l, 1.3 d_l) per step; Sec. 3 "Building LOD").
+ *   num_levels: 1 .. 8, finest first; level_n (host, num_levels): sizes.
+ *   d_means .. d_sh (host arrays of num_levels DEVICE pointers, caller-owned,
+ *     layouts as lodge_level_desc; SH 16-byte aligned); activated on the
+ *     device in FP32 into one gid-ordered store (gid = index into the levels
+ *     concatenated finest first).
+ *   filter_var (host, num_levels): the Eq. 3 variance of each level.
+ *   d_inner (host, num_levels - 1, ascending, metres): this frame's
+ *     thresholds d_1 .. d_{L-1}; Eq. 2 at the camera centre selects level
+ *     l's band [d_l, d_{l+1}).
+ *   d_rgb: H x W x 3 (device).
+ *   d_score (device, total Gaussians, optional): when given, the frame also
+ *     raises the importance scores (as lodge_importance) and cannot be saved.
+ *   save_for_backward: keep the frame for lodge_render_backward, which then
+ *     gives gradients of level train_level only, into arrays of that level's
+ *     size (the other levels are fixed, as in the build).
+ * Synchronous on stream.  Errors: LODGE_E_INVALID (sizes, thresholds,
+ * pointers, train_level), LODGE_E_OOM, LODGE_E_CUDA. */
+lodge_status lodge_render_params_lod(lodge_ctx* ctx, int32_t num_levels, const int64_t* level_n,
+                                     const float* const* d_means, const float* const* d_log_scales,
+                                     const float* const* d_quats, const float* const* d_opacity_logits,
+                                     const float* const* d_sh, int32_t sh_degree, const float* filter_var,
+                                     const double* d_inner, const lodge_camera* cam, float* d_rgb,
+                                     float* d_score, int32_t train_level, void* stream,
+                                     int32_t save_for_backward, int64_t* handle_out,
+                                     lodge_frame_stats* stats);
+
 /* Gradients of a saved lodge_render_params frame.  d_dL_drgb: H x W x 3
  * (device).  Gradients (device, caller-owned, same layouts as the
  * parameters) are ACCUMULATED (+=) so several views can be summed; zero them

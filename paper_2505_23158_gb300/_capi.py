@@ -105,6 +105,8 @@ _SIGS = {
     "lodge_kmeans_centers": [P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P],
     "lodge_importance": [P, C.c_int32, C.c_int, C.c_int32, P, C.c_int32, P, P],
     "lodge_render_lod": [P, C.c_int32, P, C.c_int32, P, P, P, P],
+    "lodge_render_params_lod": [P, C.c_int32, P, P, P, P, P, P, C.c_int32, P, P, P, P, P,
+                                C.c_int32, P, C.c_int32, C.POINTER(C.c_int64), P],
     "lodge_render_batch": [P, C.c_int32, P, P, P, P, P, P, P],
     "lodge_filter_chunk": [P, C.c_int32, C.c_int32, P, C.c_float, C.POINTER(C.c_int64), P],
     "lodge_render": [P, C.c_int32, C.c_int, P, C.c_int32, P, P, C.c_int32,

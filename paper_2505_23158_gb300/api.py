@@ -253,6 +253,40 @@ class Lodge:
                C.byref(st))
         return out, stats_dict(st), (h.value if save else None)
 
+    def render_params_lod(self, levels, cam, d_inner, filter_var, sh_degree: int = 3,
+                          train_level: int = -1, score: Optional[torch.Tensor] = None,
+                          stream=None, save: bool = False):
+        """LOD render of levels given as device parameter tensors.
+
+        levels: per level (finest first) a tuple (means (n,3), log_scales
+        (n,3), quats (n,4), logits (n,), sh (n,48)) of contiguous float32
+        cuda tensors; d_inner: this frame's thresholds d_1 .. d_{L-1};
+        filter_var: per-level Eq. 3 variance.  score: optional importance
+        accumulator over all levels' Gaussians (gid order).  save: keep the
+        frame for render_backward (gradients of `train_level` only).
+        Returns (image, stats, handle or None)."""
+        L = len(levels)
+        ptrs = [(C.c_void_p * L)() for _ in range(5)]
+        ns = (C.c_int64 * L)()
+        dev = None
+        for l, lv in enumerate(levels):
+            assert len(lv) == 5
+            for k, t in enumerate(lv):
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                ptrs[k][l] = t.data_ptr()
+            ns[l] = int(lv[0].shape[0])
+            dev = lv[0].device
+        fv = (C.c_float * L)(*[float(v) for v in filter_var])
+        d = np.ascontiguousarray(d_inner, np.float64).reshape(-1)
+        assert d.size == L - 1
+        out = torch.empty(cam.height, cam.width, 3, dtype=torch.float32, device=dev)
+        st = A.lodge_frame_stats()
+        h = C.c_int64(0)
+        A.call("lodge_render_params_lod", self._h, L, ns, *ptrs, int(sh_degree), fv,
+               C.c_void_p(d.ctypes.data) if d.size else None, C.byref(camera_struct(cam)), _ptr(out),
+               _ptr(score), int(train_level), _stream(stream), int(save), C.byref(h), C.byref(st))
+        return out, stats_dict(st), (h.value if save else None)
+
     def render_backward(self, handle: int, dL_drgb: torch.Tensor, g_means=None, g_log_scales=None,
                         g_quats=None, g_logits=None, g_sh=None, stream=None):
         A.call("lodge_render_backward", self._h, int(handle), _ptr(dL_drgb.contiguous()),
@@ -422,6 +456,43 @@ class _RenderParams(torch.autograd.Function):
         finally:
             fctx.lodge.release(fctx.handle)
         return (*gs, None, None, None, None)
+
+
+class _RenderLevelLod(torch.autograd.Function):
+    """LOD render of several levels in which only one level's parameters are
+    trained: forward lodge_render_params_lod, adjoint lodge_render_backward
+    restricted to that level."""
+
+    @staticmethod
+    def forward(fctx, means, log_scales, quats, logits, sh, lodge, fixed, train_level, cam, d_inner,
+                filter_var, sh_degree):
+        trained = (means, log_scales, quats, logits, sh)
+        levels = list(fixed[:train_level]) + [trained] + list(fixed[train_level:])
+        img, stats, h = lodge.render_params_lod(levels, cam, d_inner, filter_var, sh_degree=sh_degree,
+                                                train_level=train_level, save=True)
+        fctx.lodge = lodge
+        fctx.handle = h
+        fctx.save_for_backward(*trained)
+        return img
+
+    @staticmethod
+    def backward(fctx, g_img):
+        trained = fctx.saved_tensors
+        gs = [torch.zeros_like(t) for t in trained]
+        try:
+            fctx.lodge.render_backward(fctx.handle, g_img.contiguous(), *gs)
+        finally:
+            fctx.lodge.release(fctx.handle)
+        return (*gs, None, None, None, None, None, None, None)
+
+
+def render_level_lod(lodge: Lodge, trained, fixed, train_level: int, cam, d_inner, filter_var,
+                     sh_degree: int = 3):
+    """Image of an LOD frame over `fixed` levels plus the trained level
+    (inserted at position train_level) that backpropagates to the trained
+    level's five parameter tensors only."""
+    return _RenderLevelLod.apply(*trained, lodge, list(fixed), int(train_level), cam, d_inner,
+                                 list(filter_var), sh_degree)
 
 
 def render_differentiable(lodge: Lodge, means, log_scales, quats, logits, sh, cam,

@@ -391,10 +391,21 @@ void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t*
                       uint32_t vmask, int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                       int64_t n_rec, const float* T_final, const uint32_t* last,
                       const float* dL_drgb, double* grec, cudaStream_t s);
+// Levels of a parameter frame as the adjoint sees them: the Eq. 3 filter
+// variance of each level (gid ranges level_off) and the trained level's gid
+// range [train_lo, train_hi).  Records outside it get no gradient; the raw
+// parameter and gradient arrays hold the trained level only and are indexed
+// by gid - train_lo (the activated arrays by gid).
+struct BwdLevels {
+    int32_t num_levels = 1;
+    int64_t level_off[kMaxLevels + 1] = {0};
+    float filter_var[kMaxLevels] = {0};
+    int64_t train_lo = 0, train_hi = 0;
+};
 void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec_gid,
                         const double* grec, const float* means, const float4* act_so,
                         const float4* act_q, const float* quats, const float* sh, int sh_degree,
-                        float filter_var, float* g_means, float* g_log_scales, float* g_quats,
+                        const BwdLevels& lv, float* g_means, float* g_log_scales, float* g_quats,
                         float* g_logits, float* g_sh, cudaStream_t s);
 
 // records msg as the calling thread's lodge_last_error message; returns s

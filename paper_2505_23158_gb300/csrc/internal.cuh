@@ -79,7 +79,7 @@ struct Saved {
     const float *means = nullptr, *log_scales = nullptr, *quats = nullptr, *logits = nullptr,
                 *sh = nullptr;
     int sh_degree = 3;
-    float filter_var = 0.f;
+    BwdLevels lv;            // levels, filter variances and the trained level's gid range
     DBuf act_so, act_q;
 };
 

@@ -197,7 +197,7 @@ struct BwdParams {
     const float4* act_q;         // unit quaternion
     const float* sh;             // N x 48
     int32_t sh_degree;
-    float filter_var;
+    BwdLevels lv;
     float* g_means;
     float* g_log_scales;
     float* g_quats;
@@ -209,7 +209,11 @@ struct BwdParams {
 __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= P.n_rec) return;
-    const uint32_t g = P.rec_gid[r];
+    const uint32_t gid = P.rec_gid[r];
+    // only the trained level's Gaussians receive gradients (the other
+    // levels of an LOD frame are fixed)
+    if ((int64_t)gid < P.lv.train_lo || (int64_t)gid >= P.lv.train_hi) return;
+    const size_t g = (size_t)((int64_t)gid - P.lv.train_lo);   // into the trained level's arrays
     const size_t nr = (size_t)P.n_rec;
     const float gmx = (float)P.grec[r], gmy = (float)P.grec[nr + r];
     const float gu00 = (float)P.grec[2 * nr + r], gu01 = (float)P.grec[3 * nr + r],
@@ -226,9 +230,11 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
     const float px = R[0] * e0 + R[1] * e1 + R[2] * e2 + cam.tp[0];
     const float py = R[3] * e0 + R[4] * e1 + R[5] * e2 + cam.tp[1];
     const float pz = R[6] * e0 + R[7] * e1 + R[8] * e2 + cam.tp[2];
-    const float4 so = P.act_so[g];
-    const float4 qn = P.act_q[g];
-    const float v = P.filter_var;
+    const float4 so = P.act_so[gid];
+    const float4 qn = P.act_q[gid];
+    int lvl = 0;
+    while (lvl + 1 < P.lv.num_levels && (int64_t)gid >= P.lv.level_off[lvl + 1]) ++lvl;
+    const float v = P.lv.filter_var[lvl];
     float s[3] = {so.x, so.y, so.z}, sig[3] = {so.x, so.y, so.z};
     float comp = 1.f;
     if (v > 0.f) {
@@ -386,7 +392,7 @@ void launch_blend_bwd(const DevCamera& cam, const uint2* ranges, const uint32_t*
 void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec_gid,
                         const double* grec, const float* means, const float4* act_so,
                         const float4* act_q, const float* quats, const float* sh, int sh_degree,
-                        float filter_var, float* g_means, float* g_log_scales, float* g_quats,
+                        const BwdLevels& lv, float* g_means, float* g_log_scales, float* g_quats,
                         float* g_logits, float* g_sh, cudaStream_t s) {
     if (n_rec == 0) return;
     BwdParams P;
@@ -400,7 +406,7 @@ void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec
     P.quats = quats;
     P.sh = sh;
     P.sh_degree = sh_degree;
-    P.filter_var = filter_var;
+    P.lv = lv;
     P.g_means = g_means;
     P.g_log_scales = g_log_scales;
     P.g_quats = g_quats;

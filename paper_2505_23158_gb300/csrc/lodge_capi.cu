@@ -1862,7 +1862,119 @@ lodge_status lodge_render_params(lodge_ctx* ctx, int64_t n, const float* d_means
         sv->means = d_means; sv->log_scales = d_log_scales; sv->quats = d_quats;
         sv->logits = d_opacity_logits; sv->sh = d_sh;
         sv->sh_degree = sh_degree;
-        sv->filter_var = filter_var;
+        sv->lv.num_levels = 1;
+        for (int l = 1; l <= kMaxLevels; ++l) sv->lv.level_off[l] = n;
+        sv->lv.filter_var[0] = filter_var;
+        sv->lv.train_lo = 0;
+        sv->lv.train_hi = n;
+        take(sv->act_so, ws.act_so);
+        take(sv->act_q, ws.act_q);
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        int64_t h = ctx->next_handle++;
+        ctx->saved[h] = std::move(sv);
+        *handle_out = h;
+    }
+    return LODGE_OK;
+}
+
+// LOD rendering of levels given as raw device parameters (supplementary
+// "LOD structure optimization steps": the build of level l fine-tunes G_l
+// with LOD rendering of the levels up to l, d_l drawn per step).  The levels
+// are activated into one gid-ordered store (finest first), Eq. 2 selects
+// each level's band at the camera centre with this frame's thresholds, and
+// the frame is rendered as any LOD frame.  With d_score it raises the
+// importance scores instead (K12); with save_for_backward the adjoint will
+// give gradients of level train_level only.
+lodge_status lodge_render_params_lod(lodge_ctx* ctx, int32_t num_levels, const int64_t* level_n,
+                                     const float* const* d_means, const float* const* d_log_scales,
+                                     const float* const* d_quats, const float* const* d_opacity_logits,
+                                     const float* const* d_sh, int32_t sh_degree, const float* filter_var,
+                                     const double* d_inner, const lodge_camera* cam, float* d_rgb,
+                                     float* d_score, int32_t train_level, void* stream,
+                                     int32_t save_for_backward, int64_t* handle_out,
+                                     lodge_frame_stats* stats) {
+    if (!ctx || !cam || !d_rgb || !level_n || !filter_var) return fail(LODGE_E_INVALID, "bad argument");
+    if (num_levels < 1 || num_levels > kMaxLevels) return fail(LODGE_E_INVALID, "num_levels outside 1..%d", kMaxLevels);
+    if (num_levels > 1 && !d_inner) return fail(LODGE_E_INVALID, "d_inner is NULL");
+    if (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh)
+        return fail(LODGE_E_INVALID, "NULL parameter pointer table");
+    if (sh_degree < 0 || sh_degree > 3) return fail(LODGE_E_INVALID, "sh_degree outside 0..3");
+    if (save_for_backward && (!handle_out || d_score))
+        return fail(LODGE_E_INVALID, "save_for_backward needs handle_out and no d_score");
+    if (save_for_backward && (train_level < 0 || train_level >= num_levels))
+        return fail(LODGE_E_INVALID, "train_level outside 0..num_levels-1");
+    int64_t off[kMaxLevels + 1] = {0};
+    for (int l = 0; l < num_levels; ++l) {
+        if (level_n[l] < 0) return fail(LODGE_E_INVALID, "level %d: negative size", l);
+        if (level_n[l] > 0 && (!d_means[l] || !d_log_scales[l] || !d_quats[l] || !d_opacity_logits[l] || !d_sh[l]))
+            return fail(LODGE_E_INVALID, "level %d: NULL parameter array", l);
+        if (level_n[l] > 0 && (uintptr_t)d_sh[l] % 16 != 0)
+            return fail(LODGE_E_INVALID, "level %d: SH array must be 16-byte aligned", l);
+        if (!(filter_var[l] >= 0.f) || !std::isfinite(filter_var[l]))
+            return fail(LODGE_E_INVALID, "level %d: filter variance must be finite and >= 0", l);
+        off[l + 1] = off[l] + level_n[l];
+    }
+    for (int l = num_levels + 1; l <= kMaxLevels; ++l) off[l] = off[num_levels];
+    const int64_t n = off[num_levels];
+    if (n >= (1ll << 30)) return fail(LODGE_E_INVALID, "too many Gaussians");
+    for (int l = 0; l + 1 < num_levels; ++l)
+        if (!(d_inner[l] >= 0.0) || (l && !(d_inner[l] >= d_inner[l - 1])))
+            return fail(LODGE_E_INVALID, "thresholds must be non-negative and ascending");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot& sl = *ctx->slots[0];
+    Workspace& ws = sl.ws;
+    const size_t n1 = (size_t)std::max<int64_t>(n, 1);
+    const int64_t NP = std::max<int64_t>((n + 63) / 64 * 64, 64);
+    TRY(ensure(ctx, ws.act_so, sizeof(float4) * n1, s));
+    TRY(ensure(ctx, ws.act_q, sizeof(float4) * n1, s));
+    TRY(ensure(ctx, ws.mtmp, sizeof(float) * 3 * (size_t)NP + sizeof(float4) * 12 * (size_t)NP, s));
+    float* mp = ws.mtmp.as<float>();
+    float4* shp = reinterpret_cast<float4*>(mp + 3 * NP);
+    for (int l = 0; l < num_levels; ++l) {
+        const int64_t nl = level_n[l], o = off[l];
+        if (!nl) continue;
+        unsigned nb = (unsigned)((nl + 255) / 256);
+        activate_kernel<<<nb, 256, 0, s>>>(nl, d_log_scales[l], d_quats[l], d_opacity_logits[l],
+                                           ws.act_so.as<float4>() + o, ws.act_q.as<float4>() + o);
+        planes_kernel<<<nb, 256, 0, s>>>(nl, d_means[l], mp + o, mp + NP + o, mp + 2 * NP + o);
+        sh_planes_kernel<<<nb, 256, 0, s>>>(nl, d_sh[l], shp + o, NP);
+        CUDA_TRY(cudaGetLastError());
+    }
+    DevScene d;
+    d.n_total = n;
+    d.num_levels = num_levels;
+    d.sh_degree = sh_degree;
+    for (int l = 0; l <= kMaxLevels; ++l) d.level_off[l] = off[l];
+    for (int l = 0; l < num_levels; ++l) d.filter_var[l] = filter_var[l];
+    d.mx = mp; d.my = mp + NP; d.mz = mp + 2 * NP;
+    d.scale_op = ws.act_so.as<float4>();
+    d.quat = ws.act_q.as<float4>();
+    d.sh = shp;
+    Active act;
+    if (num_levels > 1) {
+        int64_t na = 0;
+        TRY(run_lod_select(ctx, sl, d, cam->center, d_inner, s, &na));
+        act.list = ws.list.as<uint32_t>();
+        act.n = na;
+    } else {
+        act.n = n;
+    }
+    std::unique_ptr<Saved> sv;
+    if (save_for_backward) sv.reset(new Saved());
+    TRY(render_frame(ctx, sl, d, act, *cam, d_rgb, s, sv.get(), stats, true, d_score));
+    if (sv) {
+        const int tl = train_level;
+        sv->params = true;
+        sv->n = n;
+        sv->means = d_means[tl]; sv->log_scales = d_log_scales[tl]; sv->quats = d_quats[tl];
+        sv->logits = d_opacity_logits[tl]; sv->sh = d_sh[tl];
+        sv->sh_degree = sh_degree;
+        sv->lv.num_levels = num_levels;
+        for (int l = 0; l <= kMaxLevels; ++l) sv->lv.level_off[l] = off[l];
+        for (int l = 0; l < num_levels; ++l) sv->lv.filter_var[l] = filter_var[l];
+        sv->lv.train_lo = off[tl];
+        sv->lv.train_hi = off[tl + 1];
         take(sv->act_so, ws.act_so);
         take(sv->act_q, ws.act_q);
         std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -1895,7 +2007,7 @@ lodge_status lodge_render_backward(lodge_ctx* ctx, int64_t handle, const float* 
                      v.last.as<uint32_t>(), d_dL_drgb, ws.grec.as<double>(), s);
     launch_project_bwd(v.cam, v.n_vis, v.rec_gid.as<uint32_t>(), ws.grec.as<double>(), v.means,
                        v.act_so.as<float4>(), v.act_q.as<float4>(), v.quats, v.sh, v.sh_degree,
-                       v.filter_var, d_g_means, d_g_log_scales, d_g_quats, d_g_opacity_logits, d_g_sh, s);
+                       v.lv, d_g_means, d_g_log_scales, d_g_quats, d_g_opacity_logits, d_g_sh, s);
     CUDA_TRY(cudaGetLastError());
     return sync_slot(ctx, sl, s);
 }

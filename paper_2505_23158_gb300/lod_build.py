@@ -1,0 +1,115 @@
+"""Per-level LOD build (supplementary "LOD structure optimization steps";
+Sec. 3 "Building LOD") on the library's render and adjoint.
+
+Level l is made from the finest level G_0:
+  1. copy G_0's parameters and give the copy the Eq. 3 smoothing filter of
+     depth d_l (a per-level variance added to the covariance at render
+     time; the parameters themselves are unchanged, so optimisation cannot
+     shrink a Gaussian below the filter);
+  2. three rounds, with importance thresholds 0.2 gamma, 0.6 gamma, gamma:
+     a. score every Gaussian of the levels 0..l by its importance (the
+        largest blending weight T alpha it receives, Sec. 3 "Importance
+        pruning") over the views, rendering LOD frames with thresholds
+        d_1 .. d_l, and prune the Gaussians of G_l scoring below the round's
+        threshold (the finer levels are not pruned);
+     b. run `steps` optimisation steps (the paper: 1000) of LOD rendering
+        over the levels 0..l in which d_l is drawn from U(0.7 d_l, 1.3 d_l)
+        per step, updating only G_l's parameters.
+The paper's loss is DSSIM + L1; this build uses L1 (DSSIM is not part of
+this library).  Adam drives the updates; the render, the importance walk and
+the gradients are the library's kernels (lodge_render_params_lod,
+lodge_render_backward).
+"""
+from __future__ import annotations
+
+from typing import Callable, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from .api import Lodge, render_level_lod
+
+ROUND_FRACTIONS = (0.2, 0.6, 1.0)
+
+
+def level_params(level, device) -> tuple:
+    """A synth.Level's raw parameters as contiguous float32 cuda tensors
+    (means, log_scales, quats, logits, sh (n, 48))."""
+    n = level.n
+    arrs = (level.means, level.log_scales, level.quats, level.opacity_logits,
+            np.asarray(level.sh, np.float32).reshape(n, 48))
+    return tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device) for a in arrs)
+
+
+def filter_variance(scale: float, depth: float, focal: float) -> float:
+    """Eq. 3 smoothing filter of depth d for a camera of focal length f
+    (pixels), read as a variance: (s d / f)^2."""
+    return float((scale * depth / focal) ** 2)
+
+
+def importance_scores(ctx: Lodge, levels: Sequence[tuple], views, d_inner, filter_var,
+                      sh_degree: int = 3) -> torch.Tensor:
+    """Largest blending weight of every Gaussian of `levels` (gid order,
+    finest first) over LOD renders of the views at thresholds d_inner."""
+    n = sum(int(l[0].shape[0]) for l in levels)
+    score = torch.zeros(max(n, 1), dtype=torch.float32, device=levels[0][0].device)
+    for cam in views:
+        ctx.render_params_lod(list(levels), cam, d_inner, filter_var, sh_degree=sh_degree, score=score)
+    return score[:n]
+
+
+def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[float], views,
+                targets: Sequence[torch.Tensor], gamma: float, filter_var_l: float,
+                filter_var_fixed: Sequence[float], steps: int = 1000, lr: Optional[dict] = None,
+                seed: int = 0, sh_degree: int = 3, keep_params: bool = False,
+                on_round: Optional[Callable[[int, dict], None]] = None):
+    """Build level l = len(fixed) from `base` (G_0's parameters).
+
+    fixed: parameters of levels 0 .. l-1 (not updated); d: thresholds
+    d_1 .. d_l; views / targets: cameras and their target images (H, W, 3);
+    gamma: importance threshold of the last round; filter_var_l /
+    filter_var_fixed: Eq. 3 variances of the new and the fixed levels.
+    Returns (parameters of G_l, history) where history holds per round the
+    threshold, the scores of G_l before pruning, the kept count and the loss
+    of every step (and, with keep_params, host copies of the parameters that
+    were scored and of those after the round's steps)."""
+    l = len(fixed)
+    assert len(d) == l and l >= 1
+    lr = lr or {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "logits": 5e-2, "sh": 2.5e-3}
+    rng = np.random.default_rng(seed)
+    fvs = list(filter_var_fixed) + [filter_var_l]
+    d = np.asarray(d, np.float64)
+    cur = [t.clone() for t in base]
+    off = sum(int(f[0].shape[0]) for f in fixed)
+    history: List[dict] = []
+    for r, frac in enumerate(ROUND_FRACTIONS):
+        thr = frac * gamma
+        score = importance_scores(ctx, list(fixed) + [tuple(cur)], views, d, fvs, sh_degree)
+        s_l = score[off:off + int(cur[0].shape[0])]
+        scored = [t.cpu().numpy() for t in cur] if keep_params else None
+        keep = s_l >= thr
+        cur = [t[keep].contiguous() for t in cur]
+        params = [t.detach().clone().requires_grad_(True) for t in cur]
+        names = ("means", "log_scales", "quats", "logits", "sh")
+        opt = torch.optim.Adam([{"params": [p], "lr": lr[k]} for p, k in zip(params, names)], eps=1e-15)
+        losses = []
+        for step in range(steps):
+            i = step % len(views)
+            dd = d.copy()
+            dd[-1] = rng.uniform(0.7, 1.3) * d[-1]
+            img = render_level_lod(ctx, params, fixed, l, views[i], dd, fvs, sh_degree)
+            loss = (img - targets[i]).abs().mean()
+            opt.zero_grad(set_to_none=True)
+            loss.backward()
+            opt.step()
+            losses.append(float(loss.detach()))
+        cur = [p.detach().contiguous() for p in params]
+        rec = {"round": r, "threshold": thr, "scores": s_l.detach().cpu().numpy(),
+               "kept": int(keep.sum()), "losses": np.asarray(losses)}
+        if keep_params:
+            rec["scored_params"] = scored
+            rec["params"] = [t.cpu().numpy() for t in cur]
+        history.append(rec)
+        if on_round:
+            on_round(r, rec)
+    return tuple(cur), history

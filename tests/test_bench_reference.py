@@ -22,3 +22,19 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_sample_and_extras():
+    """The CPU-baseline leg on a small scene: the CHUNK_BLEND sample starts
+    at the listed poses and the full-detail and plain-scene extras are
+    reported."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    from paper_2505_23158_gb300 import synth
+    scene, cams = synth.workload_outdoor(seed=0, n_poses=8, scale=0.003, width=96, height_px=64)
+    args = argparse.Namespace(cpu_budget_s=0.2, width=96, height=64)
+    out = bench.cpu_baseline(args, scene, cams)
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] >= 1
+    assert out["full_detail_frames_per_s"] > 0 and out["plain_256_frames_per_s"] > 0
+    assert "poses 0, 75" in out["sample"]
