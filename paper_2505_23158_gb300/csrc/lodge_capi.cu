@@ -565,7 +565,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     TRY(ensure(ctx, ws.rec_gid, sizeof(uint32_t) * na1, s));
     TRY(ensure(ctx, ws.dkey, sizeof(uint32_t) * na1, s));
     TRY(ensure(ctx, ws.dval, sizeof(uint32_t) * na1, s));
-    int64_t ptiles = std::max<int64_t>((na + kProjThreads - 1) / kProjThreads, 1);
+    const int64_t ptiles = proj_status_words(na);
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)ptiles, s));
     TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 8 * 256, s));
     // frames kept for the adjoint and the importance walk use per-tile lists
