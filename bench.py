@@ -64,7 +64,11 @@ def parse():
     ap.add_argument("--bin-log2", type=int, default=None,
                     help="key lists per bin of 2^k x 2^k tiles (default: the library's)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="duration of the serving run at --serve-rate (step mode)")
+    ap.add_argument("--serve-warmup-s", type=float, default=5.0)
+    ap.add_argument("--serve-slot-seconds", type=float, default=10.0,
+                    help="duration of the slot-worker serving run")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-large", action="store_true",
@@ -665,8 +669,41 @@ def serve_requests(rng, scenes, sids, n, rate, t0=0.0):
     return reqs
 
 
+def serve_summary(reqs, results, rate, duration):
+    """Latency percentiles of one serving run, split into queueing (arrival
+    to admission), service (admission to image done) and by whether the
+    request had to gather a chunk block into HBM."""
+    ok = [(q, r) for q, r in zip(reqs, results) if r["status"] == 0]
+    lat = np.array([r["latency_s"] for _, r in ok]) * 1e3
+    queue = np.array([r["start_s"] - q[3] for q, r in ok]) * 1e3
+    serv = np.array([r["finish_s"] - r["start_s"] for _, r in ok]) * 1e3
+    up = np.array([r["uploads"] > 0 for _, r in ok], bool)
+    t_end = max(r["finish_s"] for r in results) if results else 1.0
+
+    def pct(a, p):
+        return round(float(np.percentile(a, p)), 3) if a.size else None
+
+    by_res = {}
+    for q, r in ok:
+        by_res.setdefault(f"{q[2].width}x{q[2].height}", []).append(r["latency_s"] * 1e3)
+    steps = [r["step_frames"] for _, r in ok]
+    return {"rate_rps": rate, "duration_s": duration, "requests": len(reqs), "completed": len(ok),
+            "throughput_rps": round(len(ok) / t_end, 2),
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "queue_p50_ms": pct(queue, 50), "queue_p99_ms": pct(queue, 99),
+            "service_p50_ms": pct(serv, 50), "service_p99_ms": pct(serv, 99),
+            "p99_ms_with_upload": pct(lat[up], 99), "p99_ms_no_upload": pct(lat[~up], 99),
+            "requests_with_upload": int(up.sum()),
+            # per request: the frames of the step that served it (request-weighted)
+            "mean_frames_per_step": round(float(np.mean(steps)), 2) if steps else None,
+            "p99_ms_by_resolution": {k: round(float(np.percentile(v, 99)), 3) for k, v in sorted(by_res.items())}}
+
+
 def run_serve(args, local_rank):
-    """Serving stream over four streamed scenes under an HBM budget."""
+    """Serving stream over four streamed scenes under an HBM budget: request
+    steps (the requests that have arrived, composited by one persistent
+    launch per step) at the configuration's rate and at higher rates, and
+    the same stream on slot workers."""
     from paper_2505_23158_gb300 import synth
     from paper_2505_23158_gb300.api import STREAMED, Lodge
     t0 = time.time()
@@ -678,6 +715,8 @@ def run_serve(args, local_rank):
                                           grid=16))
     t_gen = time.time() - t0
     budget = int(args.serve_budget_gb * (1 << 30))
+    rates = [(args.serve_rate, args.serve_seconds)] + [(r, d) for r, d in ((1000.0, 10.0), (4000.0, 5.0))
+                                                         if r > args.serve_rate]
     with Lodge(local_rank, hbm_budget_bytes=budget) as ctx:
         if args.bin_log2 is not None:
             ctx.set_bin_size(args.bin_log2)
@@ -685,56 +724,42 @@ def run_serve(args, local_rank):
         sids = [ctx.load_scene(sc, STREAMED) for sc in scenes]
         t_load = time.time() - t0
         rng = np.random.default_rng(args.seed + 77)
-        warm = serve_requests(rng, scenes, sids, int(2 * args.serve_rate), args.serve_rate)
-        ctx.serve(warm, slots=args.serve_slots, realtime=True)
+        warm = serve_requests(rng, scenes, sids, int(args.serve_warmup_s * args.serve_rate), args.serve_rate)
+        ctx.serve(warm, realtime=True, batch=args.serve_batch)
         r0 = ctx.residency_stats()
-        reqs = serve_requests(rng, scenes, sids, int(args.serve_seconds * args.serve_rate),
-                              args.serve_rate)
         clk = ClockSampler(local_rank)
         clk.start()
-        results, _ = ctx.serve(reqs, slots=args.serve_slots, realtime=True)
+        sweep = []
+        for rate, dur in rates:
+            reqs = serve_requests(rng, scenes, sids, int(dur * rate), rate)
+            res, _ = ctx.serve(reqs, realtime=True, batch=args.serve_batch)
+            sweep.append(serve_summary(reqs, res, rate, dur))
         clocks = clk.stop()
         r1 = ctx.residency_stats()
-        # the same stream served in steps, each step's frames composited by
-        # one launch (a fresh draw of the same arrival process)
-        breqs = serve_requests(rng, scenes, sids, int(args.serve_seconds * args.serve_rate),
+        # the configuration's rate on slot workers (one request per slot,
+        # each composited by its own launch)
+        sreqs = serve_requests(rng, scenes, sids, int(args.serve_slot_seconds * args.serve_rate),
                                args.serve_rate)
-        bres, _ = ctx.serve(breqs, realtime=True, batch=args.serve_batch)
-    bok = [r for r in bres if r["status"] == 0]
-    blat = np.array([r["latency_s"] for r in bok]) * 1e3
-    bt_end = max(r["finish_s"] for r in bres)
-    batched = {"batch": args.serve_batch, "requests": len(breqs), "completed": len(bok),
-               "throughput_rps": round(len(bok) / bt_end, 2),
-               "p50_ms": round(float(np.percentile(blat, 50)), 3) if blat.size else None,
-               "p99_ms": round(float(np.percentile(blat, 99)), 3) if blat.size else None,
-               "mean_frames_per_step": round(len(bok) / max(sum(1 for r in bok if r["slot"] == 0), 1), 2)}
-    ok = [r for r in results if r["status"] == 0]
-    lat = np.array([r["latency_s"] for r in ok]) * 1e3
-    t_end = max(r["finish_s"] for r in results)
-    by_res = {}
-    for (sid, mode, cam, _), r in zip(reqs, results):
-        if r["status"] == 0:
-            by_res.setdefault(f"{cam.width}x{cam.height}", []).append(r["latency_s"] * 1e3)
+        sres, _ = ctx.serve(sreqs, slots=args.serve_slots, realtime=True)
+        slots = serve_summary(sreqs, sres, args.serve_rate, args.serve_slot_seconds)
+        slots["slots"] = args.serve_slots
+    main = sweep[0]
     uploads = r1["block_uploads"] - r0["block_uploads"]
     hits = r1["block_hits"] - r0["block_hits"]
     return {
-        "rate_rps": args.serve_rate, "requests": len(reqs), "completed": len(ok),
-        "duration_s": round(t_end, 3), "throughput_rps": round(len(ok) / t_end, 2),
-        "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat.size else None,
-        "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat.size else None,
-        "p99_ms_by_resolution": {k: round(float(np.percentile(v, 99)), 3) for k, v in sorted(by_res.items())},
-        "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+        **main, "batch": args.serve_batch, "sweep": sweep[1:], "slot_workers": slots,
+        "hbm_budget_gb": args.serve_budget_gb,
         "scenes_level0": [int(n * args.serve_scale) for n in SERVE_LEVEL0],
         "residency": {"block_uploads": uploads, "block_hits": hits,
                       "hit_rate": round(hits / max(hits + uploads, 1), 3),
                       "evictions": r1["block_evictions"] - r0["block_evictions"],
                       "upload_gb": round((r1["upload_bytes"] - r0["upload_bytes"]) / 1e9, 2),
                       "hbm_used_gb": round(r1["hbm_used"] / (1 << 30), 2)},
-        "batched_steps": batched,
         "clocks": clocks, "setup_s": {"generate": round(t_gen, 1), "load": round(t_load, 1)},
         "workload": "4 streamed outdoor LOD scenes (4 levels, constant density, 16x16 chunks), "
                     "Poisson arrivals, uniform scene, random street-height pose, resolution "
-                    "uniform over 640x360/1280x720/1920x1080/3840x2160, CHUNK_BLEND",
+                    f"uniform over 640x360/1280x720/1920x1080/3840x2160, CHUNK_BLEND; steps of at most "
+                    f"{args.serve_batch} arrived requests, {args.serve_warmup_s:g} s warm-up",
     }
 
 

@@ -445,6 +445,8 @@ typedef struct {
     int32_t status;        /* lodge_status of this request */
     int32_t slot;
     lodge_frame_stats stats;
+    int32_t uploads;       /* chunk blocks gathered into HBM for this request */
+    int32_t step_frames;   /* step mode: frames composited by the request's step */
 } lodge_request_result;
 
 typedef struct {

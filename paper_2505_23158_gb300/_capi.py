@@ -77,7 +77,8 @@ class lodge_request(C.Structure):
 
 class lodge_request_result(C.Structure):
     _fields_ = [("start_s", C.c_double), ("finish_s", C.c_double), ("status", C.c_int32),
-                ("slot", C.c_int32), ("stats", lodge_frame_stats)]
+                ("slot", C.c_int32), ("stats", lodge_frame_stats), ("uploads", C.c_int32),
+                ("step_frames", C.c_int32)]
 
 
 class lodge_serve_opts(C.Structure):

@@ -366,7 +366,8 @@ class Lodge:
         for i in range(n):
             r = res[i]
             out.append(dict(start_s=r.start_s, finish_s=r.finish_s, status=r.status, slot=r.slot,
-                            latency_s=r.finish_s - requests[i][3], **stats_dict(r.stats)))
+                            latency_s=r.finish_s - requests[i][3], uploads=r.uploads,
+                            step_frames=r.step_frames, **stats_dict(r.stats)))
         imgs = None
         if images:
             imgs, off = [], 0

@@ -376,7 +376,11 @@ struct BlendBatch {
 BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                        int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                        int64_t n_rec, const BlendOut& o, int bin_log2 = 0, const uint2* rec_rect = nullptr);
-void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s);
+// One launch composites every frame's tiles.  With tile_ctr (a zeroed device
+// word) the launch is persistent: a grid of a few CTAs per SM takes (frame,
+// tile) items from the counter until all are done; without it, one CTA per
+// tile.
+void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s, uint32_t* tile_ctr = nullptr);
 
 // K12: importance score: the blend's walk, and per record the largest
 // weight T * alpha it receives (rec_score, n_rec words, zeroed, FP32 bits),

@@ -149,6 +149,7 @@ struct Slot {
     // other slots' frames run at the same time (several render streams, the
     // request loop): compositing then leaves room on every SM for them
     bool share_sms = false;
+    int64_t uploads = 0;       // chunk blocks this slot's frames have gathered
     lodge_profile prof{};
     cudaEvent_t ev_beg[LODGE_NUM_STAGES] = {};
     cudaEvent_t ev_end[LODGE_NUM_STAGES] = {};

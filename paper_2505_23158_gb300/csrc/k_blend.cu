@@ -295,6 +295,27 @@ __global__ void __launch_bounds__(kBlendThreads) blend_batch_kernel(BlendBatch b
     blend_tile<kBins>(bb.f[lo], (int)(b - bb.f[lo].tile_base));
 }
 
+// The same as a persistent grid: each CTA takes the next (frame, tile) item
+// of the step from the counter until all `total` are done.
+template <bool kBins>
+__global__ void __launch_bounds__(kBlendThreads) blend_batch_loop_kernel(BlendBatch bb, uint32_t total,
+                                                                         uint32_t* __restrict__ tile_ctr) {
+    __shared__ uint32_t s_t;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const uint32_t b = s_t;
+        __syncthreads();   // s_t is rewritten for the next item
+        if (b >= total) break;
+        int lo = 0, hi = bb.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bb.f[mid].tile_base <= b) lo = mid; else hi = mid - 1;
+        }
+        blend_tile<kBins>(bb.f[lo], (int)(b - bb.f[lo].tile_base));
+    }
+}
+
 
 // K12: importance score (Sec. 3 "Importance pruning" / "Visibility
 // filtering", after RadSplat): the same per-pixel walk as blend_kernel (same
@@ -452,7 +473,7 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
     }
 }
 
-void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s) {
+void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s, uint32_t* tile_ctr) {
     BlendBatch bb;
     uint32_t base = 0;
     bb.n = 0;
@@ -466,6 +487,23 @@ void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s) {
         ++bb.n;
     }
     if (bb.n == 0) return;
+    if (tile_ctr) {
+        // as many CTAs as fit on the device at once (the step's compositing
+        // runs after every frame's earlier stages)
+        int dev = 0, nsm = 152, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (bins)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_loop_kernel<true>, kBlendThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_loop_kernel<false>, kBlendThreads, 0);
+        const unsigned grid = (unsigned)std::min<int64_t>((int64_t)base, (int64_t)nsm * std::max(per_sm, 1));
+        if (bins)
+            blend_batch_loop_kernel<true><<<grid, kBlendThreads, 0, s>>>(bb, base, tile_ctr);
+        else
+            blend_batch_loop_kernel<false><<<grid, kBlendThreads, 0, s>>>(bb, base, tile_ctr);
+        return;
+    }
     if (bins)
         blend_batch_kernel<true><<<base, kBlendThreads, 0, s>>>(bb);
     else

@@ -573,7 +573,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     const int bl = (save || importance) ? 0 : ctx->bin_log2;
     // no mid-frame sync: plain coarse-binned frames once the slot knows a key
     // capacity (the fused emission needs bins of several tiles)
-    const bool deferred = pend && !save && !importance && !job && !sl.prof_count && bl > 0 &&
+    const bool deferred = pend && !save && !importance && !sl.prof_count && bl > 0 &&
                           sl.key_cap > 0 && na > 0 && (int)sl.pending.size() < Slot::kRing;
     if (pend) pend->used = false;
     const int32_t bins_x = (cam.tiles_x + (1 << bl) - 1) >> bl;
@@ -918,37 +918,73 @@ lodge_status render_one(lodge_ctx* ctx, Slot& sl, Scene* sc, lodge_mode mode,
 // items[k].status receives each frame's outcome.
 lodge_status render_batch(lodge_ctx* ctx, BatchItem* items, int n, int first, cudaStream_t s) {
     if (n < 1 || n > kMaxBlendBatch) return fail(LODGE_E_INVALID, "batch of %d frames (1..%d)", n, kMaxBlendBatch);
-    while ((int)ctx->slots.size() < first + n) {
-        Slot* sl = nullptr;
-        TRY(create_slot(ctx, &sl));
-    }
+    std::vector<Slot*> q((size_t)n);
+    for (int k = 0; k < n; ++k) TRY(stream_slot(ctx, first + k, &q[k]));
     std::vector<BlendFrame> jobs;
     std::vector<int> ok;
+    std::vector<Slot::Pending> pd((size_t)n);
+    // every frame's stages up to the tile ranges on its own slot and stream,
+    // started after the work already queued on s; a slot that has rendered a
+    // frame before skips the mid-frame sync (counts stay on the device)
     for (int k = 0; k < n; ++k) {
         BatchItem& it = items[k];
-        Slot& sl = *ctx->slots[first + k];
+        Slot& sl = *q[k];
+        sl.share_sms = true;
+        CUDA_TRY(cudaEventRecord(sl.fence, s));
+        CUDA_TRY(cudaStreamWaitEvent(sl.own, sl.fence, 0));
         Active act;
         BlendFrame job;
-        lodge_status r = select_active(ctx, sl, it.sc, it.mode, it.cam, s, &act);
+        pd[k].frame = k;
+        lodge_status r = select_active(ctx, sl, it.sc, it.mode, it.cam, sl.own, &act);
         if (r == LODGE_OK)
-            r = render_frame(ctx, sl, it.sc->dev, act, it.cam, it.d_rgb, s, nullptr, it.st, false, nullptr,
-                             &job);
+            r = render_frame(ctx, sl, it.sc->dev, act, it.cam, it.d_rgb, sl.own, nullptr, it.st, false, nullptr,
+                             &job, &pd[k]);
         it.status = r;
         if (r == LODGE_OK) {
             jobs.push_back(job);
             ok.push_back(k);
-        } else if (it.sc->residency == kStreamed) {
-            cudaStreamSynchronize(s);
-            release_blocks(ctx, sl);
+        } else {
+            cudaStreamSynchronize(sl.own);
+            sl.pending.clear();
+            if (it.sc->residency == kStreamed) release_blocks(ctx, sl);
         }
     }
-    if (!jobs.empty()) launch_blend_batch(jobs.data(), (int)jobs.size(), s);
+    for (int k = 0; k < n; ++k) {   // s continues after every frame's stages
+        CUDA_TRY(cudaEventRecord(q[k]->fence, q[k]->own));
+        CUDA_TRY(cudaStreamWaitEvent(s, q[k]->fence, 0));
+    }
+    // one persistent launch composites the tiles of every frame of the step
+    if (!jobs.empty()) {
+        uint32_t* ctr = q[0]->d_small + kSmCtrBlend;
+        CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
+        launch_blend_batch(jobs.data(), (int)jobs.size(), s, ctr);
+    }
     const cudaError_t e = cudaGetLastError();
+    std::vector<int> redo;
     for (int k : ok) {
-        Slot& sl = *ctx->slots[first + k];
-        lodge_status r = e == cudaSuccess ? sync_slot(ctx, sl, s) : fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e));
+        Slot& sl = *q[k];
+        lodge_status r;
+        if (e != cudaSuccess) {
+            r = fail(LODGE_E_CUDA, "%s", cudaGetErrorString(e));
+        } else if (pd[k].used) {
+            std::vector<int> rk;
+            r = harvest(ctx, sl, s, &rk);
+            if (r == LODGE_OK && !rk.empty()) redo.push_back(k);   // keys outgrew the slot's capacity
+        } else {
+            r = sync_slot(ctx, sl, s);
+        }
         items[k].status = r;
-        if (items[k].sc->residency == kStreamed) release_blocks(ctx, sl);
+    }
+    for (int k : ok) {
+        if (items[k].sc->residency == kStreamed) release_blocks(ctx, *q[k]);
+        q[k]->share_sms = false;
+    }
+    // frames whose keys outgrew their slot's capacity: rendered again alone,
+    // with their sync (the capacity has grown for the next step)
+    for (int k : redo) {
+        BatchItem& it = items[k];
+        it.status = render_one(ctx, *q[k], it.sc, it.mode, it.cam, it.d_rgb, s, nullptr, it.st, true, nullptr,
+                               nullptr);
     }
     return LODGE_OK;
 }

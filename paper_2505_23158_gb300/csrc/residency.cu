@@ -151,7 +151,6 @@ void block_view(Block& b, const DevScene& scene_dev) {
 
 lodge_status acquire_block(lodge_ctx* ctx, Slot& sl, Scene* sc, int chunk, cudaStream_t s,
                            Block** out) {
-    (void)sl;
     if (chunk < 0 || chunk >= (int)sc->chunks.size())
         return fail(LODGE_E_INVALID, "chunk %d out of range", chunk);
     cudaEvent_t ready = nullptr;
@@ -210,6 +209,7 @@ lodge_status acquire_block(lodge_ctx* ctx, Slot& sl, Scene* sc, int chunk, cudaS
             b->refs = 1;
             b->last_use = ++ctx->tick;
             ctx->res.uploads += 1;
+            sl.uploads += 1;
             ctx->res.upload_bytes += (int64_t)b->n * (sizeof(uint32_t) + 3 * sizeof(float) + 2 * sizeof(float4) +
                                                       16 * ((3 * (sc->dev.sh_degree + 1) * (sc->dev.sh_degree + 1) + 3) / 4));
             ready = b->ready;

@@ -76,6 +76,7 @@ extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, i
             res.start_s = now_s();
             Scene* sc = ctx->scenes[rq.scene].get();
             const size_t img_bytes = sizeof(float) * (img_off[i + 1] - img_off[i]);
+            const int64_t up0 = sl.uploads;
             lodge_status r;
             for (;;) {
                 r = ensure(ctx, sl.ws.img, img_bytes, s);
@@ -95,6 +96,8 @@ extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, i
             }
             res.finish_s = now_s();
             res.status = r;
+            res.uploads = (int32_t)(sl.uploads - up0);
+            res.step_frames = 1;
             if (r != LODGE_OK) failures.fetch_add(1);
         }
     };
@@ -115,6 +118,8 @@ extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, i
             while (next_i < n && (!opts->realtime || reqs[next_i].arrival_s <= t)) pending.push_back(next_i++);
             std::vector<int> step(pending.begin(), pending.begin() + std::min<size_t>(pending.size(), (size_t)B));
             std::vector<BatchItem> items(step.size());
+            std::vector<int64_t> up0(step.size());
+            for (size_t k = 0; k < step.size(); ++k) up0[k] = ctx->slots[1 + k]->uploads;
             lodge_status r = LODGE_OK;
             for (size_t k = 0; k < step.size() && r == LODGE_OK; ++k) {
                 const int i = step[k];
@@ -143,6 +148,8 @@ extern "C" lodge_status lodge_serve(lodge_ctx* ctx, const lodge_request* reqs, i
                 res.finish_s = now_s();
                 res.status = ri;
                 res.slot = (int32_t)k;
+                res.uploads = (int32_t)(ctx->slots[1 + k]->uploads - up0[k]);
+                res.step_frames = (int32_t)step.size();
                 if (ri != LODGE_OK) failures.fetch_add(1);
                 pending.erase(std::find(pending.begin(), pending.end(), i));
             }

@@ -58,6 +58,16 @@ def importance_scores(ctx: Lodge, levels: Sequence[tuple], views, d_inner, filte
     return score[:n]
 
 
+def eval_loss(ctx: Lodge, fixed, trained, l: int, views, targets, d, filter_var, sh_degree: int = 3) -> float:
+    """Mean L1 over the views of LOD renders at the thresholds d."""
+    levels = list(fixed[:l]) + [tuple(trained)] + list(fixed[l:])
+    tot = 0.0
+    for cam, tgt in zip(views, targets):
+        img, _, _ = ctx.render_params_lod(levels, cam, d, filter_var, sh_degree=sh_degree)
+        tot += float((img - tgt).abs().mean())
+    return tot / max(len(views), 1)
+
+
 def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[float], views,
                 targets: Sequence[torch.Tensor], gamma: float, filter_var_l: float,
                 filter_var_fixed: Sequence[float], steps: int = 1000, lr: Optional[dict] = None,
@@ -70,12 +80,15 @@ def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[flo
     gamma: importance threshold of the last round; filter_var_l /
     filter_var_fixed: Eq. 3 variances of the new and the fixed levels.
     Returns (parameters of G_l, history) where history holds per round the
-    threshold, the scores of G_l before pruning, the kept count and the loss
-    of every step (and, with keep_params, host copies of the parameters that
-    were scored and of those after the round's steps)."""
+    threshold, the scores of G_l before pruning, the kept count, the loss of
+    every step, and the mean L1 over the views at the nominal thresholds
+    after pruning and after the round's steps (and, with keep_params, host
+    copies of the parameters that were scored and of those after the
+    round's steps)."""
     l = len(fixed)
     assert len(d) == l and l >= 1
-    lr = lr or {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "logits": 5e-2, "sh": 2.5e-3}
+    # fine-tuning rates (the tail of a 3DGS schedule: small position steps)
+    lr = lr or {"means": 1e-5, "log_scales": 2e-3, "quats": 5e-4, "logits": 1e-2, "sh": 1e-3}
     rng = np.random.default_rng(seed)
     fvs = list(filter_var_fixed) + [filter_var_l]
     d = np.asarray(d, np.float64)
@@ -89,6 +102,7 @@ def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[flo
         scored = [t.cpu().numpy() for t in cur] if keep_params else None
         keep = s_l >= thr
         cur = [t[keep].contiguous() for t in cur]
+        loss_pruned = eval_loss(ctx, fixed, cur, l, views, targets, d, fvs, sh_degree)
         params = [t.detach().clone().requires_grad_(True) for t in cur]
         names = ("means", "log_scales", "quats", "logits", "sh")
         opt = torch.optim.Adam([{"params": [p], "lr": lr[k]} for p, k in zip(params, names)], eps=1e-15)
@@ -104,8 +118,10 @@ def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[flo
             opt.step()
             losses.append(float(loss.detach()))
         cur = [p.detach().contiguous() for p in params]
+        loss_tuned = eval_loss(ctx, fixed, cur, l, views, targets, d, fvs, sh_degree)
         rec = {"round": r, "threshold": thr, "scores": s_l.detach().cpu().numpy(),
-               "kept": int(keep.sum()), "losses": np.asarray(losses)}
+               "kept": int(keep.sum()), "losses": np.asarray(losses),
+               "loss_pruned": loss_pruned, "loss_tuned": loss_tuned}
         if keep_params:
             rec["scored_params"] = scored
             rec["params"] = [t.cpu().numpy() for t in cur]

@@ -177,10 +177,38 @@ def test_batch_render_equals_single(env, scene_cams):
             sid, mode = [(r, api.CHUNK_BLEND), (s, api.CHUNK), (r, api.LOD), (s, api.CHUNK_BLEND)][i % 4]
             frames.append((sid, mode, cam))
         frames.append((p, api.FULL, pcams[0]))
+        # the first batch sizes each slot's key capacity (mid-frame syncs);
+        # the second runs every resident frame without its mid-frame sync
+        for rep in range(2):
+            imgs, stats = ctx.render_batch(frames)
+            for (sid, mode, cam), img, st in zip(frames, imgs, stats):
+                alone, st1 = ctx.render(sid, mode, cam)
+                assert torch.equal(alone, img), rep
+                assert st1["n_keys"] == st["n_keys"] and st1["n_visible"] == st["n_visible"]
+
+
+def test_batch_frames_outgrowing_capacity_rendered_again(env):
+    """A batch whose slots were sized by frames that saw nothing: the next
+    batch's frames outgrow the key capacity, are rendered again alone, and
+    every image and count equals the camera rendered alone."""
+    torch, api = env
+    scene, cams = synth.workload_outdoor(seed=8, n_poses=12, scale=0.02, width=320, height_px=180)
+    up = np.asarray(cams[0].center, np.float64)
+    away = synth.look_at(up + np.array([0.0, 0.0, 1000.0]), up + np.array([0.0, 0.0, 2000.0]), (1, 0, 0),
+                         320, 180, 70.0)
+    with api.Lodge(0) as ctx:
+        sid = ctx.load_scene(scene)
+        ctx.set_bin_size(1)
+        ctx.render_batch([(sid, api.FULL, away)] * 4)
+        ctx.profile_enable(True)
+        frames = [(sid, api.FULL, c) for c in cams[:4]]
         imgs, stats = ctx.render_batch(frames)
-        for (sid, mode, cam), img, st in zip(frames, imgs, stats):
-            alone, st1 = ctx.render(sid, mode, cam)
-            assert torch.equal(alone, img)
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        assert prof["redone"] >= 1, prof
+        for (_, mode, cam), img, st in zip(frames, imgs, stats):
+            one, st1 = ctx.render(sid, mode, cam)
+            assert torch.equal(one, img)
             assert st1["n_keys"] == st["n_keys"] and st1["n_visible"] == st["n_visible"]
 
 
@@ -201,6 +229,7 @@ def test_serve_batched_steps_equal_alone(env, scene_cams):
         results, imgs = ctx.serve(reqs, realtime=False, images=True, batch=8)
         assert all(r["status"] == 0 for r in results), [r["status"] for r in results]
         assert max(r["slot"] for r in results) == 7          # full steps of 8 frames
+        assert all(r["step_frames"] == 8 for r in results)
         for (sid, mode, cam, _), img in zip(reqs, imgs):
             alone, _ = _render(ctx, sid, mode, cam)
             assert np.array_equal(alone, img)
