@@ -179,8 +179,10 @@ struct ProjectOut {
                                      // of the visible records' depth keys (the depth sort's)
 };
 constexpr int kProjThreads = 256;
-// look-back status words of the projection: one per warp of 32 entries
-inline int64_t proj_status_words(int64_t n_active) { return std::max<int64_t>((n_active + 31) / 32, 1); }
+// look-back status words of the projection: one per CTA of kProjThreads entries
+inline int64_t proj_status_words(int64_t n_active) {
+    return std::max<int64_t>((n_active + kProjThreads - 1) / kProjThreads, 1);
+}
 // Attribute sources for streamed scenes: list entries index into chunk block
 // A (bit 31) or B, whose gid lists give the Gaussians' gids.
 struct ProjSources {

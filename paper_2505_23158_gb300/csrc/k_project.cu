@@ -1,10 +1,7 @@
 // K3: projection of the active Gaussians (EWA splatting with the per-level
 // Eq. 3 filter and the Eq. 4 opacity multiplier), degree-3 SH colour, tile
-// rect and visibility compaction in one pass, so the records come out dense
-// and in gid order.  The compaction is per warp: each warp of 32 entries
-// counts its visible ones by ballot, publishes the count and chains its
-// offset by a decoupled look-back over the warps before it, so no warp waits
-// at a block barrier for another warp's loads.
+// rect and visibility compaction in one pass (decoupled look-back), so the
+// records come out dense and in gid order.
 //
 // The integer outcomes (near cull, opacity cull, tile rect) and the depth
 // sort key are computed by the "key spec": FP32 with every operation
@@ -178,7 +175,8 @@ template <bool kBlocks>
 __global__ void __launch_bounds__(kProjThreads, 6)
 project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
                uint32_t* __restrict__ err) {
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_scan[33];
     __shared__ unsigned long long s_keys, s_bkeys;
     __shared__ uint32_t s_dh[4][256];   // depth-key digit counts (the depth sort's histogram)
     if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_keys = 0ull; s_bkeys = 0ull; }
@@ -186,6 +184,7 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         for (int j = threadIdx.x; j < 4 * 256; j += kProjThreads) (&s_dh[0][0])[j] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
+    const uint32_t ntiles = (uint32_t)((P.n_active + kProjThreads - 1) / kProjThreads);
     const int64_t i = (int64_t)tile * kProjThreads + threadIdx.x;
     const DevScene& sc = P.sc;
     const DevCamera& cam = P.cam;
@@ -240,22 +239,18 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         }
     }
 
-    // ---- compaction of visible records (gid order preserved), per warp:
-    // warp tile wt = CTA tile * 8 + warp.  Its count is published as soon as
-    // it is known and its look-back comes after the attribute work below, so
-    // successors rarely wait and its predecessors' counts are in place.
-    const int lane = threadIdx.x & 31;
-    const uint32_t wt = tile * (kProjThreads / 32) + (threadIdx.x >> 5);
-    const uint32_t nwt = (uint32_t)((P.n_active + 31) / 32);
-    const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
-    const uint32_t total = __popc(vmask);
-    const uint32_t excl = __popc(vmask & ((1u << lane) - 1u));
-    if (lane == 0 && wt < nwt) st_volatile(status + wt, (wt == 0 ? kStInc : kStAgg) | total);
+    // ---- compaction of visible records (gid order preserved).  The CTA's
+    // count is published as soon as it is known and the look-back comes
+    // after the attribute work below, so successors rarely wait on it and
+    // this CTA's own look-back finds its predecessors' counts in place.
+    uint32_t total;
+    uint32_t excl = block_exclusive_scan(vis ? 1u : 0u, s_scan, &total);
+    if (threadIdx.x == 0) st_volatile(status + tile, (tile == 0 ? kStInc : kStAgg) | total);
     uint32_t nk = vis ? (rx1 - rx0 + 1) * (ry1 - ry0 + 1) : 0u;
     {
         uint32_t wsum = nk;
         for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
-        if (lane == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
     }
     if (vis && P.o.depth_hist) {
         const uint32_t zb = __float_as_uint(z);
@@ -266,7 +261,7 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     if (bl > 0) {   // keys of the coarse bins (squares of 2^bl tiles)
         uint32_t wsum = vis ? ((rx1 >> bl) - (rx0 >> bl) + 1) * ((ry1 >> bl) - (ry0 >> bl) + 1) : 0u;
         for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
-        if (lane == 0 && wsum) atomicAdd(&s_bkeys, (unsigned long long)wsum);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_bkeys, (unsigned long long)wsum);
     }
 
     float u00 = 0.f, u01 = 0.f, u11 = 0.f;
@@ -308,38 +303,38 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         }
     }
 
-    // ---- the warp's offset: look-back over the warps before it
-    uint32_t prefix = 0;
-    if (wt < nwt) {
-        if (wt != 0) {
-            prefix = warp_lookback(status, wt, err);
-            if (lane == 0) st_volatile(status + wt, kStInc | (prefix + total));
+    if (threadIdx.x < 32) {
+        uint32_t prefix = 0;
+        if (tile != 0) {
+            prefix = warp_lookback(status, tile, err);
+            if (threadIdx.x == 0) st_volatile(status + tile, kStInc | (prefix + total));
         }
-        if (lane == 0 && wt == nwt - 1) P.o.counts[0] = prefix + total;
+        if (threadIdx.x == 0) {
+            s_prefix = prefix;
+            if (tile == ntiles - 1) P.o.counts[0] = prefix + total;
+        }
     }
-    if (vis) {
-        const uint32_t pos = prefix + excl;
-        P.o.rec_a[pos] = make_float4(mxp, myp, u00, u01);
-        // log2 of the opacity: compositing forms alpha as 2^(log2 o' - q)
-        P.o.rec_b[pos] = make_float4(u11, log2f(o), fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
-        P.o.rec_c[pos] = fmaxf(rgb[2], 0.f);
-        P.o.rec_rect[pos] = make_uint2(pr0, pr1);   // pixel range
-        P.o.rec_gid[pos] = g;
-        P.o.depth_key[pos] = __float_as_uint(z);
-        P.o.depth_val[pos] = pos;
-    }
-    // ---- the CTA's key counts and depth digit counts, once all warps are done
     __syncthreads();
     if (threadIdx.x == 0 && s_keys)
         atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 2), s_keys);
     if (threadIdx.x == 0 && s_bkeys)
         atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 4), s_bkeys);
-    if (P.o.depth_hist) {
+    if (P.o.depth_hist && total) {
         for (int j = threadIdx.x; j < 4 * 256; j += kProjThreads) {
             const uint32_t c = (&s_dh[0][0])[j];
             if (c) atomicAdd(P.o.depth_hist + j, c);
         }
     }
+    if (!vis) return;
+    const uint32_t pos = s_prefix + excl;
+    P.o.rec_a[pos] = make_float4(mxp, myp, u00, u01);
+    // log2 of the opacity: compositing forms alpha as 2^(log2 o' - q)
+    P.o.rec_b[pos] = make_float4(u11, log2f(o), fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
+    P.o.rec_c[pos] = fmaxf(rgb[2], 0.f);
+    P.o.rec_rect[pos] = make_uint2(pr0, pr1);   // pixel range
+    P.o.rec_gid[pos] = g;
+    P.o.depth_key[pos] = __float_as_uint(z);
+    P.o.depth_val[pos] = pos;
 }
 
 

@@ -58,14 +58,24 @@ def importance_scores(ctx: Lodge, levels: Sequence[tuple], views, d_inner, filte
     return score[:n]
 
 
+EVAL_FACTORS = (0.7, 0.85, 1.0, 1.15, 1.3)
+
+
 def eval_loss(ctx: Lodge, fixed, trained, l: int, views, targets, d, filter_var, sh_degree: int = 3) -> float:
-    """Mean L1 over the views of LOD renders at the thresholds d."""
+    """The objective the steps sample, evaluated deterministically: mean L1
+    over the views and over d_l at 0.7, 0.85, 1.0, 1.15 and 1.3 of its
+    nominal value (the other thresholds fixed)."""
     levels = list(fixed[:l]) + [tuple(trained)] + list(fixed[l:])
-    tot = 0.0
-    for cam, tgt in zip(views, targets):
-        img, _, _ = ctx.render_params_lod(levels, cam, d, filter_var, sh_degree=sh_degree)
-        tot += float((img - tgt).abs().mean())
-    return tot / max(len(views), 1)
+    d = np.asarray(d, np.float64)
+    tot, cnt = 0.0, 0
+    for f in EVAL_FACTORS:
+        dd = d.copy()
+        dd[-1] = f * d[-1]
+        for cam, tgt in zip(views, targets):
+            img, _, _ = ctx.render_params_lod(levels, cam, dd, filter_var, sh_degree=sh_degree)
+            tot += float((img - tgt).abs().mean())
+            cnt += 1
+    return tot / max(cnt, 1)
 
 
 def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[float], views,
@@ -81,8 +91,8 @@ def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[flo
     filter_var_fixed: Eq. 3 variances of the new and the fixed levels.
     Returns (parameters of G_l, history) where history holds per round the
     threshold, the scores of G_l before pruning, the kept count, the loss of
-    every step, and the mean L1 over the views at the nominal thresholds
-    after pruning and after the round's steps (and, with keep_params, host
+    every step, and the objective (eval_loss) after pruning and after the
+    round's steps (and, with keep_params, host
     copies of the parameters that were scored and of those after the
     round's steps)."""
     l = len(fixed)
@@ -106,6 +116,8 @@ def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[flo
         params = [t.detach().clone().requires_grad_(True) for t in cur]
         names = ("means", "log_scales", "quats", "logits", "sh")
         opt = torch.optim.Adam([{"params": [p], "lr": lr[k]} for p, k in zip(params, names)], eps=1e-15)
+        # rates decay exponentially to a tenth over the round's steps
+        sched = torch.optim.lr_scheduler.LambdaLR(opt, lambda t: 0.1 ** (t / max(steps, 1)))
         losses = []
         for step in range(steps):
             i = step % len(views)
@@ -116,6 +128,7 @@ def build_level(ctx: Lodge, fixed: Sequence[tuple], base: tuple, d: Sequence[flo
             opt.zero_grad(set_to_none=True)
             loss.backward()
             opt.step()
+            sched.step()
             losses.append(float(loss.detach()))
         cur = [p.detach().contiguous() for p in params]
         loss_tuned = eval_loss(ctx, fixed, cur, l, views, targets, d, fvs, sh_degree)
