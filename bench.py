@@ -402,15 +402,15 @@ def run_lodge(args, rank, world, local_rank):
         # colour), the exp2 on the MUFU not counted; peak = SMs x 128 FP32
         # lanes x 2 (FMA) x the maximum SM clock.  The flops this kernel's
         # own formulation needs (9.5 per evaluated pair, the shared dx
-        # counted once per two pixels, + 8 per composited pair: T alpha,
-        # T - T alpha and three colour FMAs) are given beside it.
+        # counted once per two pixels, + 9 per composited pair: T (1 - alpha),
+        # T alpha and three colour FMAs) are given beside it.
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         nf = max(prof_cnt["frames"], 1)
         pairs = prof_cnt["blend_pairs"] / nf
         flops = 15.0 * pairs
-        flops_own = (9.5 * prof_cnt["blend_pairs"] + 8.0 * prof_cnt["blend_pairs_used"]) / nf
+        flops_own = (9.5 * prof_cnt["blend_pairs"] + 9.0 * prof_cnt["blend_pairs_used"]) / nf
         t_launch = ms["blend"] / max(prof["frames"], 1) / 1e3
         ach = flops / t_launch / 1e12
         tr = measured_traffic("blend", 0)

@@ -23,8 +23,8 @@
 // U^T U = (1/2) log2(e) Sigma'^-1, log2 o', colour):
 //   q = (u00 dx + u01 dy)^2 + (u11 dy)^2,  alpha = min(0.99, 2^(log2 o' - q))
 //   (= o' 2^-q; the exponent is formed by two FMAs and the product is saved)
-//   skip if alpha < 1/255; w = T alpha, T' = T - w (= T (1 - alpha));
-//   stop if T' < 1e-4; C += w rgb; T = T'.
+//   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
+//   C += T alpha rgb; T = T'.
 #include "common.cuh"
 
 namespace lodge {
@@ -60,11 +60,11 @@ __device__ __forceinline__ void blend_px(const float alpha, const float4 bb, con
                                          uint32_t pos, uint32_t& n_eval, uint32_t& n_used) {
     if (kCount) ++n_eval;
     if (alpha >= (1.0f / 255.0f)) {
-        const float wgt = T * alpha;
-        const float Tn = T - wgt;          // T (1 - alpha)
+        const float Tn = T * (1.f - alpha);
         if (Tn < 1e-4f) {
             done = true;
         } else {
+            const float wgt = T * alpha;
             C0 = fmaf(wgt, bb.z, C0);
             C1 = fmaf(wgt, bb.w, C1);
             C2 = fmaf(wgt, cz, C2);
@@ -76,27 +76,25 @@ __device__ __forceinline__ void blend_px(const float alpha, const float4 bb, con
 }
 
 // The same step without branches, for walks that need neither the final
-// transmittance nor list positions: a skipped pair (alpha < 1/255) gets
-// weight 0 and leaves T; a pixel that stops gets T = 0, after which every
-// step leaves it unchanged (its weight is 0, T - 0 < 1e-4 stops it again).
+// transmittance nor list positions: a pixel that stops gets T = 0, after
+// which every step leaves it unchanged (its weight is 0 and T stays 0).
 // While T > 0 the arithmetic and decisions are blend_px's.
 template <bool kCount>
 __device__ __forceinline__ void blend_px_flat(const float alpha, const float4 bb, const float cz, float& T,
                                               float& C0, float& C1, float& C2, uint32_t& n_eval,
                                               uint32_t& n_used) {
-    const float a = alpha >= (1.0f / 255.0f) ? alpha : 0.f;
-    const float w = T * a;
-    const float Tn = T - w;                // T (1 - alpha), or T when skipped
-    const bool stop = Tn < 1e-4f;
-    const float wgt = stop ? 0.f : w;
+    const float Tn = T * (1.f - alpha);
+    const bool ok = alpha >= (1.0f / 255.0f);
+    const bool go = ok && !(Tn < 1e-4f);
+    const float wgt = go ? T * alpha : 0.f;
     C0 = fmaf(wgt, bb.z, C0);
     C1 = fmaf(wgt, bb.w, C1);
     C2 = fmaf(wgt, cz, C2);
     if (kCount) {
         n_eval += T > 0.f ? 1u : 0u;
-        n_used += (a > 0.f && !stop) ? 1u : 0u;
+        n_used += go ? 1u : 0u;
     }
-    T = stop ? 0.f : Tn;
+    T = go ? Tn : (ok ? 0.f : T);
 }
 
 template <bool kBins, bool kCount = false>
@@ -372,12 +370,11 @@ importance_kernel(int32_t width, int32_t height, int32_t tiles_x, const uint2* _
                 pixel_tw(a, bb, pxf - a.x, y, t, wq);
                 const float alpha = alpha_of(bb, t, wq);
                 if (alpha >= (1.0f / 255.0f)) {
-                    const float wt = T * alpha;
-                    const float Tn = T - wt;       // blend_px's arithmetic
+                    const float Tn = T * (1.f - alpha);
                     if (Tn < 1e-4f) {
                         done = true;
                     } else {
-                        w = wt;
+                        w = T * alpha;
                         C0 = fmaf(w, bb.z, C0);
                         C1 = fmaf(w, bb.w, C1);
                         C2 = fmaf(w, sc[k], C2);

@@ -78,10 +78,15 @@ struct KeySplat {
     uint32_t rx0, ry0, rx1, ry1;   // the same in tiles
 };
 
+// kPre: so_pre / q_pre already hold this Gaussian's (scale, opacity) and
+// quaternion (loaded together with its mean); otherwise they are loaded here
+// once the near cull has passed.
+template <bool kPre = false>
 __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& cam, float mxw,
                                           float myw, float mzw, const float4* __restrict__ sso,
                                           const float4* __restrict__ sq, int64_t idx, uint32_t g,
-                                          float mult, KeySplat& k) {
+                                          float mult, KeySplat& k, float4 so_pre = float4{},
+                                          float4 q_pre = float4{}) {
     const float* R = cam.R;
     k.d0 = fs(mxw, cam.chat[0]);
     k.d1 = fs(myw, cam.chat[1]);
@@ -91,7 +96,7 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
     float py = fa(fa(fa(fm(R[3], d0), fm(R[4], d1)), fm(R[5], d2)), cam.tp[1]);
     float pz = fa(fa(fa(fm(R[6], d0), fm(R[7], d1)), fm(R[8], d2)), cam.tp[2]);
     if (!(pz > cam.znear)) return false;
-    const float4 so = sso[idx];
+    const float4 so = kPre ? so_pre : sso[idx];
     int l = 0;
     while (l + 1 < sc.num_levels && (int64_t)g >= sc.level_off[l + 1]) ++l;
     const float v = sc.filter_var[l];
@@ -107,7 +112,7 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
     // without the compensated 2D filter the opacity is final here; with it,
     // the opacity cull waits for the compensation below
     if (!sc.filter2d && !(op >= (float)(1.0 / 255.0))) return false;
-    const float4 q = sq[idx];
+    const float4 q = kPre ? q_pre : sq[idx];
     float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
     float mx = fa(fm(cam.fx, u), cam.cx);
     float my = fa(fm(cam.fy, w), cam.cy);
@@ -226,8 +231,12 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
             if ((int64_t)idx >= sc.n_total) { atomicOr(err, kErrBadIndex); idx = 0; mult = 0.f; }
             g = idx;
         }
+        // the mean, (scale, opacity) and quaternion are loaded together, so
+        // that one memory latency, not three in a row, precedes the key spec
+        const float mxw = smx[idx], myw = smy[idx], mzw = smz[idx];
+        const float4 so = sso[idx], qq = sq[idx];
         KeySplat ks;
-        vis = key_splat(sc, cam, smx[idx], smy[idx], smz[idx], sso, sq, idx, g, mult, ks);
+        vis = key_splat<true>(sc, cam, mxw, myw, mzw, sso, sq, idx, g, mult, ks, so, qq);
         d0 = ks.d0; d1 = ks.d1; d2 = ks.d2;
         if (vis) {
             z = ks.z; mxp = ks.mx; myp = ks.my; o = ks.op;
