@@ -239,6 +239,13 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         vis = key_splat<true>(sc, cam, mxw, myw, mzw, sso, sq, idx, g, mult, ks, so, qq);
         d0 = ks.d0; d1 = ks.d1; d2 = ks.d2;
         if (vis) {
+            // start the SH planes' way into L2 now: the block scan and the
+            // conic come before they are read
+            const int npl = (3 * (sc.sh_degree + 1) * (sc.sh_degree + 1) + 3) / 4;
+            for (int j = 0; j < npl; ++j)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(ssh + (int64_t)j * npad + idx));
+        }
+        if (vis) {
             z = ks.z; mxp = ks.mx; myp = ks.my; o = ks.op;
 #pragma unroll
             for (int k = 0; k < 3; ++k) { B0[k] = ks.B0[k]; B1[k] = ks.B1[k]; }
