@@ -268,10 +268,18 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
         for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
     }
-    if (vis && P.o.depth_hist) {
+    if (P.o.depth_hist) {
+        // the CTA's Gaussians are neighbours in the store, so their depths
+        // share the high digits: lanes with the same digit add their count
+        // with one shared atomic instead of contending for the word
         const uint32_t zb = __float_as_uint(z);
+        const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&s_dh[p][(zb >> (8 * p)) & 0xffu], 1u);
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t d = vis ? (zb >> (8 * p)) & 0xffu : 0x100u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (vis && lane == __ffs(peers) - 1) atomicAdd(&s_dh[p][d], (uint32_t)__popc(peers));
+        }
     }
     const int bl = P.o.bin_log2;
     if (bl > 0) {   // keys of the coarse bins (squares of 2^bl tiles)
