@@ -416,6 +416,10 @@ void launch_project_bwd(const DevCamera& cam, int64_t n_rec, const uint32_t* rec
                         const BwdLevels& lv, float* g_means, float* g_log_scales, float* g_quats,
                         float* g_logits, float* g_sh, cudaStream_t s);
 
+// SM count of the current device (queried once per device; 152 on GB300),
+// for grids sized as a multiple of the SMs
+int device_sms();
+
 // records msg as the calling thread's lodge_last_error message; returns s
 lodge_status set_error(lodge_status s, const char* msg);
 

@@ -409,12 +409,12 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
     if (n_keys >= kEmitWarpMinKeys * n_vis) {
         // records average a warp's worth of keys or more: one warp per record
         const unsigned grid = (unsigned)std::min<int64_t>((n_vis + kEmitThreads / 32 - 1) / (kEmitThreads / 32),
-                                                          152 * 8);
+                                                          (int64_t)device_sms() * 8);
         emit_keys_rect_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, tiles_x, tile_key,
                                                             tile_val, rbits, P, last_mask, digit_hist);
     } else {
         const int64_t nslices = (n_keys + kEmitKeysPerCta - 1) / kEmitKeysPerCta;
-        const unsigned grid = (unsigned)std::min<int64_t>(nslices, 152 * 4);
+        const unsigned grid = (unsigned)std::min<int64_t>(nslices, (int64_t)device_sms() * 4);
         emit_keys_sliced_kernel<<<grid, kEmitThreads, 0, s>>>(koff, srec, srect, n_vis, n_keys, tiles_x,
                                                               tile_key, tile_val, rbits, P, last_mask,
                                                               digit_hist, err);

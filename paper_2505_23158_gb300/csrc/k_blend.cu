@@ -25,8 +25,6 @@
 //   (= o' 2^-q; the exponent is formed by two FMAs and the product is saved)
 //   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
 //   C += T alpha rgb; T = T'.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace lodge {
@@ -36,10 +34,6 @@ namespace {
 constexpr int kBatch = 256;        // importance kernel: records per batch
 constexpr int kBlendThreads = 128; // blend: two pixels per thread
 constexpr int kBlendBatch = 128;   // blend: records per batch (one per thread)
-// resident compositing CTAs per SM the register budget is sized for (at most
-// 40 registers a thread): the walk is bound by instruction issue, and more
-// resident warps fill the cycles in which the others wait on shared memory
-constexpr int kBlendMinCtas = 12;
 
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -270,13 +264,13 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
 }
 
 template <bool kBins, bool kCount>
-__global__ void __launch_bounds__(kBlendThreads, kBlendMinCtas) blend_kernel(BlendFrame f) {
+__global__ void __launch_bounds__(kBlendThreads) blend_kernel(BlendFrame f) {
     blend_tile<kBins, kCount>(f, blockIdx.x);
 }
 
 // fewer CTAs than tiles: each takes the next tile from the counter
 template <bool kBins, bool kCount>
-__global__ void __launch_bounds__(kBlendThreads, kBlendMinCtas) blend_loop_kernel(BlendFrame f, uint32_t* __restrict__ tile_ctr) {
+__global__ void __launch_bounds__(kBlendThreads) blend_loop_kernel(BlendFrame f, uint32_t* __restrict__ tile_ctr) {
     __shared__ int s_t;
     for (;;) {
         if (threadIdx.x == 0) s_t = (int)atomicAdd(tile_ctr, 1u);
@@ -291,7 +285,7 @@ __global__ void __launch_bounds__(kBlendThreads, kBlendMinCtas) blend_loop_kerne
 // One launch for the tiles of several frames (a serving step): CTA b
 // composites tile b - tile_base of the last frame whose tile_base <= b.
 template <bool kBins>
-__global__ void __launch_bounds__(kBlendThreads, kBlendMinCtas) blend_batch_kernel(BlendBatch bb) {
+__global__ void __launch_bounds__(kBlendThreads) blend_batch_kernel(BlendBatch bb) {
     const uint32_t b = blockIdx.x;
     int lo = 0, hi = bb.n - 1;
     while (lo < hi) {
@@ -304,7 +298,7 @@ __global__ void __launch_bounds__(kBlendThreads, kBlendMinCtas) blend_batch_kern
 // The same as a persistent grid: each CTA takes the next (frame, tile) item
 // of the step from the counter until all `total` are done.
 template <bool kBins>
-__global__ void __launch_bounds__(kBlendThreads, kBlendMinCtas) blend_batch_loop_kernel(BlendBatch bb, uint32_t total,
+__global__ void __launch_bounds__(kBlendThreads) blend_batch_loop_kernel(BlendBatch bb, uint32_t total,
                                                                          uint32_t* __restrict__ tile_ctr) {
     __shared__ uint32_t s_t;
     for (;;) {
@@ -441,31 +435,6 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
     return f;
 }
 
-// The compositing kernels ask for the largest shared-memory carveout once,
-// so that kBlendMinCtas CTAs (11 KB of staged records each) fit an SM.
-static void blend_carveout_once() {
-    static std::once_flag once;
-    std::call_once(once, [] {
-        const void* ks[] = {
-            reinterpret_cast<const void*>(blend_kernel<true, false>),
-            reinterpret_cast<const void*>(blend_kernel<false, false>),
-            reinterpret_cast<const void*>(blend_kernel<true, true>),
-            reinterpret_cast<const void*>(blend_kernel<false, true>),
-            reinterpret_cast<const void*>(blend_loop_kernel<true, false>),
-            reinterpret_cast<const void*>(blend_loop_kernel<false, false>),
-            reinterpret_cast<const void*>(blend_loop_kernel<true, true>),
-            reinterpret_cast<const void*>(blend_loop_kernel<false, true>),
-            reinterpret_cast<const void*>(blend_batch_kernel<true>),
-            reinterpret_cast<const void*>(blend_batch_kernel<false>),
-            reinterpret_cast<const void*>(blend_batch_loop_kernel<true>),
-            reinterpret_cast<const void*>(blend_batch_loop_kernel<false>)};
-        for (const void* k : ks)
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-        cudaGetLastError();   // an unsupported hint leaves the default carveout
-    });
-}
-
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* tile_val, uint32_t vmask,
                   int64_t n_keys, const float4* rec_a, const float4* rec_b, const float* rec_c,
                   int64_t n_rec, const BlendOut& o, cudaStream_t s, int bin_log2, const uint2* rec_rect,
@@ -473,14 +442,10 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
     BlendFrame f = blend_frame(cam, ranges, tile_val, vmask, n_keys, rec_a, rec_b, rec_c, n_rec, o,
                                bin_log2, rec_rect);
     if (f.ntiles == 0) return;
-    blend_carveout_once();
     f.pairs = pairs;
     unsigned grid = (unsigned)f.ntiles;
     if (tile_ctr) {
-        int dev = 0, sms = 152;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = (unsigned)std::min<int64_t>(f.ntiles, (int64_t)sms * kBlendCtasPerSM);
+        grid = (unsigned)std::min<int64_t>(f.ntiles, (int64_t)device_sms() * kBlendCtasPerSM);
     }
     if (tile_ctr) {
         if (pairs) {   // counting variant (profiling), same walk
@@ -519,13 +484,11 @@ void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s, uint32_
         ++bb.n;
     }
     if (bb.n == 0) return;
-    blend_carveout_once();
     if (tile_ctr) {
         // as many CTAs as fit on the device at once (the step's compositing
         // runs after every frame's earlier stages)
-        int dev = 0, nsm = 152, per_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = 1;
+        const int nsm = device_sms();
         if (bins)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_loop_kernel<true>, kBlendThreads, 0);
         else

@@ -455,7 +455,7 @@ void launch_threshold_cost(const DevScene& sc, const DevCamera& cam, int64_t n, 
                            const ThreshBands& b, const float* d_thr, int K, unsigned long long* acc,
                            cudaStream_t s) {
     if (n <= 0) return;
-    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4);
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 4);
     threshold_cost_kernel<<<grid, 256, threshold_cost_smem(K), s>>>(sc, cam, n, lvl, b, d_thr, K, acc);
 }
 

@@ -268,7 +268,7 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
         offs = digit_offsets;
     } else {
         cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, key_bits), s);
-        int hist_blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 4);
+        int hist_blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 4);
         hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n, P, last_mask, hist, shift0);
         hist_scan_kernel<<<P, kRadix, 0, s>>>(hist);
     }

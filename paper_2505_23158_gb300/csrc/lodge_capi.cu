@@ -28,6 +28,22 @@ lodge_status fail(lodge_status s, const char* fmt, ...) {
     return s;
 }
 
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) { cudaGetLastError(); return 152; }
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            return 152;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 lodge_status set_error(lodge_status s, const char* msg) {
     g_err = msg;
     return s;
