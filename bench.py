@@ -358,7 +358,9 @@ def run_lodge(args, rank, world, local_rank):
     # ---- full detail on the same poses
     fsteps = args.full_steps if args.full_steps is not None else max(1, args.steps // 2)
     ctx.profile_enable(False)
+    torch.cuda.nvtx.range_push("timed_full")
     t_full = timed(FULL, fsteps)
+    torch.cuda.nvtx.range_pop()
     prof_full_timed = ctx.profile_read()
     full_fps = job_throughput(fsteps * P, world, t_full)
 
