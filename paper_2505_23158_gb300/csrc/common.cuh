@@ -21,6 +21,7 @@ constexpr uint32_t kErrOverflow = 1u << 1;  // an output capacity was exceeded
 constexpr uint32_t kErrBadIndex = 1u << 2;  // an index was out of range
 
 constexpr uint32_t kSpinLimit = 1u << 22;   // iterations before a wait gives up
+constexpr uint32_t kSpinFast = 64;          // polls before a wait starts to sleep between polls
 
 // ---------------------------------------------------------------------------
 // decoupled look-back over 32-bit status words: flag in bits 31..30, value in
@@ -37,69 +38,37 @@ __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
     *reinterpret_cast<volatile uint32_t*>(p) = v;
 }
 
-// One status word of a look-back: the published word at idx (waiting for it
-// up to `limit` polls), or an inclusive zero before tile 0 or after a wait
-// that gave up (then kErrTimeout is set in *err).
-__device__ __forceinline__ uint32_t lookback_wait(const uint32_t* status, int64_t idx, uint32_t v,
-                                                  uint32_t* err, uint32_t limit) {
-    if (idx < 0) return kStInc;
-    uint32_t spins = 0;
-    while ((v & ~kStVal) == 0u) {
-        if (++spins > limit) { atomicOr(err, kErrTimeout); return kStInc; }
-        __nanosleep(32);
-        v = ld_volatile(status + idx);
-    }
-    return v;
-}
-
 // Warp-cooperative exclusive look-back for one counter (called by a full
 // warp).  status[tile] must have been published as AGG by this tile already
 // (except tile 0, which needs no look-back).  Returns the exclusive prefix in
-// every lane.  The first step reads the 32 nearest predecessors (one per
-// lane); when none of them holds an inclusive prefix yet (many tiles in
-// flight at once), later steps read 128 predecessors per round trip, four
-// per lane.  A predecessor that stays unpublished for `limit` polls sets
+// every lane.  A predecessor that stays unpublished for `limit` polls sets
 // kErrTimeout in *err and is counted as 0, so the kernel always terminates.
 __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* status, uint32_t tile,
                                                   uint32_t* err, uint32_t limit = kSpinLimit) {
     const int lane = threadIdx.x & 31;
     uint32_t prefix = 0;
     int64_t pos = (int64_t)tile - 1;
-    {
-        const int64_t idx = pos - lane;
-        const uint32_t v = lookback_wait(status, idx, idx >= 0 ? ld_volatile(status + idx) : kStInc, err, limit);
-        const uint32_t inc_mask = __ballot_sync(0xffffffffu, (v & ~kStVal) == kStInc);
-        const int stop = inc_mask ? (__ffs(inc_mask) - 1) : 31;
+    while (pos >= 0) {
+        int64_t idx = pos - lane;
+        uint32_t v = kStInc;  // lanes before tile 0 act as an inclusive zero
+        if (idx >= 0) {
+            uint32_t spins = 0;
+            v = ld_volatile(status + idx);
+            while ((v & ~kStVal) == 0u) {
+                if (++spins > limit) { atomicOr(err, kErrTimeout); v = kStInc; break; }
+                // the predecessor is usually about to publish: poll at once a
+                // few times before backing off with a sleep
+                if (spins > kSpinFast) __nanosleep(32);
+                v = ld_volatile(status + idx);
+            }
+        }
+        uint32_t inc_mask = __ballot_sync(0xffffffffu, (v & ~kStVal) == kStInc);
+        int stop = inc_mask ? (__ffs(inc_mask) - 1) : 31;
         uint32_t mine = (lane <= stop) ? (v & kStVal) : 0u;
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
         prefix += mine;
-        if (inc_mask) return prefix;
-        pos -= 32;
-    }
-    for (;;) {
-        // lane l holds predecessors pos - 4l .. pos - 4l - 3 (nearest first)
-        uint32_t v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t idx = pos - 4 * lane - j;
-            v[j] = idx >= 0 ? ld_volatile(status + idx) : kStInc;
-        }
-        int jinc = 4;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            v[j] = lookback_wait(status, pos - 4 * lane - j, v[j], err, limit);
-            if (jinc == 4 && (v[j] & ~kStVal) == kStInc) jinc = j;
-        }
-        const uint32_t inc_mask = __ballot_sync(0xffffffffu, jinc < 4);
-        const int stop = inc_mask ? (__ffs(inc_mask) - 1) : 32;
-        uint32_t mine = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (lane < stop || (lane == stop && j <= jinc)) mine += v[j] & kStVal;
-        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-        prefix += mine;
         if (inc_mask) break;
-        pos -= 128;
+        pos -= 32;
     }
     return prefix;
 }

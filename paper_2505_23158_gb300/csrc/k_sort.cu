@@ -162,7 +162,7 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
                 uint32_t v = x[j], spins = 0;
                 while ((v & ~kStVal) == 0u) {   // only for t - j >= 0: x[j] = kStInc below 0
                     if (++spins > kSpinLimit) { atomicOr(err, kErrTimeout); v = kStInc; break; }
-                    __nanosleep(20);
+                    if (spins > kSpinFast) __nanosleep(20);
                     v = ld_volatile(status + (size_t)(t - j) * kRadix + d);
                 }
                 excl += v & kStVal;
