@@ -272,7 +272,7 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
 // capacities (key_tile/tile_val hold key_cap words); d_nvis and d_nkeys
 // (u64) the frame's visible records and bin keys.  A frame whose keys exceed
 // key_cap writes none and sets kErrOverflow.
-void launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
+int launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
                          const uint2* rec_rect, int32_t bins_x, int bin_log2, int64_t key_cap,
                          const unsigned long long* d_nkeys, uint32_t* tile_key, uint32_t* tile_val,
                          int rbits, int key_bits, uint32_t* digit_hist, uint32_t* status,

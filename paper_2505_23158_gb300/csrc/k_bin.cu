@@ -352,6 +352,183 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     }
 }
 
+// Emission for large frames in three launches without look-back: count the
+// bin keys of each tile of 1024 depth-sorted records, scan the tile counts
+// in one CTA, then write each tile's keys at its offset.  With thousands of
+// tiles in flight the fused kernel's CTAs spend most of their time at the
+// barrier behind their look-back; here every CTA works independently and
+// the records' rects are read twice instead.
+constexpr int kEmitRecs = 4;                                 // records per thread
+constexpr int64_t kEmitSplitMin = 1ll << 21;                 // record capacity above which it is used
+constexpr int kEmitTileRecs = kEmitThreads * kEmitRecs;      // records per tile
+
+__device__ __forceinline__ uint32_t rec_bin_rect(const uint2* __restrict__ rec_rect, uint32_t rec,
+                                                 int bin_log2, uint32_t& x0, uint32_t& y0, uint32_t& w) {
+    const uint2 p = rec_rect[rec];   // pixel range -> tile range -> bin range
+    x0 = ((p.x & 0xffffu) / kTile) >> bin_log2;
+    y0 = ((p.x >> 16) / kTile) >> bin_log2;
+    const uint32_t x1 = ((p.y & 0xffffu) / kTile) >> bin_log2, y1 = ((p.y >> 16) / kTile) >> bin_log2;
+    w = x1 - x0 + 1u;
+    return w * (y1 - y0 + 1u);
+}
+
+__device__ __forceinline__ int64_t device_count(int64_t cap, const unsigned long long* d) {
+    if (!d) return cap;
+    const unsigned long long c = *d;
+    return c < (unsigned long long)cap ? (int64_t)c : cap;
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+emit_count_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis_cap,
+                  const unsigned long long* __restrict__ d_nvis, const uint2* __restrict__ rec_rect,
+                  int bin_log2, uint32_t* __restrict__ tile_sum, uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_part[kEmitThreads / 32];
+    const int64_t n_vis = device_count(n_vis_cap, d_nvis);
+    const int64_t t0 = (int64_t)blockIdx.x * kEmitTileRecs;
+    if (t0 >= n_vis) return;   // past the device count (later tiles too)
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kEmitRecs; ++j) {
+        const int64_t i = t0 + (int64_t)j * kEmitThreads + threadIdx.x;
+        if (i < n_vis) {
+            uint32_t rec = sorted_rec[i];
+            if ((int64_t)rec >= n_vis) { atomicOr(err, kErrBadIndex); rec = 0; }
+            uint32_t x0, y0, w;
+            sum += rec_bin_rect(rec_rect, rec, bin_log2, x0, y0, w);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kEmitThreads / 32; ++w) tot += s_part[w];
+        tile_sum[blockIdx.x] = tot;
+    }
+}
+
+// One CTA of 1024 threads: the tile counts become exclusive offsets in place;
+// their total must equal the keys the projection counted and fit key_cap.
+__global__ void __launch_bounds__(1024)
+emit_scan_kernel(uint32_t* __restrict__ tile_sum, int64_t n_vis_cap, const unsigned long long* __restrict__ d_nvis,
+                 int64_t key_cap, const unsigned long long* __restrict__ d_nkeys, uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_scan[33];
+    const int64_t n_vis = device_count(n_vis_cap, d_nvis);
+    const int64_t ntiles = (n_vis + kEmitTileRecs - 1) / kEmitTileRecs;
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < ntiles; base += 1024) {
+        const int64_t t = base + threadIdx.x;
+        const uint32_t v = t < ntiles ? tile_sum[t] : 0u;
+        uint32_t total;
+        const uint32_t e = block_exclusive_scan(v, s_scan, &total);
+        if (t < ntiles) tile_sum[t] = (uint32_t)(carry + e);
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        const int64_t n_keys = d_nkeys ? (int64_t)*d_nkeys : key_cap;
+        if ((int64_t)carry != n_keys || (int64_t)carry > key_cap) atomicOr(err, kErrOverflow);
+    }
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+emit_write_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis_cap,
+                  const unsigned long long* __restrict__ d_nvis, const uint2* __restrict__ rec_rect,
+                  int bin_log2, int32_t bins_x, int64_t key_cap, const uint32_t* __restrict__ tile_off,
+                  uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits, int passes,
+                  uint32_t last_mask, uint32_t* __restrict__ digit_hist, uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_nbig;
+    __shared__ uint32_t s_big[kEmitTileRecs];     // (thread << 2 | j) of records with many keys
+    __shared__ uint32_t s_off[kEmitTileRecs];
+    __shared__ uint32_t s_hist[3][256];
+    const int64_t n_vis = device_count(n_vis_cap, d_nvis);
+    const int64_t t0 = (int64_t)blockIdx.x * kEmitTileRecs;
+    if (t0 >= n_vis) return;
+    for (int i = threadIdx.x; i < 3 * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_nbig = 0;
+    // a thread's records are j * kEmitThreads + thread, so that the loads
+    // are coalesced; the keys follow record order, which the scan below
+    // gives as (j, thread) order
+    uint32_t rec[kEmitRecs], cnt[kEmitRecs], bx[kEmitRecs], by[kEmitRecs], bw[kEmitRecs];
+#pragma unroll
+    for (int j = 0; j < kEmitRecs; ++j) {
+        const int64_t i = t0 + (int64_t)j * kEmitThreads + threadIdx.x;
+        rec[j] = 0; cnt[j] = 0; bx[j] = 0; by[j] = 0; bw[j] = 1;
+        if (i < n_vis) {
+            rec[j] = sorted_rec[i];
+            if ((int64_t)rec[j] >= n_vis) rec[j] = 0;   // flagged by the count kernel
+            cnt[j] = rec_bin_rect(rec_rect, rec[j], bin_log2, bx[j], by[j], bw[j]);
+        }
+    }
+    const int64_t tbase = tile_off[blockIdx.x];
+    uint32_t run = 0;   // keys of the record groups before group j in this tile
+    __syncthreads();   // s_hist and s_nbig are set
+#pragma unroll
+    for (int j = 0; j < kEmitRecs; ++j) {
+        uint32_t total;
+        const uint32_t excl = block_exclusive_scan(cnt[j], s_scan, &total);
+        const int64_t at0 = tbase + run + excl;
+        if (at0 + cnt[j] > key_cap) {
+            if (cnt[j]) atomicOr(err, kErrOverflow);
+        } else if (cnt[j] > kFusedThreadKeys) {
+            const uint32_t slot = atomicAdd(&s_nbig, 1u);
+            s_big[slot] = (threadIdx.x << 2) | (uint32_t)j;
+            s_off[slot] = run + excl;
+        } else {
+            uint32_t row = 0, col = 0;
+            for (uint32_t k = 0; k < cnt[j]; ++k) {
+                const uint32_t bin = (by[j] + row) * (uint32_t)bins_x + bx[j] + col;
+                const int64_t at = at0 + k;
+                if (rbits) {
+                    tile_key[at] = (bin << rbits) | rec[j];
+                } else {
+                    tile_key[at] = bin;
+                    tile_val[at] = rec[j];
+                }
+                for (int p = 0; p < passes; ++p)
+                    atomicAdd(&s_hist[p][(bin >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+                if (++col == bw[j]) { col = 0; ++row; }
+            }
+        }
+        // the next record group's keys follow this group's
+        run += total;
+    }
+    __syncthreads();
+    // records with many keys: one warp each; their rects are read again
+    const int lane = threadIdx.x & 31;
+    const uint32_t nbig = s_nbig;
+    for (uint32_t b = threadIdx.x >> 5; b < nbig; b += kEmitThreads / 32) {
+        const uint32_t tj = s_big[b];
+        const int64_t i = t0 + (int64_t)(tj & 3u) * kEmitThreads + (tj >> 2);
+        uint32_t r = sorted_rec[i];
+        if ((int64_t)r >= n_vis) r = 0;
+        uint32_t x0, y0, w;
+        const uint32_t c = rec_bin_rect(rec_rect, r, bin_log2, x0, y0, w);
+        const int64_t at0 = tbase + s_off[b];
+        uint32_t row = lane / w, col = lane - row * w;
+        const uint32_t drow = 32u / w, dcol = 32u - drow * w;
+        for (uint32_t k = lane; k < c; k += 32) {
+            const uint32_t bin = (y0 + row) * (uint32_t)bins_x + x0 + col;
+            if (rbits) {
+                tile_key[at0 + k] = (bin << rbits) | r;
+            } else {
+                tile_key[at0 + k] = bin;
+                tile_val[at0 + k] = r;
+            }
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_hist[p][(bin >> (8 * p)) & (p == passes - 1 ? last_mask : 0xffu)], 1u);
+            row += drow;
+            col += dcol;
+            if (col >= w) { col -= w; ++row; }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < passes * 256; j += kEmitThreads) {
+        const uint32_t c = (&s_hist[0][0])[j];
+        if (c) atomicAdd(digit_hist + j, c);
+    }
+}
+
 // exclusive scan of each pass's 256-bin digit histogram, in place
 __global__ void digit_scan_kernel(uint32_t* hist) {
     __shared__ uint32_t s_scan[33];
@@ -422,21 +599,35 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
 }
 
-void launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
-                         const uint2* rec_rect, int32_t bins_x, int bin_log2, int64_t key_cap,
-                         const unsigned long long* d_nkeys, uint32_t* tile_key, uint32_t* tile_val,
-                         int rbits, int key_bits, uint32_t* digit_hist, uint32_t* status,
-                         uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
+int launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
+                        const uint2* rec_rect, int32_t bins_x, int bin_log2, int64_t key_cap,
+                        const unsigned long long* d_nkeys, uint32_t* tile_key, uint32_t* tile_val,
+                        int rbits, int key_bits, uint32_t* digit_hist, uint32_t* status,
+                        uint32_t* tile_counter, uint32_t* err, cudaStream_t s) {
     const int64_t nb = (n_vis_cap + kEmitThreads - 1) / kEmitThreads;
-    if (nb == 0) return;
+    if (nb == 0) return 0;
     const int P = (key_bits + 7) / 8;
     const int last_bits = key_bits - 8 * (P - 1);
     const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
+    if (n_vis_cap > kEmitSplitMin) {
+        // count, scan, write (the tile counts and offsets live in `status`,
+        // which holds one word per 256 records)
+        const unsigned nt = (unsigned)((n_vis_cap + kEmitTileRecs - 1) / kEmitTileRecs);
+        emit_count_kernel<<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2, status,
+                                                      err);
+        emit_scan_kernel<<<1, 1024, 0, s>>>(status, n_vis_cap, d_nvis, key_cap, d_nkeys, err);
+        emit_write_kernel<<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2, bins_x,
+                                                      key_cap, status, tile_key, tile_val, rbits, P, last_mask,
+                                                      digit_hist, err);
+        digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
+        return 4;
+    }
     emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, rec_rect, bin_log2, bins_x,
                                                             key_cap, tile_key, tile_val, rbits, P, last_mask,
                                                             digit_hist, status, tile_counter, err, d_nvis,
                                                             d_nkeys);
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
+    return 2;
 }
 
 void launch_digit_scan(uint32_t* hist, int passes, cudaStream_t s) {

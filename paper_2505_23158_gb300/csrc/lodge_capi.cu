@@ -705,8 +705,9 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, sizeof(uint32_t) * (size_t)etiles, s));
     }
     prof_begin(sl, LODGE_STAGE_EMIT, s);
+    int emit_n = 0;
     if (deferred) {
-        launch_emit_counted(rs.as<uint32_t>(), n_vis, d_nvis, ws.rec_rect.as<uint2>(), bins_x, bl, n_bkeys,
+        emit_n = launch_emit_counted(rs.as<uint32_t>(), n_vis, d_nvis, ws.rec_rect.as<uint2>(), bins_x, bl, n_bkeys,
                             d_nbk, ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits,
                             ws.doffs.as<uint32_t>(), ws.status2.as<uint32_t>(), sl.d_small + kSmCtrEmit,
                             sl.d_small + kSmErr, s);
@@ -716,7 +717,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
                     ws.tkey.as<uint32_t>(), ws.tval.as<uint32_t>(), rbits, tbits, ws.doffs.as<uint32_t>(),
                     ws.status.as<uint32_t>(), sl.d_small + kSmCtrEmit, sl.d_small + kSmErr, s);
     }
-    prof_end(sl, LODGE_STAGE_EMIT, s, deferred ? 2 : emit_launches(n_vis, n_bkeys, bl));
+    prof_end(sl, LODGE_STAGE_EMIT, s, deferred ? emit_n : emit_launches(n_vis, n_bkeys, bl));
 
     // ---- K6 bin ranges: recorded by the bin sort's last pass (begin by
     // atomic minimum from 0xffffffff, end by atomic maximum from 0); with at

@@ -135,6 +135,26 @@ def test_outdoor_full_camera_list_sampled_pixels(outdoor_full):
         assert stats[j]["n_active"] == g_ref.size
 
 
+def test_outdoor_full_detail_camera_list(outdoor_full):
+    """Full-detail frames of one call (16M active Gaussians: frames after
+    the first of each stream take the count / scan / write emission) equal
+    the same cameras rendered alone bit for bit, and frame 5's sampled tiles
+    and counts equal the oracle's."""
+    torch, api, ctx, sid, scene, cams, osc = outdoor_full
+    step = list(cams[40:46])
+    imgs, stats = ctx.render(sid, api.FULL, step)
+    for j, cam in enumerate(step):
+        one, st1 = ctx.render(sid, api.FULL, cam)
+        assert torch.equal(one, imgs[j]), j
+        assert st1["n_keys"] == stats[j]["n_keys"] and st1["n_visible"] == stats[j]["n_visible"]
+    cam = step[5]
+    g_ref, m_ref, _ = O.active_set(osc, api.FULL, cam)
+    tiles = tiles_of(cam, 24, 77)
+    ref = O.render(osc, cam, g_ref, m_ref, tiles=tiles)
+    compare_tiles(imgs[5].cpu().numpy(), ref, cam, tiles, "full-detail call frame 5")
+    assert stats[5]["n_keys"] == ref["n_keys"] and stats[5]["n_visible"] == ref["n_visible"]
+
+
 # ---------------------------------------------------------------------------
 # fine-tuning of one chunk cell (2M Gaussians, 32 views at 1280x720)
 # ---------------------------------------------------------------------------
