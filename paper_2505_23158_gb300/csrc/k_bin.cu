@@ -359,7 +359,7 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
 // barrier behind their look-back; here every CTA works independently and
 // the records' rects are read twice instead.
 constexpr int kEmitRecs = 4;                                 // records per thread
-constexpr int64_t kEmitSplitMin = 0;                          // record capacity above which it is used
+constexpr int64_t kEmitSplitMin = 1ll << 21;                 // record capacity above which it is used
 constexpr int kEmitTileRecs = kEmitThreads * kEmitRecs;      // records per tile
 
 __device__ __forceinline__ uint32_t rec_bin_rect(const uint2* __restrict__ rec_rect, uint32_t rec,
