@@ -24,7 +24,7 @@ namespace {
 constexpr int kRadix = 256;
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kMaxPasses = 4;
-constexpr int kLookback = 16;   // predecessors read per look-back step
+constexpr int kLookback = 8;    // predecessors read per look-back step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
