@@ -173,49 +173,6 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
     return true;
 }
 
-// Inverse 2D covariance in Cholesky form, with (1/2) log2(e) folded in:
-// alpha = o' * 2^-((u00 dx + u01 dy)^2 + (u11 dy)^2).  The determinant uses
-// the Cauchy-Binet sum of squared 2x2 minors, which has no cancellation
-// (Sigma' = B B^T + 0.3 I).
-__device__ __forceinline__ void conic_of(const float* B0, const float* B1, float& u00, float& u01, float& u11) {
-    const float aB = B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2];
-    const float cB = B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2];
-    const float bB = B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2];
-    const float m01 = fmaf(B0[0], B1[1], -B0[1] * B1[0]);
-    const float m02 = fmaf(B0[0], B1[2], -B0[2] * B1[0]);
-    const float m12 = fmaf(B0[1], B1[2], -B0[2] * B1[1]);
-    const float D = m01 * m01 + m02 * m02 + m12 * m12 + 0.3f * (aB + cB) + 0.09f;
-    const float c = cB + 0.3f;
-    const float rD = 1.0f / sqrtf(D);
-    u11 = sqrtf(kHalfLog2e / c);
-    u00 = u11 * c * rD;
-    u01 = -u11 * bB * rD;
-}
-
-// Colour: real SH up to the scene's degree at the unit direction camera ->
-// mean (d = mean - chat), plus 0.5 (clamped at 0 by the caller).
-__device__ __forceinline__ void sh_colour(const DevScene& sc, const DevCamera& cam, float d0, float d1, float d2,
-                                          const float4* __restrict__ ssh, int64_t npad, uint32_t idx,
-                                          float* rgb) {
-    rgb[0] = rgb[1] = rgb[2] = 0.5f;
-    float dx = d0 - cam.clo[0], dy = d1 - cam.clo[1], dz = d2 - cam.clo[2];
-    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float Y[16];
-    sh_basis(dx * inv, dy * inv, dz * inv, Y);
-    const int nf = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
-#pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        if (4 * j >= nf) break;
-        float4 v4 = __ldcs(ssh + (int64_t)j * npad + idx);
-        float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const int q = 4 * j + cc;
-            if (q < nf) rgb[q % 3] = fmaf(Y[q / 3], vv[cc], rgb[q % 3]);
-        }
-    }
-}
-
 // six CTAs per SM (at most 42 registers): the kernel is bound by the
 // latency of its dependent gathers, so resident warps matter more than the
 // few spilled words
@@ -334,8 +291,40 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     float u00 = 0.f, u01 = 0.f, u11 = 0.f;
     float rgb[3] = {0.5f, 0.5f, 0.5f};
     if (vis) {
-        conic_of(B0, B1, u00, u01, u11);
-        sh_colour(sc, cam, d0, d1, d2, ssh, npad, idx, rgb);
+        // ---- inverse 2D covariance in Cholesky form, with (1/2) log2(e)
+        // folded in: alpha = o' * 2^-((u00 dx + u01 dy)^2 + (u11 dy)^2).  The
+        // determinant uses the Cauchy-Binet sum of squared 2x2 minors, which
+        // has no cancellation (Sigma' = B B^T + 0.3 I).
+        const float aB = B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2];
+        const float cB = B1[0] * B1[0] + B1[1] * B1[1] + B1[2] * B1[2];
+        const float bB = B0[0] * B1[0] + B0[1] * B1[1] + B0[2] * B1[2];
+        const float m01 = fmaf(B0[0], B1[1], -B0[1] * B1[0]);
+        const float m02 = fmaf(B0[0], B1[2], -B0[2] * B1[0]);
+        const float m12 = fmaf(B0[1], B1[2], -B0[2] * B1[1]);
+        const float D = m01 * m01 + m02 * m02 + m12 * m12 + 0.3f * (aB + cB) + 0.09f;
+        const float c = cB + 0.3f;
+        const float rD = 1.0f / sqrtf(D);
+        u11 = sqrtf(kHalfLog2e / c);
+        u00 = u11 * c * rD;
+        u01 = -u11 * bB * rD;
+
+        // ---- colour: real SH up to degree 3 at the unit direction camera -> mean
+        float dx = d0 - cam.clo[0], dy = d1 - cam.clo[1], dz = d2 - cam.clo[2];
+        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis(dx * inv, dy * inv, dz * inv, Y);
+        const int nf = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            if (4 * j >= nf) break;
+            float4 v4 = __ldcs(ssh + (int64_t)j * npad + idx);
+            float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int idx = 4 * j + cc;
+                if (idx < nf) rgb[idx % 3] = fmaf(Y[idx / 3], vv[cc], rgb[idx % 3]);
+            }
+        }
     }
 
     if (threadIdx.x < 32) {
@@ -372,215 +361,6 @@ project_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict
     P.o.depth_val[pos] = pos;
 }
 
-
-// ---------------------------------------------------------------------------
-// Compacting projection: a CTA takes 1024 active entries and works in dense
-// phases instead of one entry per thread throughout.
-//   1. every entry's mean and (scale, opacity) are read (four consecutive
-//      entries a thread) and may_splat drops the Gaussians the key spec
-//      certainly culls; the others are compacted into shared memory;
-//   2. the key spec runs on those, the visible ones are compacted in entry
-//      order and counted (key counts, depth digits), the CTA's visible count
-//      is published and its offset found by look-back;
-//   3. the conic and the SH colour run on the visible ones, whose records are
-//      written at their offsets.
-// Phase 3 repeats the visible Gaussians' key spec (same operations, same
-// results) rather than keeping it in shared memory.  Every lane works on a
-// surviving entry in phases 2 and 3, and one look-back serves 1024 entries.
-constexpr int kProjEntries = 1024;
-constexpr int kProjPer = kProjEntries / kProjThreads;
-static_assert(kProjPer * kProjThreads == kProjEntries, "whole entries per thread");
-
-// false when the key spec certainly yields no key: behind the near plane,
-// opacity below 1/255 (both with the key spec's own operations), or a pixel
-// rect off the image even at the largest extent the Gaussian's scales allow.
-// The rect bound: the key spec's B0 = T0 M diag(sigma) with M and the
-// camera rotation orthonormal, so |B0|^2 <= sigma_max^2 |T0|^2 with
-// |T0|^2 = (fx / z)^2 (1 + u^2) (likewise B1); the key spec's Q for an
-// opacity only shrinks under the 2D filter's compensation (at most 1).  The
-// bound is widened by 1% in the variance, 0.1% and 1e-3 px in the radius,
-// far beyond the FP32 rounding of either side.
-__device__ __forceinline__ bool may_splat(const DevScene& sc, const DevCamera& cam, float mxw, float myw,
-                                          float mzw, float4 so, uint32_t g, float mult) {
-    const float* R = cam.R;
-    const float d0 = fs(mxw, cam.chat[0]), d1 = fs(myw, cam.chat[1]), d2 = fs(mzw, cam.chat[2]);
-    const float px = fa(fa(fa(fm(R[0], d0), fm(R[1], d1)), fm(R[2], d2)), cam.tp[0]);
-    const float py = fa(fa(fa(fm(R[3], d0), fm(R[4], d1)), fm(R[5], d2)), cam.tp[1]);
-    const float pz = fa(fa(fa(fm(R[6], d0), fm(R[7], d1)), fm(R[8], d2)), cam.tp[2]);
-    if (!(pz > cam.znear)) return false;
-    int l = 0;
-    while (l + 1 < sc.num_levels && (int64_t)g >= sc.level_off[l + 1]) ++l;
-    const float v = sc.filter_var[l];
-    float smax = fmaxf(fmaxf(so.x, so.y), so.z);
-    float op = fm(so.w, mult);
-    if (v > 0.f) {
-        const float sig0 = __fsqrt_rn(fa(fm(so.x, so.x), v));
-        const float sig1 = __fsqrt_rn(fa(fm(so.y, so.y), v));
-        const float sig2 = __fsqrt_rn(fa(fm(so.z, so.z), v));
-        const float comp = fm(fm(__fdiv_rn(so.x, sig0), __fdiv_rn(so.y, sig1)), __fdiv_rn(so.z, sig2));
-        op = fm(op, comp);
-        smax = fmaxf(fmaxf(sig0, sig1), sig2);
-    }
-    if (!(op >= (float)(1.0 / 255.0))) return false;
-    const float Q = extent_q(op);
-    const float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
-    const float mx = fa(fm(cam.fx, u), cam.cx);
-    const float my = fa(fm(cam.fy, w), cam.cy);
-    const float jx = cam.fx / pz, jy = cam.fy / pz;
-    const float s2 = 1.01f * smax * smax;
-    const float rx = 1.001f * sqrtf(Q * (s2 * jx * jx * (1.f + u * u) + 0.3f)) + 1e-3f;
-    const float ry = 1.001f * sqrtf(Q * (s2 * jy * jy * (1.f + w * w) + 0.3f)) + 1e-3f;
-    if (mx + rx - 0.5f < 0.f || mx - rx - 0.5f > (float)(cam.width - 1)) return false;
-    if (my + ry - 0.5f < 0.f || my - ry - 0.5f > (float)(cam.height - 1)) return false;
-    return true;
-}
-
-// An active entry's gid, attribute index and Eq. 4 multiplier (scene store).
-__device__ __forceinline__ uint32_t entry_of(const ProjParams& P, int64_t i, float& mult,
-                                             uint32_t* __restrict__ err) {
-    const uint32_t e = P.list ? P.list[i] : (uint32_t)i;
-    uint32_t idx = e & kGidMask;
-    mult = 1.f;
-    if ((e & kFlagA) && !(e & kFlagB)) mult = P.tA;
-    else if ((e & kFlagB) && !(e & kFlagA)) mult = P.tB;
-    if ((int64_t)idx >= P.sc.n_total) { atomicOr(err, kErrBadIndex); idx = 0; mult = 0.f; }
-    return idx;
-}
-
-__global__ void __launch_bounds__(kProjThreads, 6)
-project_compact_kernel(ProjParams P, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
-                       uint32_t* __restrict__ err) {
-    __shared__ uint32_t s_tile, s_prefix, s_nsurv, s_nvis;
-    __shared__ uint32_t s_scan[33];
-    __shared__ unsigned long long s_keys, s_bkeys;
-    __shared__ uint32_t s_dh[4][256];           // depth-key digit counts (the depth sort's histogram)
-    __shared__ uint32_t s_surv[kProjEntries];   // phase 1 survivors (offsets in the tile), entry order
-    __shared__ uint32_t s_vis[kProjEntries];    // phase 2 visible ones, entry order
-    if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_keys = 0ull; s_bkeys = 0ull; }
-    if (P.o.depth_hist)
-        for (int j = threadIdx.x; j < 4 * 256; j += kProjThreads) (&s_dh[0][0])[j] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint32_t ntiles = (uint32_t)((P.n_active + kProjEntries - 1) / kProjEntries);
-    const int64_t t0 = (int64_t)tile * kProjEntries;
-    const DevScene& sc = P.sc;
-    const DevCamera& cam = P.cam;
-    const int lane = threadIdx.x & 31;
-
-    // ---- phase 1: four consecutive entries a thread, mean and (scale,
-    // opacity) only; survivors compacted in entry order
-    uint32_t keepm = 0;
-#pragma unroll
-    for (int j = 0; j < kProjPer; ++j) {
-        const int64_t i = t0 + (int64_t)threadIdx.x * kProjPer + j;
-        if (i < P.n_active) {
-            float mult;
-            const uint32_t idx = entry_of(P, i, mult, err);
-            if (may_splat(sc, cam, sc.mx[idx], sc.my[idx], sc.mz[idx], sc.scale_op[idx], idx, mult))
-                keepm |= 1u << j;
-        }
-    }
-    {
-        uint32_t total;
-        const uint32_t excl = block_exclusive_scan((uint32_t)__popc(keepm), s_scan, &total);
-        uint32_t at = excl;
-#pragma unroll
-        for (int j = 0; j < kProjPer; ++j)
-            if (keepm & (1u << j)) s_surv[at++] = (uint32_t)(threadIdx.x * kProjPer + j);
-        if (threadIdx.x == 0) s_nsurv = total;
-    }
-    __syncthreads();
-    const uint32_t nsurv = s_nsurv;
-
-    // ---- phase 2: key spec of the survivors; the visible ones in entry order
-    uint32_t nvis = 0;
-    for (uint32_t base = 0; base < nsurv; base += kProjThreads) {
-        const uint32_t k = base + threadIdx.x;
-        bool vis = false;
-        uint32_t off = 0;
-        KeySplat ks;
-        if (k < nsurv) {
-            off = s_surv[k];
-            float mult;
-            const uint32_t idx = entry_of(P, t0 + off, mult, err);
-            vis = key_splat(sc, cam, sc.mx[idx], sc.my[idx], sc.mz[idx], sc.scale_op, sc.quat, idx, idx, mult, ks);
-            if (vis) {
-                const int npl = (3 * (sc.sh_degree + 1) * (sc.sh_degree + 1) + 3) / 4;
-                for (int j = 0; j < npl; ++j)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(sc.sh + (int64_t)j * P.n_pad + idx));
-            }
-        }
-        uint32_t total;
-        const uint32_t excl = block_exclusive_scan(vis ? 1u : 0u, s_scan, &total);
-        if (vis) s_vis[nvis + excl] = off;
-        nvis += total;
-        uint32_t wsum = vis ? (ks.rx1 - ks.rx0 + 1) * (ks.ry1 - ks.ry0 + 1) : 0u;
-        for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-        if (lane == 0 && wsum) atomicAdd(&s_keys, (unsigned long long)wsum);
-        const int bl = P.o.bin_log2;
-        if (bl > 0) {
-            uint32_t bsum = vis ? ((ks.rx1 >> bl) - (ks.rx0 >> bl) + 1) * ((ks.ry1 >> bl) - (ks.ry0 >> bl) + 1) : 0u;
-            for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
-            if (lane == 0 && bsum) atomicAdd(&s_bkeys, (unsigned long long)bsum);
-        }
-        if (P.o.depth_hist) {
-            const uint32_t zb = vis ? __float_as_uint(ks.z) : 0u;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const uint32_t d = vis ? (zb >> (8 * p)) & 0xffu : 0x100u;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
-                if (vis && lane == __ffs(peers) - 1) atomicAdd(&s_dh[p][d], (uint32_t)__popc(peers));
-            }
-        }
-    }
-    // the CTA's visible count, then its offset
-    if (threadIdx.x == 0) st_volatile(status + tile, (tile == 0 ? kStInc : kStAgg) | nvis);
-    if (threadIdx.x < 32) {
-        uint32_t prefix = 0;
-        if (tile != 0) {
-            prefix = warp_lookback(status, tile, err);
-            if (threadIdx.x == 0) st_volatile(status + tile, kStInc | (prefix + nvis));
-        }
-        if (threadIdx.x == 0) {
-            s_prefix = prefix;
-            if (tile == ntiles - 1) P.o.counts[0] = prefix + nvis;
-        }
-    }
-    __syncthreads();
-    const uint32_t prefix = s_prefix;
-
-    // ---- phase 3: conic and colour of the visible ones, records written
-    for (uint32_t k = threadIdx.x; k < nvis; k += kProjThreads) {
-        const uint32_t off = s_vis[k];
-        float mult;
-        const uint32_t idx = entry_of(P, t0 + off, mult, err);
-        KeySplat ks;
-        key_splat(sc, cam, sc.mx[idx], sc.my[idx], sc.mz[idx], sc.scale_op, sc.quat, idx, idx, mult, ks);
-        float u00, u01, u11;
-        conic_of(ks.B0, ks.B1, u00, u01, u11);
-        float rgb[3];
-        sh_colour(sc, cam, ks.d0, ks.d1, ks.d2, sc.sh, P.n_pad, idx, rgb);
-        const uint32_t pos = prefix + k;
-        P.o.rec_a[pos] = make_float4(ks.mx, ks.my, u00, u01);
-        P.o.rec_b[pos] = make_float4(u11, log2f(ks.op), fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f));
-        P.o.rec_c[pos] = fmaxf(rgb[2], 0.f);
-        P.o.rec_rect[pos] = make_uint2(ks.px0 | (ks.py0 << 16), ks.px1 | (ks.py1 << 16));
-        P.o.rec_gid[pos] = idx;
-        P.o.depth_key[pos] = __float_as_uint(ks.z);
-        P.o.depth_val[pos] = pos;
-    }
-    // ---- the CTA's key counts and depth digit counts
-    if (threadIdx.x == 0 && s_keys)
-        atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 2), s_keys);
-    if (threadIdx.x == 0 && s_bkeys)
-        atomicAdd(reinterpret_cast<unsigned long long*>(P.o.counts + 4), s_bkeys);
-    if (P.o.depth_hist && nvis) {
-        for (int j = threadIdx.x; j < 4 * 256; j += kProjThreads) {
-            const uint32_t c = (&s_dh[0][0])[j];
-            if (c) atomicAdd(P.o.depth_hist + j, c);
-        }
-    }
-}
 
 // K10: tile-key counts of the greedy depth-threshold search (Sec. 3,
 // "Selecting depth thresholds") for one view, for every candidate value of
@@ -661,14 +441,12 @@ void launch_project(const DevScene& sc, const DevCamera& cam, const uint32_t* li
     P.tB = tB;
     P.o = o;
     if (src) P.src = *src;
-    if (n_active == 0) return;
-    if (src) {   // chunk blocks of a streamed scene: one entry per thread
-        const int64_t ntiles = (n_active + kProjThreads - 1) / kProjThreads;
+    int64_t ntiles = (n_active + kProjThreads - 1) / kProjThreads;
+    if (ntiles == 0) return;
+    if (src)
         project_kernel<true><<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
-    } else {
-        const int64_t ntiles = (n_active + kProjEntries - 1) / kProjEntries;
-        project_compact_kernel<<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
-    }
+    else
+        project_kernel<false><<<(unsigned)ntiles, kProjThreads, 0, s>>>(P, status, tile_counter, err);
 }
 
 size_t threshold_cost_smem(int K) { return sizeof(unsigned long long) * (2 * K + 2) + sizeof(float) * K; }
