@@ -222,15 +222,14 @@ emit_keys_rect_kernel(const uint32_t* __restrict__ koff, const uint32_t* __restr
 }
 
 // Coarse bins (a few keys per record): offsets and emission in one pass.
-// A CTA takes 512 depth-sorted records, scans their bin counts and finds
+// A CTA takes 256 depth-sorted records, scans their bin counts and finds
 // its key offset by decoupled look-back.  A record of at most 32 keys is
 // written by its own thread; larger ones (the nearest records, which all
 // fall in the first CTAs) go to a shared list that the CTA's warps take one
 // record at a time, the lanes striding over the record's keys.  The bin
 // sort's digit counts are kept in shared memory and flushed once.
 constexpr uint32_t kFusedThreadKeys = 32;
-constexpr int kFusedEmitThreads = 512;   // depth-sorted records per CTA of the fused emission
-__global__ void __launch_bounds__(kFusedEmitThreads)
+__global__ void __launch_bounds__(kEmitThreads)
 emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
                   const uint2* __restrict__ rec_rect, int bin_log2, int32_t bins_x, int64_t n_keys,
                   uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits,
@@ -248,19 +247,19 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     if (d_nkeys) n_keys = (int64_t)*d_nkeys;
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_tile, s_prefix, s_nbig;
-    __shared__ uint32_t s_big[kFusedEmitThreads];
-    __shared__ uint32_t s_off[kFusedEmitThreads];
-    __shared__ uint32_t s_cnt[kFusedEmitThreads];
-    __shared__ uint2 s_rect[kFusedEmitThreads];
-    __shared__ uint32_t s_rec[kFusedEmitThreads];
+    __shared__ uint32_t s_big[kEmitThreads];
+    __shared__ uint32_t s_off[kEmitThreads];
+    __shared__ uint32_t s_cnt[kEmitThreads];
+    __shared__ uint2 s_rect[kEmitThreads];
+    __shared__ uint32_t s_rec[kEmitThreads];
     __shared__ uint32_t s_hist[3][256];
-    for (int i = threadIdx.x; i < 3 * 256; i += kFusedEmitThreads) (&s_hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 3 * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
     if (threadIdx.x == 0) { s_tile = atomicAdd(counter, 1u); s_nbig = 0; }
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint32_t ntiles = (uint32_t)((n_vis + kFusedEmitThreads - 1) / kFusedEmitThreads);
+    const uint32_t ntiles = (uint32_t)((n_vis + kEmitThreads - 1) / kEmitThreads);
     if (tile >= ntiles) return;   // past the device count (later tiles too)
-    const int64_t i = (int64_t)tile * kFusedEmitThreads + threadIdx.x;
+    const int64_t i = (int64_t)tile * kEmitThreads + threadIdx.x;
     uint32_t cnt = 0, rec = 0, x0 = 0, y0 = 0, w = 1;
     if (i < n_vis) {
         rec = sorted_rec[i];
@@ -323,7 +322,7 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
     // large records: one warp each
     const int lane = threadIdx.x & 31;
     const uint32_t nbig = s_nbig;
-    for (uint32_t b = threadIdx.x >> 5; b < nbig; b += kFusedEmitThreads / 32) {
+    for (uint32_t b = threadIdx.x >> 5; b < nbig; b += kEmitThreads / 32) {
         const uint32_t t = s_big[b];
         const uint2 rr = s_rect[t];
         const uint32_t bx0 = rr.x & 0xffffu, by0 = rr.x >> 16, bw = rr.y, bc = s_cnt[t];
@@ -347,7 +346,7 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < passes * 256; j += kFusedEmitThreads) {
+    for (int j = threadIdx.x; j < passes * 256; j += kEmitThreads) {
         const uint32_t c = (&s_hist[0][0])[j];
         if (c) atomicAdd(digit_hist + j, c);
     }
@@ -574,8 +573,7 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
     const uint32_t last_mask = last_bits >= 8 ? 0xffu : ((1u << last_bits) - 1u);
     if (n_keys > 0 && n_keys < kEmitWarpMinKeys * n_vis && bin_log2 > 0) {
         // coarse bins: a few keys per record, one fused pass
-        const int64_t nbf = (n_vis + kFusedEmitThreads - 1) / kFusedEmitThreads;
-        emit_fused_kernel<<<(unsigned)nbf, kFusedEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, bin_log2, bins_x,
+        emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis, rec_rect, bin_log2, bins_x,
                                                                 n_keys, tile_key, tile_val, rbits, P, last_mask,
                                                                 digit_hist, status, tile_counter, err, nullptr,
                                                                 nullptr);
@@ -624,8 +622,7 @@ int launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const uns
         digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
         return 4;
     }
-    const int64_t nbf = (n_vis_cap + kFusedEmitThreads - 1) / kFusedEmitThreads;
-    emit_fused_kernel<<<(unsigned)nbf, kFusedEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, rec_rect, bin_log2, bins_x,
+    emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, rec_rect, bin_log2, bins_x,
                                                             key_cap, tile_key, tile_val, rbits, P, last_mask,
                                                             digit_hist, status, tile_counter, err, d_nvis,
                                                             d_nkeys);
