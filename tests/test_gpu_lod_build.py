@@ -126,3 +126,25 @@ def test_build_level_one(env):
         assert last < first, (rec["round"], first, last)
     kept = [r["kept"] for r in hist]
     assert kept[0] >= kept[1] >= kept[2]
+
+
+def test_render_params_lod_arguments_checked(env):
+    """Descending thresholds, a trained level out of range and a saved frame
+    that also scores are refused with LODGE_E_INVALID before any work."""
+    torch, api = env
+    from paper_2505_23158_gb300 import lod_build
+    scene = synth.finetune_scene(seed=6, n=2000)
+    cam = synth.finetune_cameras(scene, seed=6, n=1, width=64, height_px=48)[0]
+    with api.Lodge(0) as ctx:
+        base = lod_build.level_params(scene.levels[0], torch.device("cuda"))
+        levels = [base, base, base]
+        with pytest.raises(api.LodgeError):
+            ctx.render_params_lod(levels, cam, [20.0, 10.0], [0.0, 0.0, 0.0])
+        with pytest.raises(api.LodgeError):
+            ctx.render_params_lod(levels, cam, [10.0, 20.0], [0.0, 0.0, 0.0], train_level=3, save=True)
+        score = torch.zeros(3 * base[0].shape[0], device="cuda")
+        with pytest.raises(api.LodgeError):
+            ctx.render_params_lod(levels, cam, [10.0, 20.0], [0.0, 0.0, 0.0], train_level=1, save=True,
+                                  score=score)
+        img, st, h = ctx.render_params_lod(levels, cam, [10.0, 20.0], [0.0, 0.0, 0.0])
+        assert h is None and img.shape == (48, 64, 3)
