@@ -4,15 +4,20 @@
 Workload: the outdoor LOD scene (16M / 4M / 1M / 250k Gaussians over a 1 km x
 1 km heightfield, 16 x 16 chunk grid, SH degree 3, fp32 attributes) and a
 300-pose street-level trajectory at 1920 x 1080.  A step renders
---poses-per-step consecutive poses of the trajectory in LOD+chunk mode with
-opacity blending (the paper's method) through one render call (the call's
-frames alternate between two streams, so one frame's stages overlap the
-next one's); value = frames/s over all ranks.  The latency of a single
-frame rendered alone, and the per-stage device times of such frames, are
-reported beside it.  The
-same poses are also rendered at full detail (every level-0 Gaussian) on the
-same GPU for the speedup.  Inputs are resident in HBM before timing (5.0 GB
-scene, larger than L2, no flush between steps).
+--poses-per-step consecutive poses (400 by default, wrapping around the
+trajectory) in LOD+chunk mode with opacity blending (the paper's method)
+through one render call, whose frames take turns on six streams; value =
+frames/s over all ranks.  Inputs are resident in HBM before timing (5.0 GB
+scene, larger than L2, no flush between steps).  Reported beside it:
+  * the same poses at full detail (every level-0 Gaussian) on the same GPU,
+    and the speedup;
+  * the latency and per-stage device times of single frames, the paper's
+    timing protocol (median of 7 renders per pose), the compositing's
+    roofline;
+  * end to end through the host-buffer call over the same steps;
+  * the oracle's frame rate on the host cores (cpu_baseline);
+  * the large scene's 64-camera 4K call, a fine-tuning step of one level,
+    and a serving sweep over four streamed scenes under a 60 GB budget.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lodge|reference]
 
