@@ -117,6 +117,8 @@ struct Slot {
     int index = 0;
     cudaStream_t own = nullptr;   // stream created for this slot (request loop)
     cudaEvent_t fence = nullptr;  // orders slot 1's stream against the caller's
+    cudaStream_t copy = nullptr;   // host-buffer calls: the images' copies back to the host
+    cudaEvent_t copy_ev = nullptr; // a frame's end on its render stream, for its copy
     Workspace ws;
     uint32_t* d_small = nullptr;
     uint32_t* h_small = nullptr;  // pinned

@@ -229,6 +229,8 @@ static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
     }
     if (sl.own) cudaStreamDestroy(sl.own);
     if (sl.fence) cudaEventDestroy(sl.fence);
+    if (sl.copy) cudaStreamDestroy(sl.copy);
+    if (sl.copy_ev) cudaEventDestroy(sl.copy_ev);
     (void)ctx;
 }
 
@@ -1577,8 +1579,19 @@ lodge_status lodge_select_lod(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode,
     return LODGE_OK;
 }
 
+// A frame's image back to the host on its slot's copy stream, after the
+// frame's work on its render stream `si`: the render stream goes on with the
+// slot's next frame while the copy runs.
+static lodge_status copy_back_async(Slot& sl, float* h_dst, const float* d_src, size_t nfloat, cudaStream_t si) {
+    if (!sl.copy) CUDA_TRY(cudaStreamCreateWithFlags(&sl.copy, cudaStreamNonBlocking));
+    if (!sl.copy_ev) CUDA_TRY(cudaEventCreateWithFlags(&sl.copy_ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(sl.copy_ev, si));
+    CUDA_TRY(cudaStreamWaitEvent(sl.copy, sl.copy_ev, 0));
+    return copy_back(h_dst, d_src, nfloat, sl.copy);
+}
+
 // The body of lodge_render; h_rgb != null also copies each frame's image to
-// h_rgb (same layout as d_rgb) on the frame's stream right after the frame,
+// h_rgb (same layout as d_rgb) on its slot's copy stream right after the frame,
 // so the copies of earlier frames overlap the rendering of later ones.
 static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mode, const lodge_camera* cams,
                                 int32_t n_cams, float* d_rgb, void* stream, int32_t save_for_backward,
@@ -1625,6 +1638,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
         for (int k = 0; k < m; ++k) {
             Slot* q = rsl[k];
             if (q->tail_pending || !q->pending.empty()) cudaStreamSynchronize(rst[k]);
+            if (h_rgb && q->copy) cudaStreamSynchronize(q->copy);
             q->tail_pending = false;
             q->pending.clear();
             q->share_sms = false;
@@ -1649,7 +1663,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
             drain();
             return r;
         }
-        if (h_rgb) r = copy_back(h_rgb + offs[i], d_rgb + offs[i], offs[i + 1] - offs[i], si);
+        if (h_rgb) r = copy_back_async(sl, h_rgb + offs[i], d_rgb + offs[i], offs[i + 1] - offs[i], si);
         if (r != LODGE_OK) {
             drain();
             return r;
@@ -1675,6 +1689,14 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
     for (int k = 1; k < m; ++k) {   // the caller's stream ends after the other streams' frames
         CUDA_TRY(cudaEventRecord(rsl[k]->fence, rst[k]));
         CUDA_TRY(cudaStreamWaitEvent(s, rsl[k]->fence, 0));
+    }
+    if (h_rgb) {   // ... and after the images' copies (before any frame is rendered again)
+        for (int k = 0; k < m; ++k) {
+            Slot* q = rsl[k];
+            if (!q->copy) continue;
+            CUDA_TRY(cudaEventRecord(q->copy_ev, q->copy));
+            CUDA_TRY(cudaStreamWaitEvent(s, q->copy_ev, 0));
+        }
     }
     for (Slot* q : rsl) q->share_sms = false;   // frames rendered again below run alone
     for (int i : redo) {
