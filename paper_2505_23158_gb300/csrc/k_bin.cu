@@ -358,9 +358,7 @@ emit_fused_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis,
 // tiles in flight the fused kernel's CTAs spend most of their time at the
 // barrier behind their look-back; here every CTA works independently and
 // the records' rects are read twice instead.
-constexpr int kEmitRecs = 4;                                 // records per thread
 constexpr int64_t kEmitSplitMin = 1ll << 21;                 // record capacity above which it is used
-constexpr int kEmitTileRecs = kEmitThreads * kEmitRecs;      // records per tile
 
 __device__ __forceinline__ uint32_t rec_bin_rect(const uint2* __restrict__ rec_rect, uint32_t rec,
                                                  int bin_log2, uint32_t& x0, uint32_t& y0, uint32_t& w) {
@@ -378,10 +376,12 @@ __device__ __forceinline__ int64_t device_count(int64_t cap, const unsigned long
     return c < (unsigned long long)cap ? (int64_t)c : cap;
 }
 
+template <int kEmitRecs>
 __global__ void __launch_bounds__(kEmitThreads)
 emit_count_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis_cap,
                   const unsigned long long* __restrict__ d_nvis, const uint2* __restrict__ rec_rect,
                   int bin_log2, uint32_t* __restrict__ tile_sum, uint32_t* __restrict__ err) {
+    constexpr int kEmitTileRecs = kEmitThreads * kEmitRecs;
     __shared__ uint32_t s_part[kEmitThreads / 32];
     const int64_t n_vis = device_count(n_vis_cap, d_nvis);
     const int64_t t0 = (int64_t)blockIdx.x * kEmitTileRecs;
@@ -410,11 +410,11 @@ emit_count_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis_cap,
 // One CTA of 1024 threads: the tile counts become exclusive offsets in place;
 // their total must equal the keys the projection counted and fit key_cap.
 __global__ void __launch_bounds__(1024)
-emit_scan_kernel(uint32_t* __restrict__ tile_sum, int64_t n_vis_cap, const unsigned long long* __restrict__ d_nvis,
+emit_scan_kernel(int tile_recs, uint32_t* __restrict__ tile_sum, int64_t n_vis_cap, const unsigned long long* __restrict__ d_nvis,
                  int64_t key_cap, const unsigned long long* __restrict__ d_nkeys, uint32_t* __restrict__ err) {
     __shared__ uint32_t s_scan[33];
     const int64_t n_vis = device_count(n_vis_cap, d_nvis);
-    const int64_t ntiles = (n_vis + kEmitTileRecs - 1) / kEmitTileRecs;
+    const int64_t ntiles = (n_vis + tile_recs - 1) / tile_recs;
     uint64_t carry = 0;
     for (int64_t base = 0; base < ntiles; base += 1024) {
         const int64_t t = base + threadIdx.x;
@@ -430,12 +430,14 @@ emit_scan_kernel(uint32_t* __restrict__ tile_sum, int64_t n_vis_cap, const unsig
     }
 }
 
+template <int kEmitRecs>
 __global__ void __launch_bounds__(kEmitThreads)
 emit_write_kernel(const uint32_t* __restrict__ sorted_rec, int64_t n_vis_cap,
                   const unsigned long long* __restrict__ d_nvis, const uint2* __restrict__ rec_rect,
                   int bin_log2, int32_t bins_x, int64_t key_cap, const uint32_t* __restrict__ tile_off,
                   uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_val, int rbits, int passes,
                   uint32_t last_mask, uint32_t* __restrict__ digit_hist, uint32_t* __restrict__ err) {
+    constexpr int kEmitTileRecs = kEmitThreads * kEmitRecs;
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_nbig;
     __shared__ uint32_t s_big[kEmitTileRecs];     // (thread << 2 | j) of records with many keys
@@ -612,22 +614,26 @@ int launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const uns
     if (n_vis_cap > kEmitSplitMin) {
         // count, scan, write (the tile counts and offsets live in `status`,
         // which holds one word per 256 records)
-        const unsigned nt = (unsigned)((n_vis_cap + kEmitTileRecs - 1) / kEmitTileRecs);
-        emit_count_kernel<<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2, status,
-                                                      err);
-        emit_scan_kernel<<<1, 1024, 0, s>>>(status, n_vis_cap, d_nvis, key_cap, d_nkeys, err);
-        emit_write_kernel<<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2, bins_x,
-                                                      key_cap, status, tile_key, tile_val, rbits, P, last_mask,
-                                                      digit_hist, err);
+        const unsigned nt = (unsigned)((n_vis_cap + 4 * kEmitThreads - 1) / (4 * kEmitThreads));
+        emit_count_kernel<4><<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2,
+                                                         status, err);
+        emit_scan_kernel<<<1, 1024, 0, s>>>(4 * kEmitThreads, status, n_vis_cap, d_nvis, key_cap, d_nkeys, err);
+        emit_write_kernel<4><<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2, bins_x,
+                                                         key_cap, status, tile_key, tile_val, rbits, P, last_mask,
+                                                         digit_hist, err);
         digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
         return 4;
     }
-    emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, rec_rect, bin_log2, bins_x,
-                                                            key_cap, tile_key, tile_val, rbits, P, last_mask,
-                                                            digit_hist, status, tile_counter, err, d_nvis,
-                                                            d_nkeys);
+    // smaller frames: the same three launches with one record a thread
+    emit_count_kernel<1><<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect,
+                                                               bin_log2, status, err);
+    emit_scan_kernel<<<1, 1024, 0, s>>>(kEmitThreads, status, n_vis_cap, d_nvis, key_cap, d_nkeys, err);
+    emit_write_kernel<1><<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2,
+                                                               bins_x, key_cap, status, tile_key, tile_val, rbits,
+                                                               P, last_mask, digit_hist, err);
     digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
-    return 2;
+    (void)tile_counter;
+    return 4;
 }
 
 void launch_digit_scan(uint32_t* hist, int passes, cudaStream_t s) {
