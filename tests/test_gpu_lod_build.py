@@ -13,8 +13,8 @@ for).  Checks:
     trained level, in every round, and the kept set equals the oracle's
     except for Gaussians whose score is within that margin of the threshold;
   * the fine-tuning steps of every round lower the objective they sample
-    (mean L1 over the views and over d_1 at 0.7, 0.85, 1.0, 1.15 and 1.3 of
-    10 m) below its value after the pruning;
+    (0.8 L1 + 0.2 (1 - SSIM), the mean over the views and over d_1 at 0.7,
+    0.85, 1.0, 1.15 and 1.3 of 10 m) below its value after the pruning;
   * level 0 is never changed.
 """
 import numpy as np
