@@ -121,7 +121,7 @@ def test_build_level_one(env):
         undecided = int((~sure_keep & ~sure_drop).sum())
         first, last = rec["loss_pruned"], rec["loss_tuned"]
         print(f"[build] round {rec['round']}: threshold {thr:.3g}, kept {rec['kept']} of {s_gpu.size}, "
-              f"{undecided} within the margin, L1 {first:.5f} -> {last:.5f}")
+              f"{undecided} within the margin, loss {first:.5f} -> {last:.5f}")
         assert rec["kept"] > 0
         assert last < first, (rec["round"], first, last)
     kept = [r["kept"] for r in hist]
