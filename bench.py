@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--no-finetune", action="store_true",
                     help="skip the fine-tuning step (2M Gaussians, 32 views at 1280x720)")
     ap.add_argument("--finetune-steps", type=int, default=3)
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the threshold search, importance, build-loop and K-means timings")
     ap.add_argument("--large-scale", type=float, default=1.0)
     ap.add_argument("--serve-batch", type=int, default=16,
                     help="frames per step of the batched serving run")
@@ -515,6 +517,8 @@ def run_lodge(args, rank, world, local_rank):
         "clocks": clocks,
         "setup_s": {"generate": round(t_gen, 1), "load_scene": round(t_load, 1)},
     }
+    if not args.no_next:
+        res["next_rows"] = run_next_rows(args, ctx, sid, scene, cams, dev)
     ctx.close()
     del out
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -530,6 +534,70 @@ def run_lodge(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         res["finetune_step"] = run_finetune(args, local_rank)
     return res
+
+
+def run_next_rows(args, ctx, sid, scene, cams, dev):
+    """The method's other steps on the bench's scene (device time of
+    synchronous calls, host clock): the greedy depth-threshold search, the
+    importance scores and visibility filtering of one chunk, one round of the
+    per-level build loop on a chunk cell, and the K-means chunk centres.
+    Runs last: the filtering edits one chunk's set."""
+    import torch
+    from paper_2505_23158_gb300 import api, lod_build, synth
+    out = {}
+    # f1: greedy threshold search over 10 trajectory views, 19 candidates
+    views = cams[::30][:10]
+    cand = np.arange(5.0, 100.0, 5.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d, _ = ctx.select_thresholds(sid, views, cand)
+    t = time.perf_counter() - t0
+    out["threshold_search"] = {"ms": round(t * 1e3, 2), "views": len(views), "candidates": int(cand.size),
+                               "levels": scene.num_levels, "chosen_m": [round(float(x), 2) for x in d]}
+    # f2: importance of one chunk's own set over 8 views inside it, then filtering
+    grid = int(round(math.sqrt(scene.chunk_centers.shape[0])))
+    chunk = (grid // 2) * grid + grid // 2
+    cv = synth.chunk_views(scene, chunk, 7, 8, args.width, args.height)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    score = ctx.importance(sid, api.CHUNK, cv, chunk=chunk)
+    torch.cuda.synchronize()
+    t_imp = time.perf_counter() - t0
+    sel, _ = ctx.select(sid, api.CHUNK, cv[0])
+    n_before = sel["n_active"]
+    t0 = time.perf_counter()
+    n_after = ctx.filter_chunk(sid, chunk, score, 0.02)
+    t_f = time.perf_counter() - t0
+    out["importance"] = {"ms_per_view": round(t_imp * 1e3 / len(cv), 3), "views": len(cv),
+                         "size": f"{args.width}x{args.height}", "chunk_set_before": int(n_before),
+                         "chunk_set_after": int(n_after), "filter_ms": round(t_f * 1e3, 2)}
+    # f3: the per-level build loop, level 1 of a 200k-Gaussian chunk cell, 8
+    # views at 640x360, 3 rounds of 100 steps (the paper: 1000)
+    fs = synth.finetune_scene(seed=args.seed + 5, n=200_000)
+    fv = synth.finetune_cameras(fs, seed=args.seed + 5, n=8, width=640, height_px=360)
+    base = lod_build.level_params(fs.levels[0], dev)
+    targets = [ctx.render_params(*base, c, save=False)[0] for c in fv]
+    var = lod_build.filter_variance(0.2, 10.0, fv[0].fy)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g1, hist = lod_build.build_level(ctx, [base], base, [10.0], fv, targets, 0.02, var, [0.0], steps=100,
+                                     seed=1)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    out["lod_build"] = {"s_total": round(t_b, 2), "steps": 300, "ms_per_step_incl_evals": round(t_b * 1e3 / 300, 2),
+                        "kept": [h["kept"] for h in hist],
+                        "loss": [[round(h["loss_pruned"], 5), round(h["loss_tuned"], 5)] for h in hist],
+                        "workload": "level 1 (d_1 = 10 m) of a 200k-Gaussian chunk cell, 8 views at 640x360, "
+                                    "3 rounds of 100 steps, loss 0.8 L1 + 0.2 (1 - SSIM)"}
+    # f4: K-means chunk centres of the trajectory's camera positions (host, FP64)
+    pos = synth.camera_positions(cams)
+    t0 = time.perf_counter()
+    k = api.num_clusters(pos, 10.0)
+    init = synth.kmeans_init(len(pos), k, seed=2)
+    _, _, it = api.kmeans_centers(pos, init, max_iter=100)
+    out["kmeans"] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "cameras": len(pos), "clusters": int(k),
+                     "iterations": int(it)}
+    return out
 
 
 def run_large(args, local_rank):
