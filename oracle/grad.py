@@ -10,7 +10,7 @@ the levels are optimised with gradients through the renderer).
 Steps, in the paper's and 3DGS's order (see oracle.c for each reading):
   activation: s = exp(log s), o = sigmoid(logit), unit quaternion;
   Eq. 3 filter: Sigma = R(q) diag(s^2 + v) R(q)^T, o *= prod s / sqrt(s^2 + v);
-  EWA: p = R mu + t, J, Sigma' = J W Sigma W^T J^T + 0.3 I, mean' in pixels;
+  EWA: p = R mu + t, J (at x/z, y/z clamped to 1.3 tan(fov/2)), Sigma' = J W Sigma W^T J^T + 0.3 I, mean' in pixels;
   colour: real SH up to degree 3 at (mu - c)/|mu - c|, + 0.5, clamped at 0;
   Eq. 1: alpha = min(0.99, o' exp(-1/2 d^T Sigma'^-1 d)), skip alpha < 1/255,
   stop before T would drop below 1e-4, C = sum T alpha rgb.
@@ -99,8 +99,14 @@ def render_t(means, log_scales, quats, logits, sh, cam, sh_degree=3, filter_var=
     cx, cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
     px, py, pz = p[:, 0], p[:, 1], p[:, 2]
     zero = torch.zeros_like(pz)
-    J = torch.stack([torch.stack([fx / pz, zero, -fx * px / (pz * pz)], 1),
-                     torch.stack([zero, fy / pz, -fy * py / (pz * pz)], 1)], 1)
+    # the Jacobian at the laterally clamped point x/z, y/z (3DGS's clamp to
+    # 1.3 tan(fov/2), the limits rounded to FP32 as in the oracle's C side)
+    limx = float(np.float32(1.3 * (int(W) / (2.0 * float(np.float32(cam.fx))))))
+    limy = float(np.float32(1.3 * (int(H) / (2.0 * float(np.float32(cam.fy))))))
+    uc = torch.clamp(px / pz, -limx, limx)
+    wc = torch.clamp(py / pz, -limy, limy)
+    J = torch.stack([torch.stack([fx / pz, zero, -fx * uc / pz], 1),
+                     torch.stack([zero, fy / pz, -fy * wc / pz], 1)], 1)
     Tm = J @ R
     C2 = Tm @ Sig @ Tm.transpose(1, 2)
     a = C2[:, 0, 0] + 0.3

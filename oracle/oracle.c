@@ -280,6 +280,18 @@ static void cam_rel(const orc_camera* cam, float chat[3], float tp[3])
                         + (double)cam->R[3 * i + 1] * (double)chat[1]) + (double)cam->R[3 * i + 2] * (double)chat[2]));
 }
 
+/* Lateral limits of the EWA Jacobian's evaluation point (the 3DGS
+ * rasteriser's clamp, kept by the paper's renderer): x/z and y/z are held
+ * within 1.3 tan(fov/2) of the axis, tan(fovx/2) = W / (2 fx),
+ * tan(fovy/2) = H / (2 fy), formed in FP64 and rounded to FP32.  Without it a
+ * Gaussian just past the near plane far off the axis gets a Jacobian that
+ * stretches its footprint over the whole image. */
+static void lateral_limits(const orc_camera* cam, float* limx, float* limy)
+{
+    *limx = (float)(1.3 * ((double)cam->width / (2.0 * (double)cam->fx)));
+    *limy = (float)(1.3 * ((double)cam->height / (2.0 * (double)cam->fy)));
+}
+
 static float cam_depth32(const orc_camera* cam, const float* mu)
 {
     float chat[3], tp[3];
@@ -297,7 +309,9 @@ static float cam_depth32(const orc_camera* cam, const float* mu)
  *  final opacity o' = (o * mult) [* comp]; cull if o' < 1/255 (no pixel can
  *    pass the 1/255 skip);
  *  u = x/z, w = y/z; mean' = (fx u + cx, fy w + cy);
- *  EWA Jacobian rows j00 = fx/z, j02 = -(j00 u), j11 = fy/z, j12 = -(j11 w);
+ *  EWA Jacobian rows j00 = fx/z, j02 = -(j00 uc), j11 = fy/z, j12 = -(j11 wc),
+ *    its evaluation point clamped laterally: uc = min(max(u, -limx), limx),
+ *    wc likewise with limy (lateral_limits; the mean keeps u, w);
  *  T = J R; M = rotation of the unit quaternion; A = T M; B = A diag(sigma);
  *  Sigma'_xx = ((B00^2 + B01^2) + B02^2) + 0.3, Sigma'_yy likewise;
  *  r = sqrt(Q Sigma'); pixel range [ceil(m - r - 0.5), floor(m + r - 0.5)]
@@ -331,8 +345,11 @@ static int key_spec(const orc_scene* sc, const orc_camera* cam, int64_t g,
     float u = px / pz, w = py / pz;
     float mx = cam->fx * u + cam->cx;
     float my = cam->fy * w + cam->cy;
-    float j00 = cam->fx / pz, j02 = -(j00 * u);
-    float j11 = cam->fy / pz, j12 = -(j11 * w);
+    float limx, limy;
+    lateral_limits(cam, &limx, &limy);
+    float uc = fminf(fmaxf(u, -limx), limx), wc = fminf(fmaxf(w, -limy), limy);
+    float j00 = cam->fx / pz, j02 = -(j00 * uc);
+    float j11 = cam->fy / pz, j12 = -(j11 * wc);
     float T0[3], T1[3];
     for (int k = 0; k < 3; ++k) {
         T0[k] = j00 * R[k] + j02 * R[6 + k];
@@ -443,8 +460,14 @@ static void splat64(const orc_scene* sc, const orc_camera* cam, int64_t g, doubl
     double fx = cam->fx, fy = cam->fy;
     o->mx = fx * p[0] / p[2] + cam->cx;
     o->my = fy * p[1] / p[2] + cam->cy;
-    double J[2][3] = { { fx / p[2], 0.0, -fx * p[0] / (p[2] * p[2]) },
-                       { 0.0, fy / p[2], -fy * p[1] / (p[2] * p[2]) } };
+    /* the Jacobian at the laterally clamped point (lateral_limits) */
+    float limx32, limy32;
+    lateral_limits(cam, &limx32, &limy32);
+    double limx = limx32, limy = limy32;
+    double uc = fmin(fmax(p[0] / p[2], -limx), limx);
+    double wc = fmin(fmax(p[1] / p[2], -limy), limy);
+    double J[2][3] = { { fx / p[2], 0.0, -fx * uc / p[2] },
+                       { 0.0, fy / p[2], -fy * wc / p[2] } };
     /* world covariance Sigma = Rq diag(s^2 + v) Rq^T (Eq. 3 filter added to
      * the covariance; v = 0 leaves 3DGS's Sigma) */
     double w = sc->quats[4 * g], x = sc->quats[4 * g + 1], y = sc->quats[4 * g + 2], z = sc->quats[4 * g + 3];

@@ -129,6 +129,10 @@ struct DevCamera {
     float fx, fy, cx, cy;
     int32_t width, height;
     float znear;
+    // lateral limits of the EWA Jacobian's evaluation point: x/z and y/z are
+    // clamped to +-1.3 tan(fov/2), tan(fovx/2) = W / (2 fx) (the 3DGS
+    // rasteriser's clamp), formed in FP64 and rounded to FP32
+    float limx, limy;
     // camera-relative evaluation: p = R (mu - chat) + tp, with chat = (float)
     // centre and tp = t + R chat formed in FP64; clo = centre - chat
     float chat[3];

@@ -241,8 +241,14 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
         for (int k = 0; k < 3; ++k) { sig[k] = sqrtf(s[k] * s[k] + v); comp *= s[k] / sig[k]; }
     }
     const float iz = 1.f / pz;
-    const float j00 = cam.fx * iz, j02 = -cam.fx * px * iz * iz;
-    const float j11 = cam.fy * iz, j12 = -cam.fy * py * iz * iz;
+    // Jacobian at the laterally clamped point uc = clamp(px / pz), wc likewise;
+    // the clamp passes the derivative only inside the limits (closed range)
+    const float ux = px * iz, uy = py * iz;
+    const bool inx = fabsf(ux) <= cam.limx, iny = fabsf(uy) <= cam.limy;
+    const float uc = fminf(fmaxf(ux, -cam.limx), cam.limx);
+    const float wc = fminf(fmaxf(uy, -cam.limy), cam.limy);
+    const float j00 = cam.fx * iz, j02 = -cam.fx * uc * iz;
+    const float j11 = cam.fy * iz, j12 = -cam.fy * wc * iz;
     float T0[3], T1[3];
     for (int k = 0; k < 3; ++k) {
         T0[k] = j00 * R[k] + j02 * R[6 + k];
@@ -305,10 +311,14 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(BwdParams P) {
         gj11 += gT1[k] * R[3 + k];
         gj12 += gT1[k] * R[6 + k];
     }
-    float gpx = gj02 * (-cam.fx * iz * iz) + gmx * cam.fx * iz;
-    float gpy = gj12 * (-cam.fy * iz * iz) + gmy * cam.fy * iz;
-    float gpz = gj00 * (-cam.fx * iz * iz) + gj02 * (2.f * cam.fx * px * iz * iz * iz) +
-                gj11 * (-cam.fy * iz * iz) + gj12 * (2.f * cam.fy * py * iz * iz * iz) +
+    // j02 = -fx uc / pz: d/dpx = -fx iz duc/dpx, d/dpz = fx uc iz^2 - fx iz duc/dpz
+    // with duc/dpx = iz, duc/dpz = -px iz^2 inside the limits and 0 outside
+    const float dux_dpx = inx ? iz : 0.f, dux_dpz = inx ? -px * iz * iz : 0.f;
+    const float duy_dpy = iny ? iz : 0.f, duy_dpz = iny ? -py * iz * iz : 0.f;
+    float gpx = gj02 * (-cam.fx * iz * dux_dpx) + gmx * cam.fx * iz;
+    float gpy = gj12 * (-cam.fy * iz * duy_dpy) + gmy * cam.fy * iz;
+    float gpz = gj00 * (-cam.fx * iz * iz) + gj02 * (cam.fx * uc * iz * iz - cam.fx * iz * dux_dpz) +
+                gj11 * (-cam.fy * iz * iz) + gj12 * (cam.fy * wc * iz * iz - cam.fy * iz * duy_dpz) +
                 gmx * (-cam.fx * px * iz * iz) + gmy * (-cam.fy * py * iz * iz);
     float gmu[3];
     for (int k = 0; k < 3; ++k) gmu[k] = R[k] * gpx + R[3 + k] * gpy + R[6 + k] * gpz;

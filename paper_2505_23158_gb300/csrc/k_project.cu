@@ -116,8 +116,12 @@ __device__ __forceinline__ bool key_splat(const DevScene& sc, const DevCamera& c
     float u = __fdiv_rn(px, pz), w = __fdiv_rn(py, pz);
     float mx = fa(fm(cam.fx, u), cam.cx);
     float my = fa(fm(cam.fy, w), cam.cy);
-    float j00 = __fdiv_rn(cam.fx, pz), j02 = -fm(j00, u);
-    float j11 = __fdiv_rn(cam.fy, pz), j12 = -fm(j11, w);
+    // the Jacobian at x/z, y/z clamped laterally to (limx, limy); the mean
+    // keeps the unclamped point
+    const float uc = fminf(fmaxf(u, -cam.limx), cam.limx);
+    const float wc = fminf(fmaxf(w, -cam.limy), cam.limy);
+    float j00 = __fdiv_rn(cam.fx, pz), j02 = -fm(j00, uc);
+    float j11 = __fdiv_rn(cam.fy, pz), j12 = -fm(j11, wc);
     float T0[3], T1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {

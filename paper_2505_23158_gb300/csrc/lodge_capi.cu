@@ -309,6 +309,8 @@ static DevCamera make_cam(const lodge_camera& c) {
     d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
     d.width = c.width; d.height = c.height;
     d.znear = c.znear;
+    d.limx = (float)(1.3 * ((double)c.width / (2.0 * (double)c.fx)));
+    d.limy = (float)(1.3 * ((double)c.height / (2.0 * (double)c.fy)));
     for (int i = 0; i < 3; ++i) d.chat[i] = (float)c.center[i];
     for (int i = 0; i < 3; ++i)
         d.tp[i] = (float)((double)c.t[i] + (((double)c.R[3 * i] * (double)d.chat[0] +

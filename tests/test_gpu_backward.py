@@ -59,6 +59,38 @@ def test_gradients_match_fp64_oracle(env, seed, n, wh, fv):
         assert e < 1e-3, f"{name}: relative L2 error {e:.3g}"
 
 
+@pytest.mark.parametrize("seed", [9, 10])
+def test_gradients_past_lateral_limits(env, seed):
+    """Large Gaussians centred off a narrow (20 degree) view, past the EWA
+    Jacobian's lateral limits x/z, y/z = +-1.3 tan(fov/2), reaching into it:
+    the clamped Jacobian's forward and adjoint against the FP64 oracle."""
+    torch, ctx = env
+    from oracle import grad as G
+    import oracle as O
+    n = 80
+    lv = _level(n, seed, spread=1.4, log_mean=-1.0)
+    cam = synth.look_at((0.0, 0.0, -2.5), (0.0, 0.0, 1.0), (0, -1, 0), 48, 40, 20.0)
+    p = lv.means.astype(np.float64) @ cam.R.astype(np.float64).T + cam.t
+    past = ((np.abs(p[:, 0] / p[:, 2]) > 1.3 * cam.width / (2.0 * cam.fx))
+            | (np.abs(p[:, 1] / p[:, 2]) > 1.3 * cam.height / (2.0 * cam.fy)))
+    sc = synth.Scene(levels=[lv], d_thresholds=np.zeros(0), chunk_centers=np.zeros((1, 3)))
+    vis = O.project(O.OracleScene(sc), cam, np.arange(n))["visible"]
+    assert (past & vis).sum() >= 10
+    w = np.random.default_rng(seed + 7).normal(size=(cam.height, cam.width, 3))
+    g_ref, img_ref = G.grads(lv, cam, w)
+    dev = torch.device("cuda")
+    ps = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+          for a in (lv.means, lv.log_scales, lv.quats, lv.opacity_logits, lv.sh.reshape(n, 48))]
+    img, st, h = ctx.render_params(*ps, cam, save=True)
+    gs = [torch.zeros_like(q) for q in ps]
+    ctx.render_backward(h, torch.from_numpy(w.astype(np.float32)).to(dev), *gs)
+    ctx.release(h)
+    assert np.abs(img.cpu().numpy() - img_ref).max() < 2e-4
+    for name, g, r in zip(["means", "log_scales", "quats", "opacity_logits", "sh"], gs, g_ref):
+        e = _rel(g.cpu().numpy().reshape(r.shape).astype(np.float64), r)
+        assert e < 1e-3, f"{name}: relative L2 error {e:.3g}"
+
+
 def test_autograd_function_and_fit_step(env):
     """The torch.autograd.Function wrapper gives the same gradients as the
     raw calls, and a few Adam steps lower an L1 loss against a perturbed

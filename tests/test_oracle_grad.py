@@ -58,9 +58,42 @@ def test_torch_forward_with_filter_and_multipliers():
 @pytest.mark.parametrize("seed", [11, 12])
 def test_autograd_matches_central_differences(seed):
     sc = _scene(12, seed, spread=0.35, log_mean=-1.8)
-    lv = sc.levels[0]
     cam = synth.look_at((0.05, -0.05, -2.0), (0.0, 0.0, 1.0), (0, -1, 0), 20, 16, 50.0)
-    w = np.random.default_rng(seed).normal(size=(16, 20, 3))
+    _check_fd(sc, cam, seed, 60)
+
+
+def _lateral(sc, cam):
+    """x/z and y/z of each Gaussian's camera point against the Jacobian's
+    lateral limits 1.3 W / (2 fx), 1.3 H / (2 fy): how many of the visible
+    Gaussians lie past them."""
+    p = sc.levels[0].means.astype(np.float64) @ cam.R.astype(np.float64).T + cam.t
+    limx = 1.3 * cam.width / (2.0 * cam.fx)
+    limy = 1.3 * cam.height / (2.0 * cam.fy)
+    past = (np.abs(p[:, 0] / p[:, 2]) > limx) | (np.abs(p[:, 1] / p[:, 2]) > limy)
+    vis = O.project(O.OracleScene(sc), cam, np.arange(sc.levels[0].n))["visible"]
+    return int((past & vis).sum())
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_autograd_past_lateral_limits(seed):
+    """Large Gaussians centred off the image, past the Jacobian's lateral
+    limits, reaching into a narrow (20 degree) view: the forward equals
+    oracle.c's, and the gradients through the clamped Jacobian (no x/z
+    derivative of its third column) equal central differences."""
+    sc = _scene(12, seed, spread=1.4, log_mean=-1.0)
+    cam = synth.look_at((0.0, 0.0, -2.5), (0.0, 0.0, 1.0), (0, -1, 0), 20, 16, 20.0)
+    assert _lateral(sc, cam) >= 5
+    ref = O.render(O.OracleScene(sc), cam, np.arange(12))
+    with torch.no_grad():
+        img = G.render_t(*G.params_t(sc.levels[0], False), cam)
+    ok = ~ref["knife"]
+    assert np.abs(img.numpy() - ref["rgb"])[ok].max() < 2e-6
+    _check_fd(sc, cam, seed, 40)
+
+
+def _check_fd(sc, cam, seed, min_checked):
+    lv = sc.levels[0]
+    w = np.random.default_rng(seed).normal(size=(cam.height, cam.width, 3))
     grads, _ = G.grads(lv, cam, w)
     base = [np.asarray(a, np.float32).astype(np.float64) for a in
             (lv.means, lv.log_scales, lv.quats, lv.opacity_logits, lv.sh)]
@@ -91,6 +124,6 @@ def test_autograd_matches_central_differences(seed):
             an = g.reshape(-1)[j]
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-7, (gi, j, fd, an)
             checked += 1
-    assert checked >= 60
+    assert checked >= min_checked
     for g in grads:
         assert np.abs(g).max() > 0

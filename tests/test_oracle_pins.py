@@ -310,6 +310,58 @@ def test_ewa_matches_monte_carlo_projection():
     assert np.allclose(C2 @ K, np.eye(2), atol=1e-12)
 
 
+def _extent_q(o32):
+    """Q of the key rect for an FP32 opacity: 2 ln(255 o_hi) * 1.001 with o_hi
+    the upper end of o's bucket (FP32 exponent and three leading mantissa
+    bits), restated from that definition."""
+    bits = int(np.float32(o32).view(np.uint32))
+    top = bits >> 20
+    hi_bits = ((top + 1) << 20) if top <= (127 << 3) else ((127 << 3) + 1) << 20
+    hi = float(np.uint32(hi_bits).view(np.float32))
+    return float(np.float32(2.0 * math.log(255.0 * hi) * 1.001))
+
+
+def test_jacobian_lateral_clamp_closed_form():
+    """The EWA Jacobian is evaluated at x/z, y/z clamped to +-1.3 tan(fov/2)
+    (tan(fovx/2) = W / (2 fx); 3DGS's rasteriser): for an isotropic Gaussian of
+    std s at camera point (x, y, z) with R = I, Sigma' = (s f / z)^2 [[1 +
+    uc^2, uc wc], [uc wc, 1 + wc^2]] + 0.3 I, uc, wc the clamped x/z, y/z,
+    while the mean keeps the unclamped point.  Checked inside the limits (no
+    change), past one limit and past both with negative signs; the FP32 key
+    rect of each is the tile range of that covariance's extent."""
+    cam = synth.plain_camera(256, 256)
+    f = float(cam.fx)
+    lim = float(np.float32(1.3 * (256 / (2.0 * f))))
+    assert abs(lim - 1.3 * math.tan(math.radians(30.0))) < 1e-6
+    sigma, o = 0.5, 0.8
+    pts = [(1.5, 0.0), (3.0, 0.9), (-3.3, -3.6)]          # camera (x, y) at z = 3
+    sc = _single_level_scene([[x, y, 0.0] for x, y in pts], [[math.log(sigma)] * 3] * 3,
+                             [[1, 0, 0, 0]] * 3, [_logit(o)] * 3, [_sh_for_rgb((1, 1, 1))] * 3)
+    osc = O.OracleScene(sc)
+    pr = O.project(osc, cam, np.arange(3))
+    assert pr["visible"].all()
+    se = float(osc.scales[0, 0])
+    k = (se * f / 3.0) ** 2
+    o32 = float(pr["o32"][0])
+    Q = _extent_q(o32)
+    for i, (x, y) in enumerate(pts):
+        u, w = float(np.float32(x)) / 3.0, float(np.float32(y)) / 3.0   # stored in FP32
+        uc, wc = min(max(u, -lim), lim), min(max(w, -lim), lim)
+        expect = np.array([k * (1 + uc * uc) + 0.3, k * uc * wc, k * (1 + wc * wc) + 0.3])
+        assert np.allclose(pr["cov"][i], expect, rtol=1e-9, atol=1e-9), (i, pr["cov"][i], expect)
+        assert abs(pr["mean2"][i, 0] - (f * u + cam.cx)) < 1e-9
+        assert abs(pr["mean2"][i, 1] - (f * w + cam.cy)) < 1e-9
+        plain = np.array([k * (1 + u * u) + 0.3, k * u * w, k * (1 + w * w) + 0.3])
+        assert (i == 0) == np.allclose(plain, expect), i
+        # key rect: pixel range [ceil(m - r - 0.5), floor(m + r - 0.5)],
+        # r = sqrt(Q Sigma'_kk), clipped to the image, in tiles of 16
+        mx, my = f * u + cam.cx, f * w + cam.cy
+        rx, ry = math.sqrt(Q * expect[0]), math.sqrt(Q * expect[2])
+        x0 = max(math.ceil(mx - rx - 0.5), 0); x1 = min(math.floor(mx + rx - 0.5), 255)
+        y0 = max(math.ceil(my - ry - 0.5), 0); y1 = min(math.floor(my + ry - 0.5), 255)
+        assert tuple(pr["rect"][i]) == (x0 // 16, y0 // 16, x1 // 16, y1 // 16), (i, pr["rect"][i])
+
+
 def test_quaternion_normalisation():
     """Activation's unit quaternion: for raw q of any scale the output has unit
     norm to FP32 rounding and is parallel to q (q_i |q^| = q^_i |q|); and a
