@@ -221,14 +221,16 @@ lodge_status lodge_kmeans_centers(const double* positions, int32_t n, int32_t k,
 
 /* Size of the bins whose key lists the renders of this context sort and
  * composite from: squares of 2^log2_tiles x 2^log2_tiles 16x16 tiles
- * (0..3; the context starts at 3, 128x128 pixels).  A Gaussian is keyed once
- * per bin its tile rect touches (Sec. 3, "Preliminaries: 3DGS", assigns it
- * to every tile it overlaps); compositing walks the bin's list for each of
- * the bin's tiles and skips the Gaussians whose tile rect misses the tile,
- * so images do not depend on the setting, only the number of keys sorted
- * does.  Frames saved for the adjoint (save_for_backward) and the
- * importance walk always use per-tile lists (log2_tiles = 0).  Errors:
- * LODGE_E_INVALID for a NULL ctx or log2_tiles outside 0..3. */
+ * (0..3), or -1 (the context's start value) to choose per frame: per-tile
+ * lists for active sets of 2^21 Gaussians or more, bins of 2x2 tiles below.
+ * A Gaussian is keyed once per bin its tile rect touches (Sec. 3,
+ * "Preliminaries: 3DGS", assigns it to every tile it overlaps); compositing
+ * walks the bin's list for each of the bin's tiles and skips the Gaussians
+ * that cannot reach a pixel of the tile, so images do not depend on the
+ * setting, only the number of keys sorted and records walked do.  Frames
+ * saved for the adjoint (save_for_backward) and the importance walk always
+ * use per-tile lists (log2_tiles = 0).  Errors: LODGE_E_INVALID for a NULL
+ * ctx or log2_tiles outside -1..3. */
 lodge_status lodge_set_bin_size(lodge_ctx* ctx, int32_t log2_tiles);
 
 /* Render n_cams cameras of one scene in `mode`.  d_rgb (device,

@@ -131,6 +131,7 @@ struct Slot {
     // from the frames that did sync).  Each such frame copies its status
     // words into a pinned ring entry; the slot's harvest reads them.
     int64_t key_cap = 0;
+    int key_cap_bl = -1;          // the bin size key_cap was learned for
     static constexpr int kRing = 32;
     uint32_t* h_ring = nullptr;   // pinned, kRing x kSmWords
     int ring_next = 0;
@@ -144,6 +145,7 @@ struct Slot {
         double tA = 1.0, tB = 1.0;
         bool packed = false;            // bin keys packed with the record
         int sort_passes = 0;
+        int bin_log2 = 0;               // 0: per-tile lists (bin keys = tile keys)
     };
     std::vector<Pending> pending;
     bool prof_on = false;
@@ -196,7 +198,7 @@ struct lodge_ctx {
     cudaStream_t upload_stream = nullptr;
     lodge::ResidencyStats res;
     int fail_next_uploads = 0;       // host-side fault injection
-    int bin_log2 = 3;                // key lists per bin of 2^bin_log2 x 2^bin_log2 tiles
+    int bin_log2 = -1;               // key lists per bin of 2^bin_log2 x 2^bin_log2 tiles (-1: by frame)
 };
 
 namespace lodge {

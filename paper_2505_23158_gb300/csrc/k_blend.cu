@@ -9,15 +9,17 @@
 // transmittance below 1e-4; a warp whose 64 pixels have all stopped skips
 // the batch, and the CTA leaves as soon as all 256 have stopped.
 //
+// Frames that keep neither the final transmittance nor list positions take
+// the filtered walk: each batch also stages the records' pixel rects, and
+// every warp ballots which of the 128 records have a pixel rect meeting its
+// own 8x8 block and an ellipse reaching one of its pixel centres
+// (splat_meets_block), and visits only those, in list order.  A record
+// failing either test would be skipped by every pixel of the block (alpha <
+// 1/255 there), so the image is the unfiltered walk's bit for bit.
 // With coarse bins (squares of 2^bin_log2 tiles) the tile walks its bin's
-// key list: each batch also stages the records' pixel rects, and every warp
-// ballots which of the 128 records have a pixel rect meeting its own 8x8
-// block (such a record's tile rect holds the tile, so it is on the tile's
-// own list) and visits only those, in list order.  A record whose rect
-// misses the block would be skipped by every pixel of it (alpha < 1/255
-// outside the rect), so the image is the per-tile lists' bit for bit.  This
-// walk is branch-free: a pixel that stops gets T = 0, which makes every
-// later step a no-op.
+// key list the same way (a record meeting the block has a tile rect holding
+// the tile, so it is on the tile's own list).  This walk is branch-free: a
+// pixel that stops gets T = 0, which makes every later step a no-op.
 //
 // Per pixel and Gaussian (record = mean', upper-triangular U with
 // U^T U = (1/2) log2(e) Sigma'^-1, log2 o', colour):
@@ -97,6 +99,32 @@ __device__ __forceinline__ void blend_px_flat(const float alpha, const float4 bb
     T = go ? Tn : (ok ? 0.f : T);
 }
 
+// Whether a splat can reach alpha >= 1/255 at some pixel centre of an 8x8
+// block whose first pixel centre is (bx, by).  With d = p - mean' and
+// q(d) = (u00 dx + u01 dy)^2 + (u11 dy)^2 (the exponent's quadratic, a convex
+// function with its minimum 0 at d = 0), the least q over the centres' box
+// [bx, bx + 7] x [by, by + 7] lies on the line dx = xc or on dy = yc, where
+// xc, yc are the box coordinates nearest the mean (0 where the box spans it):
+// along each line q is a one-dimensional quadratic whose minimiser is
+// clamped to the box.  A pixel centre can pass the 1/255 skip only if
+// q <= log2 o' + log2 255; the test adds a margin of 0.01 (in log2 units)
+// for the rounding of q, so it never drops a record that some pixel of the
+// block would composite, and the walk's result is the unfiltered walk's.
+__device__ __forceinline__ bool splat_meets_block(const float4 a, const float4 b, float bx, float by) {
+    constexpr float kLog2_255 = 7.99435343f;
+    const float X0 = bx - a.x, X1 = X0 + 7.f, Y0 = by - a.y, Y1 = Y0 + 7.f;
+    const float xc = fminf(fmaxf(0.f, X0), X1), yc = fminf(fmaxf(0.f, Y0), Y1);
+    const float u00 = a.z, u01 = a.w, u11 = b.x;
+    // on dx = xc the minimiser is dy = -u00 u01 xc / (u01^2 + u11^2)
+    const float dy = fminf(fmaxf(__fdividef(-u00 * u01 * xc, fmaf(u01, u01, u11 * u11)), Y0), Y1);
+    const float t1 = fmaf(u00, xc, u01 * dy), w1 = u11 * dy;
+    // on dy = yc it is dx = -u01 yc / u00
+    const float dx = fminf(fmaxf(__fdividef(-u01 * yc, u00), X0), X1);
+    const float t2 = fmaf(u00, dx, u01 * yc), w2 = u11 * yc;
+    const float q = fminf(fmaf(t1, t1, w1 * w1), fmaf(t2, t2, w2 * w2));
+    return q <= b.y + (kLog2_255 + 0.01f);
+}
+
 template <bool kBins, bool kCount = false>
 __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     __shared__ float4 sa[2][kBlendBatch];
@@ -123,10 +151,13 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
     const float pxf = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     const uint32_t wx0 = tx * kTile + (warp & 1) * 8, wx1 = wx0 + 7;   // the warp's 8x8 block
     const uint32_t wy0 = ty * kTile + (warp >> 1) * 8, wy1 = wy0 + 7;
+    const float bxf = (float)wx0 + 0.5f, byf = (float)wy0 + 0.5f;   // the block's first pixel centre
     const uint2* __restrict__ rec_rect = f.rec_rect;
-    // a frame of a binned batch launch may still have per-tile lists
-    const bool binned = kBins && f.bin_log2 > 0 && rec_rect != nullptr;
-    const int bin = binned ? (ty >> f.bin_log2) * f.bins_x + (tx >> f.bin_log2) : tile;
+    // the rect test needs the records' pixel rects (frames that keep the
+    // final transmittance or positions have none); a frame of a filtered
+    // batch launch may still have per-tile lists without rects
+    const bool binned = kBins && rec_rect != nullptr;
+    const int bin = (binned && f.bin_log2 > 0) ? (ty >> f.bin_log2) * f.bins_x + (tx >> f.bin_log2) : tile;
     uint2 rg = ranges[bin];
     if (rg.y > n_keys || rg.x > rg.y) rg = make_uint2(0, 0);  // never for a consistent sort
     const int n = (int)(rg.y - rg.x);
@@ -169,7 +200,8 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
         __syncthreads();
         const int cnt = min(kBlendBatch, n - b * kBlendBatch);
         if (kBins) {
-            // which records of the batch touch this tile: 4 ballots per warp
+            // which records of the batch can reach this warp's block: 4
+            // ballots per warp
             uint32_t m[kBlendBatch / 32];
 #pragma unroll
             for (int w = 0; w < kBlendBatch / 32; ++w) {
@@ -183,6 +215,8 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
                     hit = (r.x & 0xffffu) <= wx1 && (r.y & 0xffffu) >= wx0 && (r.x >> 16) <= wy1 &&
                           (r.y >> 16) >= wy0;
                 }
+                // and its ellipse reaches a pixel centre of the block
+                if (hit) hit = splat_meets_block(sa[buf][k], sb[buf][k], bxf, byf);
                 m[w] = __ballot_sync(0xffffffffu, hit);
             }
             // flat walk over the hits, 8 batch positions at a time, the warp
@@ -419,12 +453,13 @@ BlendFrame blend_frame(const DevCamera& cam, const uint2* ranges, const uint32_t
     f.vmask = vmask;
     f.n_keys = (uint32_t)n_keys;
     f.n_rec = (uint32_t)std::max<int64_t>(n_rec, 1);
-    // the binned walk keeps neither the final transmittance nor positions
-    f.bin_log2 = (rec_rect && !o.T_final && !o.last) ? bin_log2 : 0;
+    // the filtered walk keeps neither the final transmittance nor positions
+    const bool filt = rec_rect && !o.T_final && !o.last;
+    f.bin_log2 = filt ? bin_log2 : 0;
     f.bins_x = (cam.tiles_x + (1 << f.bin_log2) - 1) >> f.bin_log2;
     f.ranges = ranges;
     f.tile_val = tile_val;
-    f.rec_rect = rec_rect;
+    f.rec_rect = filt ? rec_rect : nullptr;
     f.pairs = nullptr;
     f.rec_a = rec_a;
     f.rec_b = rec_b;
@@ -447,23 +482,24 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* til
     if (tile_ctr) {
         grid = (unsigned)std::min<int64_t>(f.ntiles, (int64_t)device_sms() * kBlendCtasPerSM);
     }
+    const bool filt = f.rec_rect != nullptr;
     if (tile_ctr) {
         if (pairs) {   // counting variant (profiling), same walk
-            if (f.bin_log2 > 0)
+            if (filt)
                 blend_loop_kernel<true, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
             else
                 blend_loop_kernel<false, true><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
-        } else if (f.bin_log2 > 0) {
+        } else if (filt) {
             blend_loop_kernel<true, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
         } else {
             blend_loop_kernel<false, false><<<grid, kBlendThreads, 0, s>>>(f, tile_ctr);
         }
     } else if (pairs) {
-        if (f.bin_log2 > 0)
+        if (filt)
             blend_kernel<true, true><<<grid, kBlendThreads, 0, s>>>(f);
         else
             blend_kernel<false, true><<<grid, kBlendThreads, 0, s>>>(f);
-    } else if (f.bin_log2 > 0) {
+    } else if (filt) {
         blend_kernel<true, false><<<grid, kBlendThreads, 0, s>>>(f);
     } else {
         blend_kernel<false, false><<<grid, kBlendThreads, 0, s>>>(f);
@@ -474,13 +510,13 @@ void launch_blend_batch(const BlendFrame* frames, int n, cudaStream_t s, uint32_
     BlendBatch bb;
     uint32_t base = 0;
     bb.n = 0;
-    bool bins = false;   // the binned walk also serves frames with per-tile lists
+    bool bins = false;   // the filtered walk also serves frames without rects
     for (int i = 0; i < n && i < kMaxBlendBatch; ++i) {
         if (frames[i].ntiles == 0) continue;
         bb.f[bb.n] = frames[i];
         bb.f[bb.n].tile_base = base;
         base += (uint32_t)frames[i].ntiles;
-        bins = bins || frames[i].bin_log2 > 0;
+        bins = bins || frames[i].rec_rect != nullptr;
         ++bb.n;
     }
     if (bb.n == 0) return;

@@ -565,6 +565,9 @@ __global__ void fill_kernel(FillPlan f) {
 // left on the device, scratch sized by capacities; see Slot::Pending): it
 // then sets pend->used, appends *pend to the slot's pending list, and its
 // stats and profile counts are taken when the slot is harvested.
+// default bin size: per-tile lists from this active-set size up
+constexpr int64_t kPerTileActiveMin = 1ll << 21;
+
 static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, const Active& act,
                                  const lodge_camera& c, float* d_rgb, cudaStream_t s, Saved* save,
                                  lodge_frame_stats* st, bool end_sync, float* importance = nullptr,
@@ -589,11 +592,20 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     TRY(ensure(ctx, ws.status, sizeof(uint32_t) * (size_t)ptiles, s));
     TRY(ensure(ctx, ws.doffs, sizeof(uint32_t) * 8 * 256, s));
     // frames kept for the adjoint and the importance walk use per-tile lists
-    // (their per-pixel positions index the tile's own list)
-    const int bl = (save || importance) ? 0 : ctx->bin_log2;
-    // no mid-frame sync: plain coarse-binned frames once the slot knows a key
-    // capacity (the fused emission needs bins of several tiles)
-    const bool deferred = pend && !save && !importance && !sl.prof_count && bl > 0 &&
+    // (their per-pixel positions index the tile's own list); otherwise the
+    // context's bin size, or by default per-tile lists for active sets of
+    // kPerTileActiveMin Gaussians or more (many small splats, whose bin
+    // lists are long against their tiles' lists) and bins of 2x2 tiles below
+    const int bl = (save || importance) ? 0
+                   : ctx->bin_log2 >= 0 ? ctx->bin_log2
+                   : (na >= kPerTileActiveMin ? 0 : 1);
+    // the key capacity is learned per bin size
+    if (!save && !importance && sl.key_cap_bl != bl) {
+        sl.key_cap = 0;
+        sl.key_cap_bl = bl;
+    }
+    // no mid-frame sync: plain frames once the slot knows a key capacity
+    const bool deferred = pend && !save && !importance && !sl.prof_count &&
                           sl.key_cap > 0 && na > 0 && (int)sl.pending.size() < Slot::kRing;
     if (pend) pend->used = false;
     const int32_t bins_x = (cam.tiles_x + (1 << bl) - 1) >> bl;
@@ -655,7 +667,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         n_vis = na;              // capacities
         n_bkeys = sl.key_cap;
         d_nvis = reinterpret_cast<const unsigned long long*>(sl.d_small + kSmProj);
-        d_nbk = reinterpret_cast<const unsigned long long*>(sl.d_small + kSmProj + 4);
+        d_nbk = reinterpret_cast<const unsigned long long*>(sl.d_small + kSmProj + (bl > 0 ? 4 : 2));
     } else {
         TRY(sync_slot(ctx, sl, s));
         n_vis = sl.h_small[kSmProj];
@@ -668,9 +680,10 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         if (bl > 0) {
             std::memcpy(&nk64, sl.h_small + kSmProj + 4, 8);
             n_bkeys = (int64_t)nk64;
-            // capacity for later frames of this slot that skip the sync
-            sl.key_cap = std::max<int64_t>(sl.key_cap, n_bkeys + n_bkeys / 2 + 65536);
         }
+        // capacity for later frames of this slot that skip the sync
+        if (!save && !importance)
+            sl.key_cap = std::max<int64_t>(sl.key_cap, n_bkeys + n_bkeys / 2 + 65536);
     }
     const size_t nv1 = (size_t)std::max<int64_t>(n_vis, 1), nk1 = (size_t)std::max<int64_t>(n_bkeys, 1);
 
@@ -802,6 +815,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         pend->tB = act.tB;
         pend->packed = rbits != 0;
         pend->sort_passes = (tbits + 7) / 8;
+        pend->bin_log2 = bl;
         sl.pending.push_back(*pend);
         return LODGE_OK;
     }
@@ -875,7 +889,7 @@ static lodge_status harvest(lodge_ctx* ctx, Slot& sl, cudaStream_t s, std::vecto
         const uint32_t err = w[kSmErr];
         uint64_t nk, nb;
         std::memcpy(&nk, w + kSmProj + 2, 8);
-        std::memcpy(&nb, w + kSmProj + 4, 8);
+        std::memcpy(&nb, w + kSmProj + (p.bin_log2 > 0 ? 4 : 2), 8);
         const int64_t n_vis = w[kSmProj];
         // keep the capacity half a frame ahead of the largest seen
         sl.key_cap = std::max<int64_t>(sl.key_cap, (int64_t)(nb + nb / 2 + 65536));
@@ -2228,7 +2242,7 @@ lodge_status lodge_residency_stats(lodge_ctx* ctx, lodge_residency* out) {
 }
 
 lodge_status lodge_set_bin_size(lodge_ctx* ctx, int32_t log2_tiles) {
-    if (!ctx || log2_tiles < 0 || log2_tiles > 3) return fail(LODGE_E_INVALID, "bad argument");
+    if (!ctx || log2_tiles < -1 || log2_tiles > 3) return fail(LODGE_E_INVALID, "bad argument");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->bin_log2 = log2_tiles;
     return LODGE_OK;

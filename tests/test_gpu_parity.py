@@ -378,7 +378,7 @@ def test_camera_list_equals_single_frames(ctx, torch_cuda, log2):
                 assert torch_cuda.equal(one, img)
                 assert st1["n_keys"] == st["n_keys"]
     finally:
-        ctx.set_bin_size(3)
+        ctx.set_bin_size(-1)
 
 
 # ---------------------------------------------------------------------------
@@ -420,7 +420,7 @@ def test_binned_lists_same_image(ctx, outdoor, torch_cuda, log2):
                 ref = O.render(osc, cam, g_ref, m_ref)
                 compare_images(img.cpu().numpy(), ref, f"bins {log2} pose {i}")
     finally:
-        ctx.set_bin_size(3)
+        ctx.set_bin_size(-1)
 
 
 @pytest.mark.parametrize("wh", [(17, 33), (1, 1), (257, 129), (100, 70)])
@@ -438,15 +438,45 @@ def test_binned_lists_ragged_sizes(ctx, plain_loaded, torch_cuda, wh):
             img, _ = ctx.render(sid, FULL, cam)
             assert torch_cuda.equal(img, ref), f"bins {k}"
     finally:
-        ctx.set_bin_size(3)
+        ctx.set_bin_size(-1)
 
 
 def test_bin_size_argument_checked(ctx):
     from paper_2505_23158_gb300.api import LodgeError
-    for bad in (-1, 4):
+    for bad in (-2, 4):
         with pytest.raises(LodgeError):
             ctx.set_bin_size(bad)
-    ctx.set_bin_size(3)
+    ctx.set_bin_size(-1)
+
+
+@pytest.mark.parametrize("log2", [-1, 0, 1, 3])
+def test_filtered_walk_equals_unfiltered(ctx, torch_cuda, log2):
+    """The compositing walk that skips, per 8x8 pixel block, the records
+    whose rect misses the block or whose ellipse reaches none of its pixel
+    centres gives the image of the walk that visits every record of the
+    tile's list (the one frames kept for the adjoint use), bit for bit: on
+    the plain workload's anisotropic splats and on outdoor frames with near,
+    large and off-axis splats."""
+    dev = torch_cuda.device("cuda")
+    cases = []
+    scene, cams = synth.workload_plain(0)
+    cases.append((scene.levels[0], cams[:2]))
+    scene2, cams2 = synth.workload_outdoor(seed=3, n_poses=6, scale=0.01, width=320, height_px=180)
+    cases.append((scene2.levels[0], cams2[:3]))
+    try:
+        ctx.set_bin_size(log2)
+        for lv, cs in cases:
+            n = lv.n
+            ps = [torch_cuda.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+                  for a in (lv.means, lv.log_scales, lv.quats, lv.opacity_logits, lv.sh.reshape(n, 48))]
+            for cam in cs:
+                img, st, _ = ctx.render_params(*ps, cam, save=False)
+                ref, st2, h = ctx.render_params(*ps, cam, save=True)
+                ctx.release(h)
+                assert st["n_keys"] == st2["n_keys"]
+                assert torch_cuda.equal(img, ref)
+    finally:
+        ctx.set_bin_size(-1)
 
 
 @pytest.mark.parametrize("log2", [0, 2])
@@ -466,7 +496,7 @@ def test_counting_mode_pairs(ctx, outdoor, torch_cuda, log2):
         prof = ctx.profile_read()
         ctx.profile_enable(False)
     finally:
-        ctx.set_bin_size(3)
+        ctx.set_bin_size(-1)
     assert torch_cuda.equal(img, plain)
     g_ref, m_ref, info = O.active_set(osc, CHUNK_BLEND, cam)
     ref = O.render(osc, cam, g_ref, m_ref)
