@@ -51,14 +51,14 @@ STAGES = ["select", "union", "project", "depth_sort", "emit", "tile_sort", "rang
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lodge", "reference"], default="lodge")
     ap.add_argument("--scale", type=float, default=1.0, help="scene size factor (1.0 = full)")
     ap.add_argument("--n-poses", type=int, default=300)
     ap.add_argument("--poses-per-step", type=int, default=400,
                     help="consecutive poses per render call (one step), wrapping around the "
-                         "300-pose trajectory; 400 keeps 20 timed steps above one second")
+                         "300-pose trajectory; 400 keeps the 20 timed steps above one second")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--full-steps", type=int, default=None)
