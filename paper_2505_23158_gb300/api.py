@@ -383,8 +383,9 @@ class Lodge:
         return {f: getattr(r, f) for f, _ in r._fields_}
 
     def set_bin_size(self, log2_tiles: int):
-        """Key lists per bin of 2**log2_tiles x 2**log2_tiles tiles (0..3);
-        images do not depend on it (lodge_set_bin_size)."""
+        """Key lists per bin of 2**log2_tiles x 2**log2_tiles tiles (0..3),
+        or -1 to choose per frame (the default); images do not depend on it
+        (lodge_set_bin_size)."""
         A.call("lodge_set_bin_size", self._h, int(log2_tiles))
 
     def inject_upload_failures(self, n: int):

@@ -271,8 +271,9 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
                  int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s);
-// The same emission with the counts on the device (bins of several tiles
-// only, one fused launch plus the digit scan): n_vis_cap and key_cap are
+// The same emission with the counts on the device (one fused launch plus
+// the digit scan, or count / scan / write above a 2^21-record capacity; bins
+// of any size, per-tile lists included): n_vis_cap and key_cap are
 // capacities (key_tile/tile_val hold key_cap words); d_nvis and d_nkeys
 // (u64) the frame's visible records and bin keys.  A frame whose keys exceed
 // key_cap writes none and sets kErrOverflow.
