@@ -134,6 +134,7 @@ struct Slot {
     int key_cap_bl = -1;          // the bin size key_cap was learned for
     static constexpr int kRing = 32;
     uint32_t* h_ring = nullptr;   // pinned, kRing x kSmWords
+    cudaEvent_t ring_ev[kRing] = {};   // each entry's copy done (on the frame's stream)
     int ring_next = 0;
     struct Pending {
         int ring = 0;                   // ring entry

@@ -203,6 +203,7 @@ lodge_status create_slot(lodge_ctx* ctx, Slot** out) {
     CUDA_TRY(cudaMallocHost((void**)&sl->h_small, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMallocHost((void**)&sl->h_tail, sizeof(uint32_t) * kSmWords));
     CUDA_TRY(cudaMallocHost((void**)&sl->h_ring, sizeof(uint32_t) * kSmWords * Slot::kRing));
+    for (int k = 0; k < Slot::kRing; ++k) CUDA_TRY(cudaEventCreateWithFlags(&sl->ring_ev[k], cudaEventDisableTiming));
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
         CUDA_TRY(cudaEventCreate(&sl->ev_beg[k]));
         CUDA_TRY(cudaEventCreate(&sl->ev_end[k]));
@@ -223,6 +224,8 @@ static void destroy_slot(lodge_ctx* ctx, Slot& sl) {
     if (sl.h_small) cudaFreeHost(sl.h_small);
     if (sl.h_tail) cudaFreeHost(sl.h_tail);
     if (sl.h_ring) cudaFreeHost(sl.h_ring);
+    for (int k = 0; k < Slot::kRing; ++k)
+        if (sl.ring_ev[k]) cudaEventDestroy(sl.ring_ev[k]);
     for (int k = 0; k < LODGE_NUM_STAGES; ++k) {
         if (sl.ev_beg[k]) cudaEventDestroy(sl.ev_beg[k]);
         if (sl.ev_end[k]) cudaEventDestroy(sl.ev_end[k]);
@@ -804,6 +807,7 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
         sl.ring_next = (sl.ring_next + 1) % Slot::kRing;
         CUDA_TRY(cudaMemcpyAsync(sl.h_ring + (size_t)ring * kSmWords, sl.d_small, sizeof(uint32_t) * kSmWords,
                                  cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaEventRecord(sl.ring_ev[ring], s));
         pend->ring = ring;
         pend->used = true;
         pend->st = st;
@@ -878,50 +882,73 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
 // deferred frames (stats, profile).  A frame whose bin keys outgrew the
 // slot's capacity wrote no keys: the capacity grows and the frame's index is
 // appended to *redo, to be rendered again with its mid-frame sync.
+static void take_pending(Slot& sl, const Slot::Pending& p, std::vector<int>* redo, lodge_status* r);
+
 static lodge_status harvest(lodge_ctx* ctx, Slot& sl, cudaStream_t s, std::vector<int>* redo) {
     (void)ctx;
     if (sl.pending.empty()) return LODGE_OK;
     CUDA_TRY(cudaStreamSynchronize(s));
     prof_collect(sl);
     lodge_status r = LODGE_OK;
-    for (const Slot::Pending& p : sl.pending) {
-        const uint32_t* w = sl.h_ring + (size_t)p.ring * kSmWords;
-        const uint32_t err = w[kSmErr];
-        uint64_t nk, nb;
-        std::memcpy(&nk, w + kSmProj + 2, 8);
-        std::memcpy(&nb, w + kSmProj + (p.bin_log2 > 0 ? 4 : 2), 8);
-        const int64_t n_vis = w[kSmProj];
-        // keep the capacity half a frame ahead of the largest seen
-        sl.key_cap = std::max<int64_t>(sl.key_cap, (int64_t)(nb + nb / 2 + 65536));
-        if (err & kErrOverflow) {
-            sl.prof.redone += 1;
-            if (redo) redo->push_back(p.frame);
-            continue;
-        }
-        if (r == LODGE_OK && (err & kErrTimeout))
-            r = fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
-        if (r == LODGE_OK && (err & kErrBadIndex))
-            r = fail(LODGE_E_INVALID, "out-of-range index in an active list (status 0x%x)", err);
-        sl.prof.frames += 1;
-        sl.prof.keys += (int64_t)nk;
-        sl.prof.bin_keys += (int64_t)nb;
-        if (p.packed) sl.prof.packed_keys += (int64_t)nb;
-        sl.prof.bin_sort_passes += nb > 1 ? p.sort_passes : 0;
-        sl.prof.visible += n_vis;
-        sl.prof.active += p.n_active;
-        if (p.st) {
-            p.st->n_active = p.n_active;
-            p.st->n_visible = n_vis;
-            p.st->n_keys = (int64_t)nk;
-            p.st->n_tiles = p.n_tiles;
-            p.st->chunk_a = p.A;
-            p.st->chunk_b = p.B;
-            p.st->t_a = p.tA;
-            p.st->t_b = p.tB;
-        }
-    }
+    for (const Slot::Pending& p : sl.pending) take_pending(sl, p, redo, &r);
     sl.pending.clear();
     return r;
+}
+
+// The oldest deferred frames of a slot, until `keep` remain: each waits for
+// its own ring entry only, so the slot's later frames keep running while the
+// host goes on enqueuing (a full harvest would drain the slot's stream).
+static lodge_status harvest_front(Slot& sl, size_t keep, std::vector<int>* redo) {
+    lodge_status r = LODGE_OK;
+    size_t k = 0;
+    for (; k + keep < sl.pending.size(); ++k) {
+        const Slot::Pending& p = sl.pending[k];
+        CUDA_TRY(cudaEventSynchronize(sl.ring_ev[p.ring]));
+        take_pending(sl, p, redo, &r);
+    }
+    sl.pending.erase(sl.pending.begin(), sl.pending.begin() + (ptrdiff_t)k);
+    return r;
+}
+
+// one deferred frame's status words and counts: stats, profile counters,
+// capacity, errors; a frame that overflowed its key capacity is listed for
+// rendering again
+static void take_pending(Slot& sl, const Slot::Pending& p, std::vector<int>* redo, lodge_status* rp) {
+    lodge_status& r = *rp;
+    const uint32_t* w = sl.h_ring + (size_t)p.ring * kSmWords;
+    const uint32_t err = w[kSmErr];
+    uint64_t nk, nb;
+    std::memcpy(&nk, w + kSmProj + 2, 8);
+    std::memcpy(&nb, w + kSmProj + (p.bin_log2 > 0 ? 4 : 2), 8);
+    const int64_t n_vis = w[kSmProj];
+    // keep the capacity half a frame ahead of the largest seen
+    sl.key_cap = std::max<int64_t>(sl.key_cap, (int64_t)(nb + nb / 2 + 65536));
+    if (err & kErrOverflow) {
+        sl.prof.redone += 1;
+        if (redo) redo->push_back(p.frame);
+        return;
+    }
+    if (r == LODGE_OK && (err & kErrTimeout))
+        r = fail(LODGE_E_TIMEOUT, "a device-side wait timed out (status 0x%x)", err);
+    if (r == LODGE_OK && (err & kErrBadIndex))
+        r = fail(LODGE_E_INVALID, "out-of-range index in an active list (status 0x%x)", err);
+    sl.prof.frames += 1;
+    sl.prof.keys += (int64_t)nk;
+    sl.prof.bin_keys += (int64_t)nb;
+    if (p.packed) sl.prof.packed_keys += (int64_t)nb;
+    sl.prof.bin_sort_passes += nb > 1 ? p.sort_passes : 0;
+    sl.prof.visible += n_vis;
+    sl.prof.active += p.n_active;
+    if (p.st) {
+        p.st->n_active = p.n_active;
+        p.st->n_visible = n_vis;
+        p.st->n_keys = (int64_t)nk;
+        p.st->n_tiles = p.n_tiles;
+        p.st->chunk_a = p.A;
+        p.st->chunk_b = p.B;
+        p.st->t_a = p.tA;
+        p.st->t_b = p.tB;
+    }
 }
 
 // Select and render one camera of a scene on a slot; blocks of streamed
@@ -1671,7 +1698,7 @@ static lodge_status render_cams(lodge_ctx* ctx, int32_t scene_id, lodge_mode mod
         Slot::Pending pd;
         pd.frame = i;
         lodge_status r = LODGE_OK;
-        if (defer && (int)sl.pending.size() >= Slot::kRing) r = harvest(ctx, sl, si, &redo);
+        if (defer && (int)sl.pending.size() >= Slot::kRing) r = harvest_front(sl, Slot::kRing / 2, &redo);
         if (r == LODGE_OK)
             r = render_one(ctx, sl, sc, mode, cams[i], d_rgb + offs[i], si, sv.get(),
                            stats ? stats + i : nullptr, last, nullptr, defer ? &pd : nullptr);
