@@ -554,3 +554,43 @@ def test_deferred_frames_with_nothing_visible(torch_cuda):
                 one, st1 = c2.render(sid, mode, cam)
                 assert torch_cuda.equal(one, img)
                 assert st1["n_keys"] == st["n_keys"]
+
+
+def _dense_cluster_scene(n, seed=5):
+    """n small, nearly opaque Gaussians packed into a 5 cm cube that the
+    256x256 plain camera sees inside one 16x16 tile (pixels 144..159 in x and
+    y): that tile's bin holds every one of them."""
+    rng = np.random.default_rng(seed)
+    lvl = synth.Level((rng.uniform(-0.025, 0.025, (n, 3)) + [0.325, 0.325, 0.0]).astype(np.float32),
+                      np.full((n, 3), np.log(0.004), np.float32),
+                      rng.normal(size=(n, 4)).astype(np.float32),
+                      np.full(n, 2.0, np.float32),
+                      rng.normal(0, 0.3, (n, 16, 3)).astype(np.float32))
+    return synth.Scene(levels=[lvl], d_thresholds=np.zeros(0), chunk_centers=np.zeros((1, 3)))
+
+
+@pytest.mark.parametrize("log2", [1, 3])
+def test_deferred_frames_equal_synced_frames_dense_bins(ctx, torch_cuda, log2):
+    """Frames of a camera list that run without a mid-frame sync (capacities,
+    counts on the device) give the images of frames with their sync (here in
+    counting mode) bit for bit, also when one bin holds thousands of keys: on
+    the plain workload (bins of hundreds to about 1300 keys) and on clusters
+    of 6000 and 30000 Gaussians inside one tile."""
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams = synth.workload_plain(0)
+    cam = synth.plain_camera(256, 256)
+    cases = [(ctx.load_scene(scene), cams[:3]),
+             (ctx.load_scene(_dense_cluster_scene(6000)), [cam] * 3),
+             (ctx.load_scene(_dense_cluster_scene(30000)), [cam] * 3)]
+    try:
+        ctx.set_bin_size(log2)
+        for sid, cs in cases:
+            ctx.profile_enable(True, count_pairs=True)
+            refs = [ctx.render(sid, FULL, c)[0].clone() for c in cs]
+            ctx.profile_enable(False)
+            ctx.render(sid, FULL, cs[0])           # the slot learns its key capacity
+            imgs, _ = ctx.render(sid, FULL, list(cs))
+            for img, ref in zip(imgs, refs):
+                assert torch_cuda.equal(img, ref)
+    finally:
+        ctx.set_bin_size(-1)
