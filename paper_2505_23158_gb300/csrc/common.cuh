@@ -246,12 +246,15 @@ constexpr int64_t sort_scratch_words(int64_t n, int passes) {
 // scratch, tiles past the count exit at once, and digit_offsets must be
 // given (the sort then runs for any count, 0 and 1 included).
 // scratch_cleared: the caller has zeroed the scratch (no memset here).
+// digit_counts: digit_offsets holds the per-pass digit counts instead, which
+// each pass scans itself (no separate scan launch).
 size_t sort_scratch_bytes(int64_t n, int key_bits);
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
                     const uint32_t* digit_offsets = nullptr, bool final_keys = true, int shift0 = 0,
                     uint2* ranges = nullptr, uint32_t range_tiles = 0,
-                    const unsigned long long* d_count = nullptr, bool scratch_cleared = false);
+                    const unsigned long long* d_count = nullptr, bool scratch_cleared = false,
+                    bool digit_counts = false);
 int onesweep_launches(int64_t n, int key_bits, bool offsets_supplied);
 
 // K4: emit (bin, record) pairs in depth order.  A bin is a square of
@@ -271,12 +274,14 @@ void launch_emit(const uint32_t* sorted_rec, int64_t n_vis, const uint2* rec_rec
                  int64_t n_keys, uint32_t* tile_key, uint32_t* tile_val, int rbits, int key_bits,
                  uint32_t* digit_hist, uint32_t* status, uint32_t* tile_counter, uint32_t* err,
                  cudaStream_t s);
-// The same emission with the counts on the device (one fused launch plus
-// the digit scan, or count / scan / write above a 2^21-record capacity; bins
-// of any size, per-tile lists included): n_vis_cap and key_cap are
-// capacities (key_tile/tile_val hold key_cap words); d_nvis and d_nkeys
-// (u64) the frame's visible records and bin keys.  A frame whose keys exceed
-// key_cap writes none and sets kErrOverflow.
+// The same emission with the counts on the device (one fused launch, or
+// count / scan / write above a 2^21-record capacity; bins of any size,
+// per-tile lists included): n_vis_cap and key_cap are capacities
+// (key_tile/tile_val hold key_cap words); d_nvis and d_nkeys (u64) the
+// frame's visible records and bin keys.  digit_hist receives the bin sort's
+// digit counts, not scanned (launch_onesweep with digit_counts scans them).
+// A frame whose keys exceed key_cap writes none and sets kErrOverflow.
+// Returns the launches.
 int launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const unsigned long long* d_nvis,
                          const uint2* rec_rect, int32_t bins_x, int bin_log2, int64_t key_cap,
                          const unsigned long long* d_nkeys, uint32_t* tile_key, uint32_t* tile_val,

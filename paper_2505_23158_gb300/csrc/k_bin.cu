@@ -621,15 +621,13 @@ int launch_emit_counted(const uint32_t* sorted_rec, int64_t n_vis_cap, const uns
         emit_write_kernel<4><<<nt, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, d_nvis, rec_rect, bin_log2, bins_x,
                                                          key_cap, status, tile_key, tile_val, rbits, P, last_mask,
                                                          digit_hist, err);
-        digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
-        return 4;
+        return 3;
     }
     emit_fused_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(sorted_rec, n_vis_cap, rec_rect, bin_log2, bins_x,
                                                             key_cap, tile_key, tile_val, rbits, P, last_mask,
                                                             digit_hist, status, tile_counter, err, d_nvis,
                                                             d_nkeys);
-    digit_scan_kernel<<<P, 256, 0, s>>>(digit_hist);
-    return 2;
+    return 1;
 }
 
 void launch_digit_scan(uint32_t* hist, int passes, cudaStream_t s) {

@@ -66,7 +66,8 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
               uint32_t dmask, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ status,
               uint32_t* __restrict__ counter, uint32_t* __restrict__ err, uint2* __restrict__ ranges,
-              int range_shift, uint32_t range_tiles, const unsigned long long* __restrict__ d_count) {
+              int range_shift, uint32_t range_tiles, const unsigned long long* __restrict__ d_count,
+              bool raw_counts) {
     constexpr int kTileN = kSortThreads * kIPT;
     __shared__ uint32_t s_whist[kWarps][kRadix];
     __shared__ uint32_t s_keys[kTileN];
@@ -85,6 +86,13 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
         const unsigned long long c = *d_count;
         if (c < (unsigned long long)n) n = (int64_t)c;
         if ((int64_t)tile * kTileN >= n) return;   // all later tiles are empty too
+    }
+    // the pass's digit offsets: given, or the exclusive scan of its digit
+    // counts taken here (every CTA the same)
+    uint32_t dbase = offsets[tid];
+    if (raw_counts) {
+        uint32_t dtotal;
+        dbase = block_exclusive_scan(dbase, s_scan, &dtotal);
     }
     const int64_t seg = (int64_t)tile * kTileN + (int64_t)warp * 32 * kIPT;
     const int64_t base = seg + lane;
@@ -172,7 +180,7 @@ onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin
         }
         st_volatile(st, kStInc | (excl + run));
     }
-    s_gbase[d] = offsets[d] + excl;
+    s_gbase[d] = dbase + excl;
     uint32_t total;
     s_dstart[d] = block_exclusive_scan(run, s_scan, &total);
     __syncthreads();
@@ -230,13 +238,13 @@ template <bool kWK, bool kV>
 void launch_pass(bool small, int64_t ntiles, const uint32_t* ki, const uint32_t* vi, uint32_t* ko,
                  uint32_t* vo, int64_t n, int shift, uint32_t dm, const uint32_t* off, uint32_t* st,
                  uint32_t* ctr, uint32_t* err, uint2* ranges, int range_shift, uint32_t range_tiles,
-                 const unsigned long long* d_count, cudaStream_t s) {
+                 const unsigned long long* d_count, bool raw, cudaStream_t s) {
     if (small)
         onesweep_pass<kSmallIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles, d_count);
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles, d_count, raw);
     else
         onesweep_pass<kSortIPT, kWK, kV><<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles, d_count);
+            ki, vi, ko, vo, n, shift, dm, off, st, ctr, err, ranges, range_shift, range_tiles, d_count, raw);
 }
 
 }  // namespace
@@ -248,7 +256,8 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int key_bits, void* scratch, uint32_t* err, cudaStream_t s,
                     const uint32_t* digit_offsets, bool final_keys, int shift0, uint2* ranges,
-                    uint32_t range_tiles, const unsigned long long* d_count, bool scratch_cleared) {
+                    uint32_t range_tiles, const unsigned long long* d_count, bool scratch_cleared,
+                    bool digit_counts) {
     const int P = passes_for(key_bits);
     if (P == 0 || (d_count ? n < 1 : n <= 1)) return 0;
     if (d_count && !digit_offsets) return 0;   // device counts need supplied digit offsets
@@ -260,6 +269,8 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
     uint32_t* status = counters + 32;
     const uint32_t last_mask = last_mask_for(key_bits);
     const uint32_t* offs = hist;
+    // supplied digit counts are scanned by the passes themselves
+    const bool raw = digit_offsets && digit_counts;
     if (digit_offsets) {
         // exclusive digit offsets supplied: clear only counters and look-back words
         if (!scratch_cleared)
@@ -280,10 +291,10 @@ int launch_onesweep(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t
         const int sh = shift0 + 8 * p;
         uint2* rg = p == P - 1 ? ranges : nullptr;
         if (values) {
-            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, s);
-            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, s);
+            if (wk) launch_pass<true, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, raw, s);
+            else launch_pass<false, true>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, raw, s);
         } else {
-            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, s);
+            launch_pass<true, false>(small, ntiles, ki, vi, ko, vo, n, sh, dm, offs + p * kRadix, stp, counters + p, err, rg, shift0, range_tiles, d_count, raw, s);
         }
         std::swap(ki, ko);
         std::swap(vi, vo);

@@ -696,11 +696,11 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
     if (!deferred)   // (frames without a sync set up their own sort scratch above)
         TRY(ensure(ctx, ws.sort, std::max(sort_scratch_bytes(n_vis, 32), sort_scratch_bytes(n_bkeys, tbits)), s));
     prof_begin(sl, LODGE_STAGE_DEPTH_SORT, s);
-    if (n_vis > 1) launch_digit_scan(po.depth_hist, 4, s);
+    // (the passes scan the projection's digit counts themselves)
     int w1 = launch_onesweep(ws.dkey.as<uint32_t>(), ws.dval.as<uint32_t>(), ws.dkey2.as<uint32_t>(),
                              ws.dval2.as<uint32_t>(), n_vis, 32, ws.sort.p, sl.d_small + kSmErr, s,
-                             po.depth_hist, true, 0, nullptr, 0, d_nvis, deferred);
-    prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, (n_vis > 1 ? 1 : 0) + onesweep_launches(n_vis, 32, true));
+                             po.depth_hist, true, 0, nullptr, 0, d_nvis, deferred, true);
+    prof_end(sl, LODGE_STAGE_DEPTH_SORT, s, onesweep_launches(n_vis, 32, true));
     DBuf& zs = w1 ? ws.dkey2 : ws.dkey;
     DBuf& rs = w1 ? ws.dval2 : ws.dval;
 
@@ -756,7 +756,8 @@ static lodge_status render_frame(lodge_ctx* ctx, Slot& sl, const DevScene& dsc, 
                              ws.tkey2.as<uint32_t>(), rbits ? nullptr : ws.tval2.as<uint32_t>(), n_bkeys,
                              tbits, deferred ? ws.sort2.p : ws.sort.p, sl.d_small + kSmErr, s,
                              ws.doffs.as<uint32_t>(), true, rbits,
-                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins, d_nbk, deferred);
+                             fused_ranges ? ws.ranges.as<uint2>() : nullptr, (uint32_t)nbins, d_nbk, deferred,
+                             deferred);   // deferred frames' emission leaves its digit counts unscanned
     prof_end(sl, LODGE_STAGE_TILE_SORT, s, onesweep_launches(n_bkeys, tbits, true));
     DBuf& ks = w2 ? ws.tkey2 : ws.tkey;
     DBuf& vs = w2 ? ws.tval2 : ws.tval;
