@@ -240,7 +240,7 @@ def measured_traffic(kernel_stage: str, units_per_launch: float):
     where the summary gives bytes per unit; None if there is no summary for
     it or its kernel source changed since."""
     import hashlib
-    files = {"tile_sort": "traffic_onesweep_tile_sort.txt", "blend": "traffic_blend_kernel.txt"}
+    files = {"blend": "traffic_blend_kernel.txt"}
     f = files.get(kernel_stage)
     if f is None:
         return None
