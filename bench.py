@@ -6,7 +6,7 @@ Workload: the outdoor LOD scene (16M / 4M / 1M / 250k Gaussians over a 1 km x
 300-pose street-level trajectory at 1920 x 1080.  A step renders
 --poses-per-step consecutive poses (400 by default, wrapping around the
 trajectory) in LOD+chunk mode with opacity blending (the paper's method)
-through one render call, whose frames take turns on six streams; value =
+through one render call, whose frames take turns on eight streams; value =
 frames/s over all ranks.  Inputs are resident in HBM before timing (5.0 GB
 scene, larger than L2, no flush between steps).  Reported beside it:
   * the same poses at full detail (every level-0 Gaussian) on the same GPU,

@@ -221,14 +221,14 @@ const char* last_error();
 lodge_status create_slot(lodge_ctx* ctx, Slot** out);
 // slot k >= 1 with its own stream (created on first use)
 lodge_status stream_slot(lodge_ctx* ctx, int k, Slot** out);
-// streams the frames of one multi-camera render call take turns on: six
-// for chunk frames; two for full-detail frames, whose working set (the whole
-// finest level) is far larger than L2, so that more of them in flight only
-// evict each other (measured at 1080p: chunk frames 5986 / 6344 frames/s
-// with 4 / 6 streams and no gain at 8; full-detail 717 / 641 / 613 with
-// 2 / 3 / 4)
-constexpr int kRenderStreams = 6;
-constexpr int kRenderStreamsFull = 2;
+// streams the frames of one multi-camera render call take turns on: eight
+// for chunk frames, three for full-detail frames, whose working set (the
+// whole finest level) is far larger than L2 (measured at 1080p: chunk frames
+// 5519 / 5718 / 5803 frames/s with 4 / 6 / 8 streams; full-detail frames
+// 596 / 705 with 2 / 3, their long compositing tails filled by the next
+// frame's stages)
+constexpr int kRenderStreams = 8;
+constexpr int kRenderStreamsFull = 3;
 
 // a batch of frames composited by one launch (lodge_capi.cu)
 struct BatchItem {
