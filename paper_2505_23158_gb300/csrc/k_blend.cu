@@ -222,28 +222,29 @@ __device__ __forceinline__ void blend_tile(const BlendFrame& f, int tile) {
             // flat walk over the hits, 8 batch positions at a time, the warp
             // leaving once all its pixels have stopped (T = 0)
             if (!__all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) {
-#pragma unroll 1
-                for (int g = 0; g < kBlendBatch / 8; ++g) {
-                    const uint32_t mw = g < 8 ? (g < 4 ? m[0] : m[1]) : (g < 12 ? m[2] : m[3]);
-                    uint32_t mb = (mw >> (8 * (g & 3))) & 0xffu;
-                    if (!mb) continue;
-                    // the eight positions unrolled (a warp-uniform test each),
-                    // so that the records' shared addresses are immediates
-                    const float4* ga = &sa[buf][g * 8];
-                    const float4* gb = &sb[buf][g * 8];
-                    const float* gc = &sc[buf][g * 8];
+                // the hits in batch order, taken bit by bit from the masks
+                // (a warp visits a quarter or less of a staged batch; a scan
+                // over all 128 positions with a test each cost more)
+                bool open = true;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (!(mb & (1u << j))) continue;
-                        const float4 a = ga[j];
-                        const float4 bb = gb[j];
-                        const float cz = gc[j];
+                for (int w = 0; w < kBlendBatch / 32; ++w) {
+                    uint32_t mw = open ? m[w] : 0u;
+                    uint32_t cnt8 = 0;
+                    while (mw) {
+                        const int k = w * 32 + __ffs(mw) - 1;
+                        mw &= mw - 1u;
+                        const float4 a = sa[buf][k];
+                        const float4 bb = sb[buf][k];
+                        const float cz = sc[buf][k];
                         float t0, w0, t1, w1;
                         row_pair_tw(a, bb, pxf - a.x, py0, t0, w0, t1, w1);
                         blend_px_flat<kCount>(alpha_of(bb, t0, w0), bb, cz, T0, C00, C01, C02, n_eval, n_used);
                         blend_px_flat<kCount>(alpha_of(bb, t1, w1), bb, cz, T1, C10, C11, C12, n_eval, n_used);
+                        if ((++cnt8 & 7u) == 0u && __all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) {
+                            open = false;
+                            break;
+                        }
                     }
-                    if (__all_sync(0xffffffffu, T0 == 0.f && T1 == 0.f)) break;
                 }
             }
         } else if (!__all_sync(0xffffffffu, done0 && done1)) {
