@@ -594,3 +594,24 @@ def test_deferred_frames_equal_synced_frames_dense_bins(ctx, torch_cuda, log2):
                 assert torch_cuda.equal(img, ref)
     finally:
         ctx.set_bin_size(-1)
+
+
+def test_long_camera_list_stats_and_images(ctx, plain_loaded, torch_cuda):
+    """A call over 300 cameras: each of the eight render slots gets more
+    frames than its 32-entry status ring holds, so the ring is taken entry by
+    entry while later frames run; every frame's stats equal the camera
+    rendered alone, and a sample of images equals the single renders bit for
+    bit."""
+    from paper_2505_23158_gb300.api import FULL
+    scene, cams, osc, sid = plain_loaded
+    rng = np.random.default_rng(9)
+    cl = []
+    for i in range(300):
+        eye = (rng.uniform(-0.4, 0.4), rng.uniform(-0.4, 0.4), -3.0 + rng.uniform(-0.3, 0.3))
+        cl.append(synth.look_at(eye, (0.0, 0.0, 1.0), (0, -1, 0), 64, 48, 60.0))
+    imgs, stats = ctx.render(sid, FULL, cl)
+    for i in list(range(0, 300, 7)) + [299]:
+        one, st = ctx.render(sid, FULL, cl[i])
+        assert st["n_keys"] == stats[i]["n_keys"] and st["n_visible"] == stats[i]["n_visible"], i
+        if i % 21 == 0 or i == 299:
+            assert torch_cuda.equal(one, imgs[i]), i
